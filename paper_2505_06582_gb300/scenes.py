@@ -1,0 +1,234 @@
+"""Seeded synthetic scenes for Gaussian Wave Splatting workloads.
+
+This module only draws inputs: Gaussian records (mean, quaternion, scales, opacity,
+per-wavelength amplitude), SLM descriptions and cotangent arrays.  It contains none of
+the method's arithmetic (no spectra, no propagation, no blending), so both the CUDA
+path and the CPU oracle can be fed from it without sharing any computation.
+
+Distributions follow the workloads of the paper's evaluation (2D Gaussians in a
+hologram volume about 1 cm deep in front of a 1920x1080, 8 um SLM; scenes of 15k to
+1M Gaussians; Sec. 5 and the supplement's hardware section), with the datasets
+replaced by random surfaces because the trained scenes are not available:
+
+* ``uniform_scene``  -- means uniform over the SLM aperture at z ~ U[z0, z1],
+  quaternions uniform on S^3 (4 iid normals, normalised), log-normal scales.
+* ``surface_scene``  -- means on random spheres (SLM-facing hemispheres) and tilted
+  planes, each Gaussian lying in its surface's tangent plane with a random in-plane
+  angle.
+
+Units: metres.  Means are float64; everything else is float32.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "SLM", "Scene", "uniform_scene", "surface_scene", "config_scene", "batched_sizes",
+    "cotangent", "random_field", "CONFIGS",
+]
+
+
+@dataclass
+class SLM:
+    """Hologram plane: H rows (y) by W columns (x), pixel pitch and wavelengths (m)."""
+    H: int
+    W: int
+    pitch_x: float
+    pitch_y: float
+    wavelengths: tuple
+
+    @property
+    def n_lambda(self) -> int:
+        return len(self.wavelengths)
+
+
+@dataclass
+class Scene:
+    mean: np.ndarray      # float64 [N,3]
+    quat: np.ndarray      # float32 [N,4]  (w, x, y, z)
+    scale: np.ndarray     # float32 [N,2]  (s_u, s_v)
+    opacity: np.ndarray   # float32 [N]
+    amp: np.ndarray       # float32 [N, n_lambda]
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.mean.shape[0])
+
+    def subset(self, idx) -> "Scene":
+        idx = np.asarray(idx)
+        return Scene(self.mean[idx].copy(), self.quat[idx].copy(), self.scale[idx].copy(),
+                     self.opacity[idx].copy(), self.amp[idx].copy(), dict(self.meta))
+
+    def concat(self, other: "Scene") -> "Scene":
+        return Scene(np.concatenate([self.mean, other.mean]), np.concatenate([self.quat, other.quat]),
+                     np.concatenate([self.scale, other.scale]),
+                     np.concatenate([self.opacity, other.opacity]),
+                     np.concatenate([self.amp, other.amp]), dict(self.meta))
+
+
+def _quat_from_frame(r1, r2, r3):
+    """Unit quaternion (w,x,y,z) whose rotation matrix has columns r1, r2, r3.
+
+    Input preparation only (builds a rotation from a drawn tangent frame)."""
+    m00, m10, m20 = r1[:, 0], r1[:, 1], r1[:, 2]
+    m01, m11, m21 = r2[:, 0], r2[:, 1], r2[:, 2]
+    m02, m12, m22 = r3[:, 0], r3[:, 1], r3[:, 2]
+    tr = m00 + m11 + m22
+    q = np.zeros((r1.shape[0], 4))
+    c0 = tr > 0
+    s = np.sqrt(np.maximum(tr + 1.0, 1e-300)) * 2
+    q[c0] = np.stack([0.25 * s, (m21 - m12) / s, (m02 - m20) / s, (m10 - m01) / s], 1)[c0]
+    c1 = (~c0) & (m00 > m11) & (m00 > m22)
+    s = np.sqrt(np.maximum(1.0 + m00 - m11 - m22, 1e-300)) * 2
+    q[c1] = np.stack([(m21 - m12) / s, 0.25 * s, (m01 + m10) / s, (m02 + m20) / s], 1)[c1]
+    c2 = (~c0) & (~c1) & (m11 > m22)
+    s = np.sqrt(np.maximum(1.0 + m11 - m00 - m22, 1e-300)) * 2
+    q[c2] = np.stack([(m02 - m20) / s, (m01 + m10) / s, 0.25 * s, (m12 + m21) / s], 1)[c2]
+    c3 = (~c0) & (~c1) & (~c2)
+    s = np.sqrt(np.maximum(1.0 + m22 - m00 - m11, 1e-300)) * 2
+    q[c3] = np.stack([(m10 - m01) / s, (m02 + m20) / s, (m12 + m21) / s, 0.25 * s], 1)[c3]
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    return q
+
+
+def _tangent_frame(normal, psi):
+    """Right-handed frame (r1, r2, r3=normal) with in-plane angle psi."""
+    n = normal / np.linalg.norm(normal, axis=1, keepdims=True)
+    helper = np.where(np.abs(n[:, 2:3]) < 0.9, np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]]))
+    e1 = np.cross(helper, n)
+    e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+    e2 = np.cross(n, e1)
+    c, s = np.cos(psi)[:, None], np.sin(psi)[:, None]
+    r1 = c * e1 + s * e2
+    r2 = -s * e1 + c * e2
+    return r1, r2, n
+
+
+def _lognormal_scales(rng, n, median, sigma_log):
+    return np.exp(rng.normal(math.log(median), sigma_log, size=(n, 2))).astype(np.float32)
+
+
+def uniform_scene(seed: int, n: int, slm: SLM, z_range=(1e-3, 5e-3), scale_median_px=4.0,
+                  sigma_log=0.5, opacity_range=(0.2, 1.0)) -> Scene:
+    """Means uniform over the aperture, quaternions uniform on S^3."""
+    rng = np.random.default_rng(seed)
+    ax, ay = slm.W * slm.pitch_x, slm.H * slm.pitch_y
+    mean = np.empty((n, 3))
+    mean[:, 0] = rng.uniform(-ax / 2, ax / 2, n)
+    mean[:, 1] = rng.uniform(-ay / 2, ay / 2, n)
+    mean[:, 2] = rng.uniform(z_range[0], z_range[1], n)
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    scale = _lognormal_scales(rng, n, scale_median_px * slm.pitch_x, sigma_log)
+    opacity = rng.uniform(opacity_range[0], opacity_range[1], n).astype(np.float32)
+    amp = rng.uniform(0.0, 1.0, (n, slm.n_lambda)).astype(np.float32)
+    return Scene(mean, q.astype(np.float32), scale, opacity, amp, {"kind": "uniform", "seed": seed})
+
+
+def surface_scene(seed: int, n: int, slm: SLM, n_surfaces=8, scale_median_px=2.0, sigma_log=0.5,
+                  opacity_range=(0.05, 1.0), z_clip=(2e-3, 10e-3)) -> Scene:
+    """Gaussians on random spheres (SLM-facing hemispheres) and tilted planes."""
+    rng = np.random.default_rng(seed)
+    ax, ay = slm.W * slm.pitch_x, slm.H * slm.pitch_y
+    counts = np.full(n_surfaces, n // n_surfaces)
+    counts[: n - counts.sum()] += 1
+    pts, nrm = [], []
+    for k in range(n_surfaces):
+        m = int(counts[k])
+        if m == 0:
+            continue
+        if rng.uniform() < 0.5:  # sphere, points on the hemisphere facing the SLM (z < z_c)
+            c = np.array([rng.uniform(-0.3 * ax, 0.3 * ax), rng.uniform(-0.3 * ay, 0.3 * ay),
+                          rng.uniform(4e-3, 8e-3)])
+            rad = rng.uniform(0.5e-3, 2e-3)
+            v = rng.normal(size=(m, 3))
+            v /= np.linalg.norm(v, axis=1, keepdims=True)
+            v[:, 2] = -np.abs(v[:, 2])
+            pts.append(c + rad * v)
+            nrm.append(v)
+        else:  # plane with a normal within 30 degrees of +z, a random rectangle of the aperture
+            cos_t = rng.uniform(math.cos(math.radians(30.0)), 1.0)
+            sin_t = math.sqrt(1.0 - cos_t * cos_t)
+            phi = rng.uniform(0, 2 * math.pi)
+            nv = np.array([sin_t * math.cos(phi), sin_t * math.sin(phi), cos_t])
+            hx, hy = rng.uniform(0.1, 0.45) * ax, rng.uniform(0.1, 0.45) * ay
+            cx, cy = rng.uniform(-ax / 2 + hx, ax / 2 - hx), rng.uniform(-ay / 2 + hy, ay / 2 - hy)
+            z0 = rng.uniform(3e-3, 9e-3)
+            x = rng.uniform(cx - hx, cx + hx, m)
+            y = rng.uniform(cy - hy, cy + hy, m)
+            z = z0 - (nv[0] * (x - cx) + nv[1] * (y - cy)) / nv[2]
+            pts.append(np.stack([x, y, z], 1))
+            nrm.append(np.tile(nv, (m, 1)))
+    mean = np.concatenate(pts)
+    normal = np.concatenate(nrm)
+    mean[:, 2] = np.clip(mean[:, 2], z_clip[0], z_clip[1])
+    psi = rng.uniform(0, 2 * math.pi, mean.shape[0])
+    r1, r2, r3 = _tangent_frame(normal, psi)
+    q = _quat_from_frame(r1, r2, r3).astype(np.float32)
+    scale = _lognormal_scales(rng, mean.shape[0], scale_median_px * slm.pitch_x, sigma_log)
+    opacity = rng.uniform(opacity_range[0], opacity_range[1], mean.shape[0]).astype(np.float32)
+    amp = rng.uniform(0.0, 1.0, (mean.shape[0], slm.n_lambda)).astype(np.float32)
+    return Scene(mean, q, scale, opacity, amp, {"kind": "surface", "seed": seed, "surfaces": n_surfaces})
+
+
+RGB = (638e-9, 520e-9, 450e-9)
+
+# name -> (slm, generator kwargs).  Sizes and distributions of the five workloads.
+CONFIGS = {
+    "c0_plain_fp64": dict(slm=SLM(128, 128, 8e-6, 8e-6, (520e-9,)), kind="uniform", seed=0, n=64),
+    "c1_slm_size": dict(slm=SLM(1080, 1920, 8e-6, 8e-6, RGB), kind="surface", seed=1, n=20_000, n_surfaces=8),
+    "c2_precision_at_scale": dict(slm=SLM(2160, 3840, 3.74e-6, 3.74e-6, RGB), kind="surface", seed=2,
+                                  n=1_000_000, n_surfaces=32),
+    "c4_differentiable": dict(slm=SLM(1080, 1920, 8e-6, 8e-6, RGB), kind="surface", seed=4, n=100_000,
+                              n_surfaces=8),
+    "headline_1m_1080p_3l": dict(slm=SLM(1080, 1920, 8e-6, 8e-6, RGB), kind="surface", seed=1,
+                                 n=1_000_000, n_surfaces=32),
+    "paper_tab3_1024x1280": dict(slm=SLM(1024, 1280, 8e-6, 8e-6, (520e-9,)), kind="surface", seed=5,
+                                 n=15_000, n_surfaces=8),
+    "paper_tab3_2000x2000": dict(slm=SLM(2000, 2000, 8e-6, 8e-6, (520e-9,)), kind="surface", seed=5,
+                                 n=15_000, n_surfaces=8),
+}
+
+
+def config_scene(name: str, n: int | None = None, seed: int | None = None):
+    """(scene, slm) for a named workload; ``n`` overrides the Gaussian count."""
+    cfg = CONFIGS[name]
+    slm = cfg["slm"]
+    n = cfg["n"] if n is None else n
+    seed = cfg["seed"] if seed is None else seed
+    if cfg["kind"] == "uniform":
+        return uniform_scene(seed, n, slm), slm
+    return surface_scene(seed, n, slm, n_surfaces=cfg.get("n_surfaces", 8)), slm
+
+
+def batched_sizes(n_scenes=64, lo=1_000, hi=200_000, seed=3):
+    """Scene sizes log-uniform in [lo, hi] (the batched multi-scene workload)."""
+    rng = np.random.default_rng(seed)
+    return [int(round(math.exp(rng.uniform(math.log(lo), math.log(hi))))) for _ in range(n_scenes)]
+
+
+def batched_scenes(slm: SLM, n_scenes=64, lo=1_000, hi=200_000, seed=3):
+    sizes = batched_sizes(n_scenes, lo, hi, seed)
+    return [surface_scene(seed + k, sizes[k], slm) for k in range(n_scenes)]
+
+
+def cotangent(seed: int, slm: SLM, dtype=np.complex64) -> np.ndarray:
+    """Seeded complex normal array [n_lambda][H][W] (a synthetic upstream gradient)."""
+    rng = np.random.default_rng(seed)
+    shape = (slm.n_lambda, slm.H, slm.W)
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(dtype)
+
+
+def random_field(seed: int, shape, dtype=np.complex128, zero_frac=0.0) -> np.ndarray:
+    """Seeded complex field with log-normal amplitudes and uniform phases."""
+    rng = np.random.default_rng(seed)
+    a = np.exp(rng.normal(0.0, 1.0, shape))
+    ph = rng.uniform(-math.pi, math.pi, shape)
+    f = a * np.exp(1j * ph)
+    if zero_frac > 0:
+        f[rng.uniform(size=shape) < zero_frac] = 0
+    return f.astype(dtype)
