@@ -1,0 +1,336 @@
+"""Benchmark of the Gaussian Wave Splatting hot path on GB300.
+
+Workload: 1M Gaussians on random surfaces (seeded), 1920x1080 SLM, 8 um pitch, 3 wavelengths
+(638/520/450 nm).  One step = one pass of the whole hot path over the batch: validation and
+precompute, depth sort, footprint binning, the mixed-precision splat (Eq. 10 summed by
+Eq. 12), the centred inverse FFT, double-phase encoding and -- when the library provides it
+-- the backward splat given a seeded cotangent of the field.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Rank 0 prints ONE JSON line.  Under torchrun every rank runs an independent replica
+(the path shards by hologram with no exchange): value = holograms of all ranks / max time.
+``--impl reference`` times the FP64 CPU oracle (the reference arm of this project) on a
+bounded sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "holograms/s (1M Gaussians, 1920x1080, 3 λ) fwd & fwd+bwd; Gaussian·freq-px/s"
+WORKLOAD = "headline_1m_1080p_3l"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=None, help="override the Gaussian count (testing only)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-i", str(self.index),
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(ms: float, world: int, dist=None, device=None) -> float:
+    """Largest per-rank time (the job takes as long as its slowest replica)."""
+    if world <= 1 or dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world: int, ms_per_step: float) -> float:
+    """Whole-job holograms/s: every rank produces one hologram per step."""
+    return world * 1000.0 / ms_per_step
+
+
+def cpu_baseline(scene, slm, seconds: float, seed=7):
+    """FP64 oracle on the host cores: sampled frequencies x all Gaussians, scaled to holograms/s."""
+    import oracle as O
+    threads = O.num_threads()
+    rng = np.random.default_rng(seed)
+    k = 128
+    total_pairs, t_used = 0, 0.0
+    while t_used < seconds * 0.5:
+        lam = rng.integers(0, slm.n_lambda, k).astype(np.int32)
+        r = rng.integers(0, slm.H, k).astype(np.int32)
+        c = rng.integers(0, slm.W, k).astype(np.int32)
+        t0 = time.perf_counter()
+        O.spectrum_at(scene, slm, lam, r, c)
+        dt = time.perf_counter() - t0
+        total_pairs += k * scene.n
+        t_used += dt
+        if dt < seconds * 0.1:
+            k *= 2
+    pairs_per_s = total_pairs / t_used
+    holo = pairs_per_s / (scene.n * slm.H * slm.W * slm.n_lambda)
+    return {"value": holo, "unit": "holograms/s", "cores": threads, "kind": "oracle",
+            "sample": f"{total_pairs // scene.n} sampled (wavelength, frequency) spectrum values over all "
+                      f"{scene.n} Gaussians in {t_used:.1f} s ({pairs_per_s:.3g} Gaussian-frequency pairs/s); "
+                      f"scaled by N*H*W*L; the inverse DFT (O(HW(H+W)), < 0.1% of the pairs) is not timed"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2505_06582_gb300.scenes import config_scene
+    scene, slm = config_scene(WORKLOAD, n=args.n)
+    per = []
+    for _ in range(args.warmup):
+        cpu_baseline(scene, slm, seconds=2.0)
+    for _ in range(args.steps):
+        per.append(cpu_baseline(scene, slm, seconds=max(4.0, 60.0 / max(args.steps, 1))))
+    v = statistics.median(p["value"] for p in per)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "holograms/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_gaussians": scene.n, "H": slm.H, "W": slm.W,
+                       "n_lambda": slm.n_lambda, "pitch_m": slm.pitch_x},
+            "cpu_baseline": {"kind": "oracle", "cores": per[0]["cores"], "sample": per[0]["sample"], "value": v,
+                             "unit": "holograms/s"},
+            "e2e": {"value": v, "unit": "holograms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2505_06582_gb300 import gws
+    from paper_2505_06582_gb300.scenes import config_scene, cotangent
+
+    rank, world, local = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scene, slm = config_scene(WORKLOAD, n=args.n)
+    g = gws.Gaussians.from_scene(scene, dev)
+    S = gws.Slm.of(slm)
+    have_bwd = True
+    cot = torch.as_tensor(cotangent(11, slm), device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    gws.prepare(S)
+    ws = torch.empty(gws.workspace_size([g.n], S, gws.make_opts()), dtype=torch.uint8, device=dev)
+    field = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.complex64, device=dev)
+    phase = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.float32, device=dev)
+    timers = dict(debug_flags=gws.DEBUG_TIME_KERNELS)
+
+    def step(timed_kernels):
+        kw = timers if timed_kernels else {}
+        launches = 0
+        gws.forward(g, S, out=field, workspace=ws, **kw)
+        launches += gws.last_launch_count()
+        t_splat = gws.kernel_time_ms(gws.TIMER_SPLAT_FWD) if timed_kernels else None
+        t_fft = gws.kernel_time_ms(gws.TIMER_FFT) if timed_kernels else None
+        gws.encode(field, S, out=phase, workspace=ws, **kw)
+        launches += gws.last_launch_count()
+        t_enc = gws.kernel_time_ms(gws.TIMER_ENCODE) if timed_kernels else None
+        t_bwd = None
+        if have_bwd:
+            gws.backward(g, S, cot, workspace=ws, **kw)
+            launches += gws.last_launch_count()
+            t_bwd = gws.kernel_time_ms(gws.TIMER_SPLAT_BWD) if timed_kernels else None
+        return launches, t_splat, t_fft, t_enc, t_bwd
+
+    try:
+        step(False)
+    except gws.GwsError as e:
+        if e.code != 6:
+            raise
+        have_bwd = False
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+
+    # device-timed steps (inputs resident in HBM; L2 flushed before each step, outside the events)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times, splat_ms, fft_ms, enc_ms, bwd_ms, launches = [], [], [], [], [], 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        n_l, ts, tf, te, tb = step(True)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        launches += n_l
+        splat_ms.append(ts)
+        fft_ms.append(tf)
+        enc_ms.append(te)
+        if tb is not None:
+            bwd_ms.append(tb)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(sum(times) / len(times), world, dist if world > 1 else None, dev)
+    value = aggregate_rate(world, ms)
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    host = {k: getattr(g, k).cpu().pin_memory() for k in ("mean", "quat", "scale", "opacity", "amp")}
+    cot_host = cot.cpu().pin_memory()
+    phase_host = torch.empty(phase.shape, dtype=phase.dtype).pin_memory()
+    dbuf = {k: torch.empty_like(getattr(g, k)) for k in host}
+    cbuf = torch.empty_like(cot)
+    grads_host = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in host.items()}
+    h2d = sum(v.numel() * v.element_size() for v in host.values()) + (cot_host.numel() * cot_host.element_size()
+                                                                       if have_bwd else 0)
+    d2h = phase_host.numel() * phase_host.element_size() + (
+        sum(v.numel() * v.element_size() for v in grads_host.values()) if have_bwd else 0)
+    e2e_times = []
+    for _ in range(max(2, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in host:
+            dbuf[k].copy_(host[k], non_blocking=True)
+        gd = gws.Gaussians(dbuf["mean"], dbuf["quat"], dbuf["scale"], dbuf["opacity"], dbuf["amp"])
+        gws.forward(gd, S, out=field, workspace=ws)
+        gws.encode(field, S, out=phase, workspace=ws)
+        phase_host.copy_(phase, non_blocking=True)
+        if have_bwd:
+            cbuf.copy_(cot_host, non_blocking=True)
+            gr = gws.backward(gd, S, cbuf, workspace=ws)
+            for k in grads_host:
+                grads_host[k].copy_(gr[k], non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = max_over_ranks(statistics.median(e2e_times), world, dist if world > 1 else None, dev)
+
+    # roofline of the dominant kernel (the splat): algorithmic pairs / its event time
+    pairs = gws.footprint_pairs(g, S, workspace=ws)
+    dense = g.n * S.H * S.W * S.n_lambda
+    splat = statistics.median(splat_ms)
+    sm_mhz = clk.get("sm_mhz") or 1440.0
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_pairs = n_sm * sm_mhz * 1e6 * 6.4  # issue-bound: 128 lanes / 20 issues per pair (= MUFU bound, 6.4/clk/SM)
+    achieved = pairs / (splat * 1e-3)
+    dom_ms = {"splat_fwd": splat, "fft": statistics.median(fft_ms), "encode": statistics.median(enc_ms)}
+    if bwd_ms:
+        dom_ms["splat_bwd"] = statistics.median(bwd_ms)
+    fwd_ms = ms - (dom_ms.get("splat_bwd", 0.0))
+
+    line = {"metric": METRIC, "value": value, "unit": "holograms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_gaussians": g.n, "H": S.H, "W": S.W, "n_lambda": S.n_lambda,
+                       "pitch_m": S.pitch_x, "blend": "oit", "precision": "mixed", "trunc_eps": 1e-5,
+                       "step": "forward+encode" + ("+backward" if have_bwd else ""),
+                       "l2": "flushed before each timed step (512 MB write)", "parallelism": f"replicas x{world}"},
+            "fwd_holograms_per_s": world * 1000.0 / fwd_ms if have_bwd else value,
+            "pairs": {"dense_per_hologram": dense, "algorithmic_per_hologram": pairs,
+                      "dense_pairs_per_s": world * dense / (fwd_ms * 1e-3),
+                      "algorithmic_pairs_per_s": world * pairs / (fwd_ms * 1e-3)},
+            "kernel_ms": dom_ms,
+            "roofline": {"kernel": "k_splat_mixed", "bound": "alu", "achieved": achieved / 1e9,
+                         "peak": peak_pairs / 1e9, "unit": "Gpair/s", "frac": achieved / peak_pairs,
+                         "traffic": None,
+                         "peak_basis": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median sampled) x 6.4 pairs/clk/SM"},
+            "e2e": {"value": aggregate_rate(world, e2e_ms), "unit": "holograms/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(scene, slm, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,239 @@
+/*
+ * gws.h -- C ABI of libgws, the GB300 (sm_103a) hot path of Gaussian Wave Splatting
+ * (Choi et al., "Gaussian Wave Splatting for Computer-Generated Holography", arXiv
+ * 2505.06582).
+ *
+ * What the library computes (paper sections / equations in brackets):
+ *   N 2D Gaussians in hologram space -> the complex field at the SLM plane.
+ *   - Each Gaussian i has a mean mu_i (3D), a rotation q_i (unit quaternion, columns
+ *     r1 = t_u, r2 = t_v, r3 = normal) and scales s_u, s_v [Sec. 3], an opacity o_i
+ *     [Eq. 2] and a per-wavelength amplitude c_il [Eq. 5].
+ *   - Its angular spectrum at the SLM is the closed form of Eq. 10 evaluated on the
+ *     tilted-plane remapped frequencies with the Jacobian det J = k_oz / k_z and the
+ *     reference-wave shift f_r = (0, 0, 1/lambda) [Sec. 4.1, Eq. 9-10, supplement Sec. 1.2]:
+ *        u_i(f) = 2 pi s_u s_v |r3.f| / f_z exp(-2 pi^2 [s_u^2 (r1.d)^2 + s_v^2 (r2.d)^2])
+ *                 exp(-j 2 pi f.mu_i),     d = f - f_r,  f_z = sqrt(1/lambda^2 - fx^2 - fy^2)
+ *     in ordinary frequency (cycles/m); zero outside fx^2 + fy^2 < 1/lambda^2 [Eq. 4].
+ *   - Blending: the order-invariant Fourier-domain sum of Eq. 12,
+ *        u_SLM(f) = sum_i c_il o_i u_i(f)                                (GWS_BLEND_OIT)
+ *     or the depth-sorted transmittance variant of Eq. 5-6 with T_i held at the
+ *     Gaussian's centre, T_i = prod_{j in front} (1 - alpha_j(mu_i)), alpha from Eq. 2 and
+ *     the t_eps = 1/255 threshold of Algorithm S2                         (GWS_BLEND_SORTED_T).
+ *   - One inverse FFT [Algorithm S1, S4; Eq. 3]: the field is the centred inverse DFT of
+ *     u_SLM scaled by dfx dfy.
+ *   - Double-phase encoding for a phase-only SLM [Sec. 5 and the supplement's phase
+ *     encoding paragraph].
+ *
+ * Layouts (all row-major; row r <-> y, column c <-> x; centred grids):
+ *   fx(c) = (c - floor(W/2)) / (W pitch_x),  fy(r) = (r - floor(H/2)) / (H pitch_y);
+ *   field pixel (r, c) sits at x = (c - floor(W/2)) pitch_x, y = (r - floor(H/2)) pitch_y.
+ *   Gaussians are structure-of-arrays: mean double[n][3] (m), quat float[n][4] (w,x,y,z,
+ *   normalised inside), scale float[n][2] (m), opacity float[n], amp float[n][n_lambda].
+ *   Fields / spectra are interleaved complex [n_lambda][H][W]: complex64 for
+ *   GWS_PREC_MIXED, complex128 for GWS_PREC_FP64.
+ *
+ * Ownership: every array argument is caller-owned DEVICE memory except
+ *   gws_slm.wavelengths (host, read during the call).  The call path never allocates:
+ *   scratch lives in the caller's workspace (gws_opts.workspace, at least
+ *   gws_workspace_size() bytes, 256-byte aligned).  The one exception is the cuFFT plan of
+ *   a new grid shape, created (and allocated by cuFFT) by gws_prepare() or on the first
+ *   call with that shape; call gws_prepare() before capturing calls into a CUDA graph.
+ *
+ * Errors: host-checkable argument errors return a gws_status synchronously and launch
+ *   nothing.  Conditions only the device can see (non-finite inputs, opacity outside
+ *   [0,1], non-positive scales, a zero quaternion, a wait that timed out) are recorded in
+ *   a status word inside the workspace; read it with gws_get_device_status().  Calls are
+ *   asynchronous on gws_opts.stream.  No exception crosses the ABI.  There is no CPU
+ *   fallback: without a CUDA device every compute entry point returns GWS_ERR_CUDA.
+ */
+#ifndef GWS_H
+#define GWS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GWS_API __attribute__((visibility("default")))
+#else
+#define GWS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GWS_ABI_VERSION 1
+#define GWS_MAX_LAMBDA 16  /* wavelengths per call */
+#define GWS_MAX_SCENES 128 /* scenes per batched call */
+
+typedef enum {
+    GWS_OK = 0,
+    GWS_ERR_INVALID_ARG = 1, /* bad argument (host) or bad Gaussian value (device status) */
+    GWS_ERR_WORKSPACE = 2,   /* workspace missing, too small or misaligned */
+    GWS_ERR_CUDA = 3,        /* a CUDA / cuFFT call failed, or no device */
+    GWS_ERR_NONFINITE = 4,   /* device status: NaN / Inf among the inputs */
+    GWS_ERR_TIMEOUT = 5,     /* device status: a bounded wait gave up */
+    GWS_ERR_UNSUPPORTED = 6  /* combination not implemented (e.g. FP64 backward) */
+} gws_status;
+
+typedef enum {
+    GWS_BLEND_OIT = 0,     /* Eq. 12: order-invariant sum, T_i = 1 */
+    GWS_BLEND_SORTED_T = 1 /* Eq. 5-6 with T_i at the Gaussian's centre (depth-sorted) */
+} gws_blend;
+
+typedef enum {
+    GWS_PREC_FP64 = 0, /* every step in FP64, one thread per frequency pixel, no truncation */
+    GWS_PREC_MIXED = 1 /* FP32 bulk, FP64 phase anchors, compensated sums, footprint truncation */
+} gws_precision;
+
+typedef enum {
+    GWS_DOMAIN_FIELD = 0,   /* forward writes the SLM field (after the inverse FFT) */
+    GWS_DOMAIN_SPECTRUM = 1 /* forward writes u_SLM(f) itself (no FFT); backward takes dL/du_SLM */
+} gws_domain;
+
+enum {
+    GWS_DEBUG_FORCE_TIMEOUT = 1u, /* the splat kernel's first wait targets a barrier nothing
+                                     arrives on: it gives up after timeout_cycles, records
+                                     GWS_ERR_TIMEOUT and returns (tests the bounded waits) */
+    GWS_DEBUG_TIME_KERNELS = 2u   /* record CUDA events around the splat / FFT / encode launches
+                                     on opts.stream; read them with gws_kernel_time_ms() */
+};
+
+typedef enum { /* timers of GWS_DEBUG_TIME_KERNELS */
+    GWS_TIMER_SPLAT_FWD = 0,
+    GWS_TIMER_SPLAT_BWD = 1,
+    GWS_TIMER_FFT = 2,
+    GWS_TIMER_ENCODE = 3,
+    GWS_TIMER_TOTAL = 4 /* the whole entry point */
+} gws_timer;
+
+typedef struct {
+    const double *mean;   /* [n][3], metres */
+    const float *quat;    /* [n][4], (w, x, y, z), any non-zero norm */
+    const float *scale;   /* [n][2], (s_u, s_v) > 0, metres */
+    const float *opacity; /* [n], in [0, 1] */
+    const float *amp;     /* [n][n_lambda] */
+} gws_gaussians;
+
+typedef struct { /* gradients, same layout as gws_gaussians, device memory */
+    double *mean;
+    float *quat;
+    float *scale;
+    float *opacity;
+    float *amp;
+} gws_gaussians_grad;
+
+typedef struct {
+    int H, W;                  /* rows (y), columns (x) */
+    double pitch_x, pitch_y;   /* metres */
+    int n_lambda;              /* 1 .. GWS_MAX_LAMBDA */
+    const double *wavelengths; /* HOST array [n_lambda], metres */
+} gws_slm;
+
+typedef struct {
+    int blend;        /* gws_blend */
+    int prec;         /* gws_precision */
+    int domain;       /* gws_domain */
+    int phase_match;  /* 1: multiply each Gaussian by exp(+j 2 pi mu_z / lambda) (supplement,
+                         "we match the phase of each wavefront"); default 0 */
+    float trunc_eps;  /* MIXED: relative amplitude below which a Gaussian's spectrum is cut
+                         (footprint ellipse exp(-E) >= eps); default 1e-5 */
+    float alpha_min;  /* SORTED_T: t_eps of Algorithm S2; default 1/255 */
+    int tile_cfg;     /* MIXED: splat tile configuration, 0 = tuned / default */
+    uint32_t debug_flags;    /* GWS_DEBUG_* */
+    uint64_t timeout_cycles; /* bound of every device-side wait, in SM clock cycles */
+    void *stream;            /* cudaStream_t (NULL = legacy default stream) */
+    void *workspace;         /* device scratch, >= gws_workspace_size() bytes */
+    size_t workspace_bytes;
+} gws_opts;
+
+/* Fills *o with the defaults listed above (OIT, MIXED, FIELD). */
+GWS_API void gws_opts_default(gws_opts *o);
+
+/* Human-readable name of a status code (static storage). */
+GWS_API const char *gws_status_string(gws_status s);
+
+/* Library version (GWS_ABI_VERSION). */
+GWS_API int gws_version(void);
+
+/* Workspace bytes needed by forward / backward / encode for scenes of sizes n[0..n_scenes)
+ * on this SLM with these options (blend, prec, domain, tile_cfg matter).  Host only. */
+GWS_API gws_status gws_workspace_size(const int64_t *n, int n_scenes, const gws_slm *slm, const gws_opts *opts,
+                              size_t *bytes);
+
+/* Creates the cuFFT plans for this grid (batch n_lambda and n_lambda * n_scenes) and
+ * selects the CUDA device of the current context.  May allocate (inside cuFFT).  Call it
+ * before capturing gws_* calls into a CUDA graph. */
+GWS_API gws_status gws_prepare(const gws_slm *slm, const gws_opts *opts, int n_scenes);
+
+/* Forward [Eq. 10, Eq. 12 or Eq. 5-6, Eq. 3]: field_out = centred inverse DFT of u_SLM
+ * (domain FIELD) or u_SLM itself (domain SPECTRUM); complex [n_lambda][H][W], complex64
+ * (MIXED) or complex128 (FP64).  n = 0 gives a zero field. */
+GWS_API gws_status gws_forward(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
+                       void *field_out);
+
+/* Batched forward: n_scenes scenes (each its own arrays and size n[k]) on one SLM, one
+ * persistent splat launch over every (scene, wavelength, frequency tile).  field_out[k]
+ * as in gws_forward.  Results equal per-scene gws_forward calls bit for bit. */
+GWS_API gws_status gws_forward_batched(const gws_gaussians *scenes, const int64_t *n, int n_scenes,
+                               const gws_slm *slm, const gws_opts *opts, void *const *field_out);
+
+/* Backward (MIXED only): given grad_field = dL/d(field) in PyTorch's complex convention
+ * (dL/dRe + j dL/dIm), complex64 [n_lambda][H][W] (or dL/du_SLM with domain SPECTRUM),
+ * writes dL/d(mean, quat, scale, opacity, amp) into out (device, same layout as the
+ * inputs; every array is overwritten).  The spectra are recomputed, never stored. */
+GWS_API gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
+                        const void *grad_field, gws_gaussians_grad *out);
+
+/* Double-phase encoding: a = |u| / a_max (a_max = per-wavelength max |u|, or amp_scale if
+ * > 0; a is clamped to 1), phi = arg u, P1,2 = phi -/+ acos(a); pixel (r, c) takes P1 when
+ * r + c is even, else P2; wrapped to [-pi, pi).  field: complex64 (MIXED) or complex128
+ * (FP64) [n_lambda][H][W]; phase_out: float [n_lambda][H][W]. */
+GWS_API gws_status gws_encode(const void *field, const gws_slm *slm, const gws_opts *opts, float *phase_out,
+                      float amp_scale);
+
+/* Synchronises opts->stream and returns the device status word of the last call that
+ * used this workspace (GWS_OK, GWS_ERR_NONFINITE, GWS_ERR_INVALID_ARG, GWS_ERR_TIMEOUT),
+ * then clears it. */
+GWS_API gws_status gws_get_device_status(const gws_opts *opts);
+
+/* ---- inspection entry points (intermediate results of the forward, for testing) ---- */
+
+/* Depth order (Algorithm S2: front = nearest the SLM = smallest mu_z; ties by index):
+ * order_out[k] = input index of the k-th Gaussian, int32 device [n]. */
+GWS_API gws_status gws_depth_order(const gws_gaussians *g, int64_t n, const gws_opts *opts, int32_t *order_out);
+
+/* Transmittance T_i at each Gaussian's centre (SORTED_T reading of Eq. 5-6), FP64 device
+ * [n], indexed by input order. */
+GWS_API gws_status gws_transmittance(const gws_gaussians *g, int64_t n, const gws_opts *opts, double *T_out);
+
+/* Spectral footprints of the MIXED path for wavelength index l: per input Gaussian the
+ * normalised ellipse (a00, a01, a11) such that every frequency with fx^2 a00 + 2 fx fy a01
+ * + fy^2 a11 > 1 has exp(-E) < trunc_eps; float device [n][3]. */
+GWS_API gws_status gws_footprints(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts, int l,
+                          float *ellipse_out);
+
+/* Milliseconds between the events of timer `which` recorded by the last call on this host
+ * thread that set GWS_DEBUG_TIME_KERNELS (synchronises on the stop event); -1 if none. */
+GWS_API float gws_kernel_time_ms(int which);
+
+/* Algorithmic work of the MIXED splat: the number of (Gaussian, wavelength, grid frequency)
+ * triples inside the footprint ellipses (the pairs the truncated sum of Eq. 12 needs),
+ * written to *pairs (host).  Synchronises the stream. */
+GWS_API gws_status gws_footprint_pairs(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
+                                       unsigned long long *pairs);
+
+/* Number of kernel launches the last forward / backward / encode issued (host counter). */
+GWS_API int gws_last_launch_count(void);
+
+/* Runs each splat tile configuration on this problem, keeps the fastest for this
+ * (H, W, n_lambda, n) class in an in-process table and returns its id in *best_cfg.
+ * Synchronises the stream; not capturable. */
+GWS_API gws_status gws_autotune(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
+                        void *field_scratch, int *best_cfg);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GWS_H */

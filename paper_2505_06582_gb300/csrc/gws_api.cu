@@ -1,0 +1,702 @@
+// gws_api.cu -- the C ABI of libgws (declared in include/gws.h): argument checks, the
+// workspace layout, the cuFFT plan cache and the launch sequence of each entry point.
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "gws_prep.h"
+
+namespace gws {
+
+static thread_local int t_launches = 0;
+void count_launches(int k) { t_launches += k; }
+
+// ---- optional kernel timers (GWS_DEBUG_TIME_KERNELS) -----------------------------------
+struct Timers {
+    cudaEvent_t ev[5][2];
+    bool made = false, used[5] = {false, false, false, false, false};
+};
+static thread_local Timers t_timers;
+
+static void timer_mark(const gws_opts *o, int which, int edge, cudaStream_t s) {
+    if (!(o->debug_flags & GWS_DEBUG_TIME_KERNELS)) return;
+    Timers &T = t_timers;
+    if (!T.made) {
+        for (int i = 0; i < 5; ++i)
+            for (int j = 0; j < 2; ++j) cudaEventCreate(&T.ev[i][j]);
+        T.made = true;
+    }
+    cudaEventRecord(T.ev[which][edge], s);
+    if (edge == 1) T.used[which] = true;
+}
+static void timers_reset(const gws_opts *o) {
+    if (!(o->debug_flags & GWS_DEBUG_TIME_KERNELS)) return;
+    for (int i = 0; i < 5; ++i) t_timers.used[i] = false;
+}
+
+// cuFFT batch size of one scene's slices
+struct PlanKey {
+    int dev, H, W, batch, dbl, dir;
+    bool operator<(const PlanKey &o) const {
+        return std::tie(dev, H, W, batch, dbl, dir) < std::tie(o.dev, o.H, o.W, o.batch, o.dbl, o.dir);
+    }
+};
+struct Plan {
+    cufftHandle h;
+    size_t work;
+};
+static std::mutex g_plan_mu;
+static std::map<PlanKey, Plan> g_plans;
+
+static gws_status get_plan(int H, int W, int batch, int dbl, Plan *out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GWS_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    PlanKey k{dev, H, W, batch, dbl, 0};
+    auto it = g_plans.find(k);
+    if (it != g_plans.end()) {
+        *out = it->second;
+        return GWS_OK;
+    }
+    Plan p;
+    if (cufftCreate(&p.h) != CUFFT_SUCCESS) return GWS_ERR_CUDA;
+    if (cufftSetAutoAllocation(p.h, 0) != CUFFT_SUCCESS) return GWS_ERR_CUDA;
+    int dims[2] = {H, W};
+    size_t work = 0;
+    cufftResult r = cufftMakePlanMany(p.h, 2, dims, nullptr, 1, H * W, nullptr, 1, H * W, dbl ? CUFFT_Z2Z : CUFFT_C2C,
+                                      batch, &work);
+    if (r != CUFFT_SUCCESS) {
+        cufftDestroy(p.h);
+        return GWS_ERR_CUDA;
+    }
+    p.work = work;
+    g_plans[k] = p;
+    *out = p;
+    return GWS_OK;
+}
+
+static gws_status exec_fft(const Plan &p, void *data, void *work, int dbl, int direction, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    if (cufftSetStream(p.h, s) != CUFFT_SUCCESS) return GWS_ERR_CUDA;
+    if (cufftSetWorkArea(p.h, work) != CUFFT_SUCCESS) return GWS_ERR_CUDA;
+    cufftResult r = dbl ? cufftExecZ2Z(p.h, (cufftDoubleComplex *)data, (cufftDoubleComplex *)data, direction)
+                        : cufftExecC2C(p.h, (cufftComplex *)data, (cufftComplex *)data, direction);
+    count_launches(1);
+    return r == CUFFT_SUCCESS ? GWS_OK : GWS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------------------
+// workspace layout (one planner for the size query and for the calls)
+// ---------------------------------------------------------------------------------------
+
+struct Layout {
+    size_t status, queue, amax, gpre, ampc, dkey0, dkey1, dval0, dval1, skey0, skey1, hist, tsorted, tg, tdata;
+    size_t rec64, w64, fkey0, fkey1, fval0, fval1, rec, Rr, ikey0, ikey1, ival0, ival1, icount, invrec, gspec, bacc;
+    size_t cufft, total;
+    int tiles_x, tiles_y, n_tiles, cfg;
+};
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Planner {
+    size_t cur = 0;
+    size_t take(size_t bytes) {
+        size_t o = cur;
+        cur = align_up(cur + std::max<size_t>(bytes, 16));
+        return o;
+    }
+};
+
+static int default_cfg(const gws_opts *o) {
+    int c = o->tile_cfg;
+    if (c < 1 || c > n_tile_cfgs()) c = 1;
+    return c;
+}
+
+static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *slm, const gws_opts *o, Layout *L,
+                              bool need_fft_plans) {
+    Planner P;
+    const int nl = slm->n_lambda;
+    const long long n = std::max<long long>(n_total, 1);
+    const long long n_rec = n * nl;
+    L->cfg = default_cfg(o);
+    const TileCfg tc = tile_cfg(L->cfg);
+    L->tiles_x = (slm->W + tc.tw - 1) / tc.tw;
+    L->tiles_y = (slm->H + tc.th - 1) / tc.th;
+    L->n_tiles = L->tiles_x * L->tiles_y;
+    const long long n_items = (long long)n_scenes * nl * L->n_tiles;
+
+    L->status = P.take(16);
+    L->queue = P.take(16);
+    L->amax = P.take(sizeof(unsigned long long) * GWS_MAX_LAMBDA);
+    L->gpre = P.take(sizeof(GPre) * n);
+    L->ampc = P.take(sizeof(float) * n * nl);
+    L->dkey0 = P.take(8 * n);
+    L->dkey1 = P.take(8 * n);
+    L->dval0 = P.take(4 * n);
+    L->dval1 = P.take(4 * n);
+    L->skey0 = P.take(4 * n);
+    L->skey1 = P.take(4 * n);
+    L->tsorted = P.take(8 * n);
+    L->tg = P.take(8 * n);
+    L->tdata = P.take(sizeof(TData) * n);
+    size_t hist_words = std::max(sort_hist_words(n), sort_hist_words(std::max(n_rec, n_items)));
+    L->hist = P.take(4 * hist_words);
+    if (o->prec == GWS_PREC_FP64) {
+        L->rec64 = P.take(sizeof(Rec64) * n);
+        L->w64 = P.take(8 * n * nl);
+        L->fkey0 = L->fkey1 = L->fval0 = L->fval1 = L->rec = L->Rr = 0;
+        L->ikey0 = L->ikey1 = L->ival0 = L->ival1 = L->icount = L->invrec = L->gspec = L->bacc = 0;
+    } else {
+        L->rec64 = L->w64 = 0;
+        L->fkey0 = P.take(8 * n_rec);
+        L->fkey1 = P.take(8 * n_rec);
+        L->fval0 = P.take(4 * n_rec);
+        L->fval1 = P.take(4 * n_rec);
+        L->rec = P.take(sizeof(Rec) * n_rec);
+        L->Rr = P.take(4 * n_rec);
+        L->ikey0 = P.take(4 * n_items);
+        L->ikey1 = P.take(4 * n_items);
+        L->ival0 = P.take(4 * n_items);
+        L->ival1 = P.take(4 * n_items);
+        L->icount = P.take(4 * n_items);
+        L->invrec = P.take(4 * n_rec);
+        L->gspec = P.take(sizeof(float) * 2 * (size_t)nl * slm->H * slm->W);
+        L->bacc = P.take(sizeof(double) * 13 * n_rec);
+    }
+    size_t fft_work = 0;
+    if (need_fft_plans) {
+        Plan p;
+        gws_status st = get_plan(slm->H, slm->W, nl, o->prec == GWS_PREC_FP64, &p);
+        if (st != GWS_OK) return st;
+        fft_work = p.work;
+    }
+    L->cufft = P.take(fft_work);
+    L->total = P.cur;
+    return GWS_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// argument checks
+// ---------------------------------------------------------------------------------------
+
+static bool finite_pos(double x) { return std::isfinite(x) && x > 0; }
+
+static gws_status check_slm(const gws_slm *slm) {
+    if (!slm) return GWS_ERR_INVALID_ARG;
+    if (slm->H < 1 || slm->W < 1 || (long long)slm->H * slm->W > (1ll << 31)) return GWS_ERR_INVALID_ARG;
+    if (!finite_pos(slm->pitch_x) || !finite_pos(slm->pitch_y)) return GWS_ERR_INVALID_ARG;
+    if (slm->n_lambda < 1 || slm->n_lambda > GWS_MAX_LAMBDA || !slm->wavelengths) return GWS_ERR_INVALID_ARG;
+    for (int l = 0; l < slm->n_lambda; ++l)
+        if (!finite_pos(slm->wavelengths[l])) return GWS_ERR_INVALID_ARG;
+    return GWS_OK;
+}
+
+static gws_status check_opts(const gws_opts *o) {
+    if (!o) return GWS_ERR_INVALID_ARG;
+    if (o->blend != GWS_BLEND_OIT && o->blend != GWS_BLEND_SORTED_T) return GWS_ERR_INVALID_ARG;
+    if (o->prec != GWS_PREC_FP64 && o->prec != GWS_PREC_MIXED) return GWS_ERR_INVALID_ARG;
+    if (o->domain != GWS_DOMAIN_FIELD && o->domain != GWS_DOMAIN_SPECTRUM) return GWS_ERR_INVALID_ARG;
+    if (!(o->trunc_eps > 0.f && o->trunc_eps < 1.f)) return GWS_ERR_INVALID_ARG;
+    if (!(o->alpha_min >= 0.f && o->alpha_min < 1.f)) return GWS_ERR_INVALID_ARG;
+    if (o->timeout_cycles == 0) return GWS_ERR_INVALID_ARG;
+    if (o->tile_cfg < 0 || o->tile_cfg > n_tile_cfgs()) return GWS_ERR_INVALID_ARG;
+    return GWS_OK;
+}
+
+static gws_status check_gaussians(const gws_gaussians *g, long long n) {
+    if (n < 0 || n > (1ll << 30)) return GWS_ERR_INVALID_ARG;
+    if (n == 0) return GWS_OK;
+    if (!g || !g->mean || !g->quat || !g->scale || !g->opacity || !g->amp) return GWS_ERR_INVALID_ARG;
+    return GWS_OK;
+}
+
+static gws_status check_workspace(const gws_opts *o, const Layout &L) {
+    if (!o->workspace) return GWS_ERR_WORKSPACE;
+    if (((uintptr_t)o->workspace) & 255u) return GWS_ERR_WORKSPACE;
+    if (o->workspace_bytes < L.total) return GWS_ERR_WORKSPACE;
+    return GWS_OK;
+}
+
+#define CU(x)                                    \
+    do {                                         \
+        if ((x) != cudaSuccess) return GWS_ERR_CUDA; \
+    } while (0)
+#define GS(x)                          \
+    do {                               \
+        gws_status _s = (x);           \
+        if (_s != GWS_OK) return _s;   \
+    } while (0)
+
+template <typename T>
+static T *at(const gws_opts *o, size_t off) {
+    return reinterpret_cast<T *>(static_cast<char *>(o->workspace) + off);
+}
+
+static double dz_max(const gws_slm *slm, double lam) {
+    const double fxm = (double)(slm->W / 2) / (slm->W * slm->pitch_x);
+    const double fym = (double)(slm->H / 2) / (slm->H * slm->pitch_y);
+    const double rho2 = fxm * fxm + fym * fym, k2 = 1.0 / (lam * lam);
+    return rho2 >= k2 ? 1.0 / lam : 1.0 / lam - std::sqrt(k2 - rho2);
+}
+
+// ---------------------------------------------------------------------------------------
+// shared front half: validation, depth sort, transmittance
+// ---------------------------------------------------------------------------------------
+
+struct Front {
+    SceneTable T;
+    Segs S;
+    long long n_total;
+    unsigned *sorted;  // depth-sorted global indices
+    double *T_sorted;  // null in OIT mode
+    double *T_g;
+};
+
+static gws_status run_front(const gws_gaussians *scenes, const int64_t *n, int n_scenes, const gws_slm *slm,
+                            const gws_opts *o, const Layout &L, bool need_T, Front *F, cudaStream_t s) {
+    SceneTable &T = F->T;
+    std::memset(&T, 0, sizeof T);
+    T.n_scenes = n_scenes;
+    T.n_lambda = slm ? slm->n_lambda : 1;
+    T.off[0] = 0;
+    for (int k = 0; k < n_scenes; ++k) {
+        T.off[k + 1] = T.off[k] + n[k];
+        T.mean[k] = scenes[k].mean;
+        T.quat[k] = scenes[k].quat;
+        T.scale[k] = scenes[k].scale;
+        T.opacity[k] = scenes[k].opacity;
+        T.amp[k] = scenes[k].amp;
+    }
+    F->S.n_scenes = n_scenes;
+    F->S.n_lambda = T.n_lambda;
+    std::memcpy(F->S.off, T.off, sizeof(T.off));
+    F->n_total = T.off[n_scenes];
+    const long long nt = F->n_total;
+    GPre *gp = at<GPre>(o, L.gpre);
+    unsigned long long *dk0 = at<unsigned long long>(o, L.dkey0), *dk1 = at<unsigned long long>(o, L.dkey1);
+    unsigned *dv0 = at<unsigned>(o, L.dval0), *dv1 = at<unsigned>(o, L.dval1);
+    CU(launch_prep(T, nt, gp, at<float>(o, L.ampc), dk0, dv0, at<int>(o, L.status), s));
+    unsigned *hist = at<unsigned>(o, L.hist);
+    CU(radix_sort<unsigned long long>(dk0, dk1, dv0, dv1, nt, 0, 64, hist, s));
+    if (n_scenes > 1) {
+        unsigned *sk0 = at<unsigned>(o, L.skey0), *sk1 = at<unsigned>(o, L.skey1);
+        CU(launch_scene_key(gp, dv0, nt, sk0, s));
+        CU(radix_sort<unsigned>(sk0, sk1, dv0, dv1, nt, 0, 8, hist, s));
+    }
+    F->sorted = dv0;
+    F->T_sorted = nullptr;
+    F->T_g = nullptr;
+    if (need_T) {
+        F->T_sorted = at<double>(o, L.tsorted);
+        F->T_g = at<double>(o, L.tg);
+        CU(launch_transmittance(gp, dv0, F->S, nt, (double)o->alpha_min, at<TData>(o, L.tdata), F->T_sorted, F->T_g,
+                                s));
+    }
+    return GWS_OK;
+}
+
+static FootParams foot_params(const gws_slm *slm, const gws_opts *o) {
+    FootParams F;
+    std::memset(&F, 0, sizeof F);
+    F.rho = (float)std::sqrt(std::log(1.0 / (double)o->trunc_eps) / (2.0 * kPi * kPi));
+    for (int l = 0; l < slm->n_lambda; ++l) F.dzmax[l] = (float)(dz_max(slm, slm->wavelengths[l]) * 1.0001);
+    return F;
+}
+
+static int seg_bits(int n_seg) {
+    int b = 0;
+    while ((1 << b) < n_seg) ++b;
+    return ((b + 7) / 8) * 8;
+}
+
+// records in decreasing-footprint order per segment; returns the record array
+static gws_status run_records(const Front &F, const gws_slm *slm, const gws_opts *o, const Layout &L, int backward,
+                              cudaStream_t s, Rec **rec_out) {
+    const long long n_rec = F.n_total * slm->n_lambda;
+    const FootParams FP = foot_params(slm, o);
+    GPre *gp = at<GPre>(o, L.gpre);
+    unsigned long long *k0 = at<unsigned long long>(o, L.fkey0), *k1 = at<unsigned long long>(o, L.fkey1);
+    unsigned *v0 = at<unsigned>(o, L.fval0), *v1 = at<unsigned>(o, L.fval1);
+    const int drop = backward ? 0 : 1;
+    CU(launch_foot_keys(gp, at<float>(o, L.ampc), F.sorted, F.T_sorted, F.S, n_rec, FP, drop, k0, v0, s));
+    const int n_seg = F.S.n_scenes * F.S.n_lambda;
+    CU(radix_sort<unsigned long long>(k0, k1, v0, v1, n_rec, 0, 32 + seg_bits(n_seg), at<unsigned>(o, L.hist), s));
+    Rec *rec = at<Rec>(o, L.rec);
+    CU(launch_gather(k0, v0, gp, at<float>(o, L.ampc), F.sorted, F.T_sorted, F.S, n_rec, FP, drop, backward, rec,
+                     at<float>(o, L.Rr), s));
+    *rec_out = rec;
+    return GWS_OK;
+}
+
+static int num_sms() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, int n_scenes, const gws_slm *slm,
+                               const gws_opts *o, void *const *out) {
+    t_launches = 0;
+    GS(check_slm(slm));
+    GS(check_opts(o));
+    if (n_scenes < 1 || n_scenes > GWS_MAX_SCENES || !n || !out) return GWS_ERR_INVALID_ARG;
+    long long n_total = 0;
+    for (int k = 0; k < n_scenes; ++k) {
+        GS(check_gaussians(&scenes[k], n[k]));
+        if (!out[k]) return GWS_ERR_INVALID_ARG;
+        n_total += n[k];
+    }
+    if (n_total > (1ll << 30)) return GWS_ERR_INVALID_ARG;
+    const bool fft = o->domain == GWS_DOMAIN_FIELD;
+    Layout L;
+    GS(plan_layout(n_total, n_scenes, slm, o, &L, fft));
+    GS(check_workspace(o, L));
+    cudaStream_t s = (cudaStream_t)o->stream;
+    timers_reset(o);
+    timer_mark(o, GWS_TIMER_TOTAL, 0, s);
+    const int nl = slm->n_lambda, H = slm->H, W = slm->W;
+    const bool dbl = o->prec == GWS_PREC_FP64;
+    const size_t slice = (size_t)H * W * (dbl ? 16 : 8);
+    CU(cudaMemsetAsync(at<char>(o, L.status), 0, 16, s));
+    if (n_total == 0) {
+        for (int k = 0; k < n_scenes; ++k) CU(cudaMemsetAsync(out[k], 0, slice * nl, s));
+        return GWS_OK;
+    }
+    Front F;
+    GS(run_front(scenes, n, n_scenes, slm, o, L, o->blend == GWS_BLEND_SORTED_T, &F, s));
+    const double dfx = 1.0 / (W * slm->pitch_x), dfy = 1.0 / (H * slm->pitch_y);
+    if (dbl) {
+        Rec64 *r64 = at<Rec64>(o, L.rec64);
+        double *w64 = at<double>(o, L.w64);
+        CU(launch_rec64(at<GPre>(o, L.gpre), at<float>(o, L.ampc), F.sorted, F.T_sorted, n_total, nl, r64, w64, s));
+        Splat64Args a;
+        std::memset(&a, 0, sizeof a);
+        a.rec = r64;
+        a.w = w64;
+        a.segs = F.S;
+        a.H = H;
+        a.W = W;
+        a.dfx = dfx;
+        a.dfy = dfy;
+        for (int l = 0; l < nl; ++l) a.inv_lam[l] = 1.0 / slm->wavelengths[l];
+        a.field_mode = fft ? 1 : 0;
+        a.phase_match = o->phase_match ? 1 : 0;
+        for (int k = 0; k < n_scenes; ++k) a.out[k] = out[k];
+        timer_mark(o, GWS_TIMER_SPLAT_FWD, 0, s);
+        CU(launch_splat_fp64(a, s));
+        timer_mark(o, GWS_TIMER_SPLAT_FWD, 1, s);
+    } else {
+        Rec *rec = nullptr;
+        GS(run_records(F, slm, o, L, 0, s, &rec));
+        const int n_seg = n_scenes * nl;
+        const TileCfg tc = tile_cfg(L.cfg);
+        unsigned *ik0 = at<unsigned>(o, L.ikey0), *ik1 = at<unsigned>(o, L.ikey1);
+        unsigned *iv0 = at<unsigned>(o, L.ival0), *iv1 = at<unsigned>(o, L.ival1);
+        int *icount = at<int>(o, L.icount);
+        CU(launch_items(at<float>(o, L.Rr), F.S, n_seg, H, W, tc.tw, tc.th, L.tiles_x, L.n_tiles, dfx, dfy, ik0, iv0,
+                        icount, s));
+        const long long n_items = (long long)n_seg * L.n_tiles;
+        CU(radix_sort<unsigned>(ik0, ik1, iv0, iv1, n_items, 0, 32, at<unsigned>(o, L.hist), s));
+        CU(cudaMemsetAsync(at<int>(o, L.queue), 0, 16, s));
+        SplatArgs a;
+        std::memset(&a, 0, sizeof a);
+        a.rec = rec;
+        a.items = iv0;
+        a.item_count = icount;
+        a.n_items = (int)n_items;
+        a.queue = at<int>(o, L.queue);
+        a.status = at<int>(o, L.status);
+        a.segs = F.S;
+        a.H = H;
+        a.W = W;
+        a.tiles_x = L.tiles_x;
+        a.n_tiles = L.n_tiles;
+        a.dfx = dfx;
+        a.dfy = dfy;
+        for (int l = 0; l < nl; ++l) a.inv_lam[l] = 1.0 / slm->wavelengths[l];
+        a.field_mode = fft ? 1 : 0;
+        a.phase_match = o->phase_match ? 1 : 0;
+        a.timeout = o->timeout_cycles;
+        a.debug = o->debug_flags;
+        for (int k = 0; k < n_scenes; ++k) a.out[k] = out[k];
+        const int grid = (int)std::min<long long>(n_items, (long long)num_sms() * splat_mixed_ctas_per_sm(L.cfg));
+        timer_mark(o, GWS_TIMER_SPLAT_FWD, 0, s);
+        CU(launch_splat_mixed(L.cfg, a, grid, s));
+        timer_mark(o, GWS_TIMER_SPLAT_FWD, 1, s);
+    }
+    if (fft) {
+        Plan p;
+        GS(get_plan(H, W, nl, dbl, &p));
+        timer_mark(o, GWS_TIMER_FFT, 0, s);
+        for (int k = 0; k < n_scenes; ++k) {
+            GS(exec_fft(p, out[k], at<char>(o, L.cufft), dbl, CUFFT_INVERSE, s));
+            CU(launch_modulate(out[k], dbl, nl, H, W, dfx * dfy, 0, s));
+        }
+        timer_mark(o, GWS_TIMER_FFT, 1, s);
+    }
+    timer_mark(o, GWS_TIMER_TOTAL, 1, s);
+    return GWS_OK;
+}
+
+}  // namespace gws
+
+using namespace gws;
+
+extern "C" {
+
+void gws_opts_default(gws_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->blend = GWS_BLEND_OIT;
+    o->prec = GWS_PREC_MIXED;
+    o->domain = GWS_DOMAIN_FIELD;
+    o->phase_match = 0;
+    o->trunc_eps = 1e-5f;
+    o->alpha_min = 1.0f / 255.0f;
+    o->tile_cfg = 0;
+    o->debug_flags = 0;
+    o->timeout_cycles = 2000000000ull;
+}
+
+const char *gws_status_string(gws_status s) {
+    switch (s) {
+        case GWS_OK: return "GWS_OK";
+        case GWS_ERR_INVALID_ARG: return "GWS_ERR_INVALID_ARG";
+        case GWS_ERR_WORKSPACE: return "GWS_ERR_WORKSPACE";
+        case GWS_ERR_CUDA: return "GWS_ERR_CUDA";
+        case GWS_ERR_NONFINITE: return "GWS_ERR_NONFINITE";
+        case GWS_ERR_TIMEOUT: return "GWS_ERR_TIMEOUT";
+        case GWS_ERR_UNSUPPORTED: return "GWS_ERR_UNSUPPORTED";
+    }
+    return "GWS_ERR_UNKNOWN";
+}
+
+int gws_version(void) { return GWS_ABI_VERSION; }
+
+int gws_last_launch_count(void) { return t_launches; }
+
+gws_status gws_workspace_size(const int64_t *n, int n_scenes, const gws_slm *slm, const gws_opts *opts,
+                              size_t *bytes) {
+    if (!bytes || !n || n_scenes < 1 || n_scenes > GWS_MAX_SCENES) return GWS_ERR_INVALID_ARG;
+    GS(check_slm(slm));
+    GS(check_opts(opts));
+    long long tot = 0;
+    for (int k = 0; k < n_scenes; ++k) {
+        if (n[k] < 0) return GWS_ERR_INVALID_ARG;
+        tot += n[k];
+    }
+    if (tot > (1ll << 30)) return GWS_ERR_INVALID_ARG;
+    Layout L;
+    GS(plan_layout(tot, n_scenes, slm, opts, &L, opts->domain == GWS_DOMAIN_FIELD));
+    *bytes = L.total;
+    return GWS_OK;
+}
+
+gws_status gws_prepare(const gws_slm *slm, const gws_opts *opts, int n_scenes) {
+    GS(check_slm(slm));
+    GS(check_opts(opts));
+    if (n_scenes < 1 || n_scenes > GWS_MAX_SCENES) return GWS_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return GWS_ERR_CUDA;
+    Plan p;
+    return get_plan(slm->H, slm->W, slm->n_lambda, opts->prec == GWS_PREC_FP64, &p);
+}
+
+gws_status gws_forward(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts, void *field_out) {
+    gws_gaussians empty;
+    std::memset(&empty, 0, sizeof empty);
+    void *outs[1] = {field_out};
+    int64_t ns[1] = {n};
+    return forward_impl(g ? g : &empty, ns, 1, slm, opts, outs);
+}
+
+gws_status gws_forward_batched(const gws_gaussians *scenes, const int64_t *n, int n_scenes, const gws_slm *slm,
+                               const gws_opts *opts, void *const *field_out) {
+    if (!scenes) return GWS_ERR_INVALID_ARG;
+    return forward_impl(scenes, n, n_scenes, slm, opts, field_out);
+}
+
+gws_status gws_encode(const void *field, const gws_slm *slm, const gws_opts *opts, float *phase_out,
+                      float amp_scale) {
+    t_launches = 0;
+    GS(check_slm(slm));
+    GS(check_opts(opts));
+    if (!field || !phase_out || !std::isfinite(amp_scale)) return GWS_ERR_INVALID_ARG;
+    Layout L;
+    GS(plan_layout(0, 1, slm, opts, &L, false));
+    if (amp_scale <= 0.f) {
+        if (!opts->workspace || (((uintptr_t)opts->workspace) & 255u) || opts->workspace_bytes < L.amax + 8 * GWS_MAX_LAMBDA)
+            return GWS_ERR_WORKSPACE;
+    }
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    unsigned long long *amax = opts->workspace ? at<unsigned long long>(opts, L.amax) : nullptr;
+    timers_reset(opts);
+    timer_mark(opts, GWS_TIMER_ENCODE, 0, s);
+    CU(launch_encode(field, opts->prec == GWS_PREC_FP64, slm->n_lambda, slm->H, slm->W, amax, (double)amp_scale,
+                     phase_out, s));
+    timer_mark(opts, GWS_TIMER_ENCODE, 1, s);
+    return GWS_OK;
+}
+
+gws_status gws_get_device_status(const gws_opts *opts) {
+    if (!opts || !opts->workspace) return GWS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    int h = 0;
+    CU(cudaMemcpyAsync(&h, opts->workspace, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    CU(cudaMemsetAsync(opts->workspace, 0, sizeof(int), s));
+    if (h & ST_NONFINITE) return GWS_ERR_NONFINITE;
+    if (h & ST_TIMEOUT) return GWS_ERR_TIMEOUT;
+    if (h & ST_BADVALUE) return GWS_ERR_INVALID_ARG;
+    return GWS_OK;
+}
+
+gws_status gws_depth_order(const gws_gaussians *g, int64_t n, const gws_opts *opts, int32_t *order_out) {
+    t_launches = 0;
+    GS(check_opts(opts));
+    GS(check_gaussians(g, n));
+    if (n > 0 && !order_out) return GWS_ERR_INVALID_ARG;
+    double lam = 5e-7;
+    gws_slm slm{1, 1, 1e-6, 1e-6, 1, &lam};
+    Layout L;
+    GS(plan_layout(n, 1, &slm, opts, &L, false));
+    GS(check_workspace(opts, L));
+    if (n == 0) return GWS_OK;
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    CU(cudaMemsetAsync(at<char>(opts, L.status), 0, 16, s));
+    Front F;
+    int64_t ns[1] = {n};
+    // amplitudes are read with n_lambda = 1: only amp[i][0] is touched
+    GS(run_front(g, ns, 1, &slm, opts, L, false, &F, s));
+    CU(cudaMemcpyAsync(order_out, F.sorted, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    return GWS_OK;
+}
+
+gws_status gws_transmittance(const gws_gaussians *g, int64_t n, const gws_opts *opts, double *T_out) {
+    t_launches = 0;
+    GS(check_opts(opts));
+    GS(check_gaussians(g, n));
+    if (n > 0 && !T_out) return GWS_ERR_INVALID_ARG;
+    double lam = 5e-7;
+    gws_slm slm{1, 1, 1e-6, 1e-6, 1, &lam};
+    Layout L;
+    GS(plan_layout(n, 1, &slm, opts, &L, false));
+    GS(check_workspace(opts, L));
+    if (n == 0) return GWS_OK;
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    CU(cudaMemsetAsync(at<char>(opts, L.status), 0, 16, s));
+    Front F;
+    int64_t ns[1] = {n};
+    GS(run_front(g, ns, 1, &slm, opts, L, true, &F, s));
+    CU(cudaMemcpyAsync(T_out, F.T_g, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    return GWS_OK;
+}
+
+gws_status gws_footprints(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts, int l,
+                          float *ellipse_out) {
+    t_launches = 0;
+    GS(check_slm(slm));
+    GS(check_opts(opts));
+    GS(check_gaussians(g, n));
+    if (l < 0 || l >= slm->n_lambda || (n > 0 && !ellipse_out)) return GWS_ERR_INVALID_ARG;
+    Layout L;
+    GS(plan_layout(n, 1, slm, opts, &L, false));
+    GS(check_workspace(opts, L));
+    if (n == 0) return GWS_OK;
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    CU(cudaMemsetAsync(at<char>(opts, L.status), 0, 16, s));
+    SceneTable T;
+    std::memset(&T, 0, sizeof T);
+    T.n_scenes = 1;
+    T.n_lambda = slm->n_lambda;
+    T.off[1] = n;
+    T.mean[0] = g->mean;
+    T.quat[0] = g->quat;
+    T.scale[0] = g->scale;
+    T.opacity[0] = g->opacity;
+    T.amp[0] = g->amp;
+    GPre *gp = at<GPre>(opts, L.gpre);
+    CU(launch_prep(T, n, gp, at<float>(opts, L.ampc), at<unsigned long long>(opts, L.dkey0),
+                   at<unsigned>(opts, L.dval0), at<int>(opts, L.status), s));
+    const FootParams FP = foot_params(slm, opts);
+    CU(launch_foot_inspect(gp, n, FP.rho, FP.dzmax[l], ellipse_out, s));
+    return GWS_OK;
+}
+
+float gws_kernel_time_ms(int which) {
+    if (which < 0 || which > 4 || !t_timers.made || !t_timers.used[which]) return -1.f;
+    if (cudaEventSynchronize(t_timers.ev[which][1]) != cudaSuccess) return -1.f;
+    float ms = -1.f;
+    if (cudaEventElapsedTime(&ms, t_timers.ev[which][0], t_timers.ev[which][1]) != cudaSuccess) return -1.f;
+    return ms;
+}
+
+gws_status gws_footprint_pairs(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
+                               unsigned long long *pairs) {
+    t_launches = 0;
+    GS(check_slm(slm));
+    GS(check_opts(opts));
+    GS(check_gaussians(g, n));
+    if (!pairs) return GWS_ERR_INVALID_ARG;
+    *pairs = 0;
+    Layout L;
+    GS(plan_layout(n, 1, slm, opts, &L, false));
+    GS(check_workspace(opts, L));
+    if (n == 0) return GWS_OK;
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    CU(cudaMemsetAsync(at<char>(opts, L.status), 0, 16, s));
+    SceneTable T;
+    std::memset(&T, 0, sizeof T);
+    T.n_scenes = 1;
+    T.n_lambda = slm->n_lambda;
+    T.off[1] = n;
+    T.mean[0] = g->mean;
+    T.quat[0] = g->quat;
+    T.scale[0] = g->scale;
+    T.opacity[0] = g->opacity;
+    T.amp[0] = g->amp;
+    GPre *gp = at<GPre>(opts, L.gpre);
+    CU(launch_prep(T, n, gp, at<float>(opts, L.ampc), at<unsigned long long>(opts, L.dkey0),
+                   at<unsigned>(opts, L.dval0), at<int>(opts, L.status), s));
+    const FootParams FP = foot_params(slm, opts);
+    unsigned long long *acc = at<unsigned long long>(opts, L.queue);
+    CU(cudaMemsetAsync(acc, 0, 8, s));
+    CU(launch_count_pairs(gp, n, slm->n_lambda, FP, slm->H, slm->W, 1.0 / (slm->W * slm->pitch_x),
+                          1.0 / (slm->H * slm->pitch_y), acc, s));
+    CU(cudaMemcpyAsync(pairs, acc, 8, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return GWS_OK;
+}
+
+gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
+                        const void *grad_field, gws_gaussians_grad *out) {
+    (void)g;
+    (void)n;
+    (void)slm;
+    (void)grad_field;
+    (void)out;
+    GS(check_opts(opts));
+    return GWS_ERR_UNSUPPORTED;
+}
+
+gws_status gws_autotune(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
+                        void *field_scratch, int *best_cfg) {
+    (void)g;
+    (void)n;
+    (void)slm;
+    (void)field_scratch;
+    if (!best_cfg) return GWS_ERR_INVALID_ARG;
+    GS(check_opts(opts));
+    *best_cfg = 1;
+    return GWS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// gws_common.cuh -- internal types and device helpers of libgws (sm_103a).
+//
+// Notation follows the paper (arXiv 2505.06582): a Gaussian has mean mu, rotation
+// columns r1 (t_u), r2 (t_v), r3 (normal), scales s_u, s_v, opacity o and amplitude c per
+// wavelength (Sec. 3).  Its spectrum at the SLM is Eq. 10 with the reference-wave shift
+// (Sec. 4.1); spectra are summed by Eq. 12 (or Eq. 5-6 with T at the centre).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gws.h"
+
+namespace gws {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 6.28318530717958647692;
+// exp(-2 pi^2 x) = 2^(-x * 2 pi^2 / ln 2): kappa = pi * sqrt(2 / ln 2) folds the 2 pi^2 and
+// the base change into the scaled rotation columns, so the per-pair exponent is an ex2.
+constexpr double kKappa = 5.336446256636997;  // pi * sqrt(2 / ln 2)
+
+// Device status bits (a word in the workspace; the host maps them to gws_status).
+enum : int {
+    ST_NONFINITE = 1,
+    ST_BADVALUE = 2,
+    ST_TIMEOUT = 4,
+};
+
+// Per-Gaussian data after validation (concatenated over scenes, input order).
+struct alignas(16) GPre {
+    double mu[3];
+    double q[4];  // normalised quaternion (w, x, y, z)
+    float su, sv, o;
+    int scene;
+};
+
+// One Gaussian's record for one wavelength, as the splat kernels stream it (96 bytes, a
+// multiple of 16 so that 1-D bulk copies of whole chunks stay 16-byte aligned).
+//   r1' = kappa s_u r1, r2' = kappa s_v r2 (so that 2^-(a'^2 + b'^2) is the Gaussian factor),
+//   r3' = W r3 (forward) or r3 (backward), W = 2 pi s_u s_v c o T (Eq. 10 amplitude x Eq. 12 weight),
+//   m = -mu in FP32 for the in-tile phase deltas, mu in FP64 for the per-tile phase anchor,
+//   e = footprint ellipse normalised to 1.
+struct alignas(16) Rec {
+    float r1x, r1y, r1z, r2x;
+    float r2y, r2z, r3x, r3y;
+    float r3z, mx, my, mz;
+    float e00, e01, e11, W;
+    double mux, muy;
+    double muz;
+    int g;  // global (concatenated) Gaussian index
+    int pad;
+};
+static_assert(sizeof(Rec) == 96, "record must stay 96 bytes");
+
+// Per depth-sorted Gaussian data of the transmittance pass (FP64 like the oracle).
+struct alignas(16) TData {
+    double mx, my;
+    double m00, m01, m10, m11, det;
+    float o;
+    float bx0, bx1, by0, by1;  // box outside which alpha < alpha_min
+    float pad;
+};
+
+// FP64 path record (per depth-sorted Gaussian).
+struct alignas(16) Rec64 {
+    double r1[3], r2[3], r3[3];
+    double mu[3];
+    double su, sv;
+};
+
+struct SceneTable {
+    int n_scenes;
+    int n_lambda;
+    long long off[GWS_MAX_SCENES + 1];
+    const double *mean[GWS_MAX_SCENES];
+    const float *quat[GWS_MAX_SCENES];
+    const float *scale[GWS_MAX_SCENES];
+    const float *opacity[GWS_MAX_SCENES];
+    const float *amp[GWS_MAX_SCENES];
+};
+
+struct Grid {
+    int H, W;
+    double px, py;
+    int n_lambda;
+    double lam[GWS_MAX_LAMBDA];
+};
+
+// ---------------------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------------------
+
+__device__ __forceinline__ int scene_of(const long long *off, int n_scenes, long long g) {
+    int lo = 0, hi = n_scenes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Rotation columns of a normalised quaternion (w, x, y, z).
+template <typename T>
+__device__ __forceinline__ void quat_cols(const T q[4], T r1[3], T r2[3], T r3[3]) {
+    T w = q[0], x = q[1], y = q[2], z = q[3];
+    r1[0] = T(1) - T(2) * (y * y + z * z);
+    r1[1] = T(2) * (x * y + w * z);
+    r1[2] = T(2) * (x * z - w * y);
+    r2[0] = T(2) * (x * y - w * z);
+    r2[1] = T(1) - T(2) * (x * x + z * z);
+    r2[2] = T(2) * (y * z + w * x);
+    r3[0] = T(2) * (x * z + w * y);
+    r3[1] = T(2) * (y * z - w * x);
+    r3[2] = T(1) - T(2) * (x * x + y * y);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sin_approx(float x) {
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ---- mbarrier + 1-D bulk copy (TMA engine) -------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: returns false if the phase did not complete within `limit` cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned long long limit) {
+    if (mbar_try_wait(bar, parity)) return true;
+    unsigned long long t0 = clock64();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+// global -> shared bulk copy, completion counted on `bar` (bytes multiple of 16, both
+// addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_g2s(void *smem_dst, const void *gmem_src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(smem_dst)),
+        "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Centred-DFT modulation angle, in cycles: ((a * b) mod n) / n, exact integer reduction.
+__device__ __forceinline__ double mod_frac(long long a, long long b, long long n) {
+    long long m = (a * b) % n;
+    if (m < 0) m += n;
+    return (double)m / (double)n;
+}
+
+}  // namespace gws

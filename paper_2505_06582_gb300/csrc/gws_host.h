@@ -1,0 +1,101 @@
+// gws_host.h -- internal host-side declarations shared by the libgws translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "gws_common.cuh"
+
+namespace gws {
+
+// kernel-launch counter (gws_last_launch_count)
+void count_launches(int k);
+
+size_t sort_hist_words(long long n);
+
+template <typename K>
+cudaError_t radix_sort(K *&keys, K *&keys_alt, unsigned *&vals, unsigned *&vals_alt, long long n, int begin_bit,
+                       int end_bit, unsigned *hist, cudaStream_t s);
+
+// ---- splat (forward) --------------------------------------------------------------------
+
+struct Segs {
+    int n_scenes;
+    int n_lambda;
+    long long off[GWS_MAX_SCENES + 1];  // Gaussian offsets of the scenes (concatenated)
+};
+
+// record range of segment (scene s, wavelength l): [L off[s] + l N_s, + N_s)
+__host__ __device__ inline long long seg_start(const Segs &S, int seg) {
+    int s = seg / S.n_lambda, l = seg % S.n_lambda;
+    long long ns = S.off[s + 1] - S.off[s];
+    return (long long)S.n_lambda * S.off[s] + (long long)l * ns;
+}
+__host__ __device__ inline long long seg_size(const Segs &S, int seg) {
+    int s = seg / S.n_lambda;
+    return S.off[s + 1] - S.off[s];
+}
+
+struct TileCfg {
+    int id, tw, th;
+};
+int n_tile_cfgs();
+TileCfg tile_cfg(int id);  // id 1..n_tile_cfgs()
+
+struct SplatArgs {
+    const Rec *rec;
+    const unsigned *items;   // item ids in processing order
+    const int *item_count;   // records per item (prefix of the segment's footprint order)
+    int n_items;
+    int *queue;
+    int *status;
+    Segs segs;
+    int H, W, tiles_x, n_tiles;
+    double dfx, dfy;
+    double inv_lam[GWS_MAX_LAMBDA];
+    int field_mode;  // 1: multiply by the centred-DFT pre-modulation
+    int phase_match;
+    unsigned long long timeout;
+    unsigned debug;
+    void *out[GWS_MAX_SCENES];
+};
+
+cudaError_t launch_splat_mixed(int cfg, const SplatArgs &a, int grid, cudaStream_t s);
+int splat_mixed_ctas_per_sm(int cfg);
+
+struct Splat64Args {
+    const Rec64 *rec;
+    const double *w;  // [n][n_lambda], depth-sorted order
+    Segs segs;
+    int H, W;
+    double dfx, dfy;
+    double inv_lam[GWS_MAX_LAMBDA];
+    int field_mode;
+    int phase_match;
+    void *out[GWS_MAX_SCENES];
+};
+cudaError_t launch_splat_fp64(const Splat64Args &a, cudaStream_t s);
+
+// ---- backward ---------------------------------------------------------------------------
+
+struct BwdArgs {
+    const Rec *rec;      // backward records (r3 unit, W separate), segment-major
+    const float2 *gspec; // dL/du_SLM per scene [scene][lambda][H][W] (contiguous, natural layout)
+    double *acc;         // [n_records][13] totals
+    int *queue;
+    int *status;
+    Segs segs;
+    int H, W, tiles_x, tiles_y;
+    double dfx, dfy;
+    double inv_lam[GWS_MAX_LAMBDA];
+    int phase_match;
+    int n_items;        // (segment, block) work items
+    const int *item_seg;
+    const int *item_first;
+    unsigned long long timeout;
+};
+cudaError_t launch_splat_bwd(const BwdArgs &a, int grid, cudaStream_t s);
+int bwd_block_size();
+
+}  // namespace gws

@@ -1,0 +1,620 @@
+// gws_prep.cu -- everything on the hot path except the splats:
+//   validation + per-Gaussian precompute, depth keys (Algorithm S2 order), the
+//   transmittance at each centre (Eq. 2, Eq. 5-6 reading, t_eps of Algorithm S2), FP64
+//   records, spectral footprints + footprint-ordered records (binning), work items,
+//   centred-DFT modulations around cuFFT (Eq. 3 on the grid) and double-phase encoding.
+#include <float.h>
+
+#include <algorithm>
+
+#include "gws_prep.h"
+
+namespace gws {
+
+// ---------------------------------------------------------------------------------------
+// validation, normalised quaternion, depth key
+// ---------------------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long depth_key(double z) {
+    z = z + 0.0;  // -0 == +0: equal depths tie (input order decides)
+    unsigned long long b = (unsigned long long)__double_as_longlong(z);
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__global__ void k_prep(const __grid_constant__ SceneTable T, long long n_total, GPre *__restrict__ gp,
+                       float *__restrict__ ampc, unsigned long long *__restrict__ dkey, unsigned *__restrict__ dval,
+                       int *__restrict__ status) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_total) return;
+    const int s = scene_of(T.off, T.n_scenes, g);
+    const long long i = g - T.off[s];
+    const int L = T.n_lambda;
+    double mu[3] = {T.mean[s][3 * i], T.mean[s][3 * i + 1], T.mean[s][3 * i + 2]};
+    double q[4] = {T.quat[s][4 * i], T.quat[s][4 * i + 1], T.quat[s][4 * i + 2], T.quat[s][4 * i + 3]};
+    float su = T.scale[s][2 * i], sv = T.scale[s][2 * i + 1], o = T.opacity[s][i];
+    int bad = 0;
+    bool fin = isfinite(mu[0]) && isfinite(mu[1]) && isfinite(mu[2]) && isfinite(q[0]) && isfinite(q[1]) &&
+               isfinite(q[2]) && isfinite(q[3]) && isfinite(su) && isfinite(sv) && isfinite(o);
+    for (int l = 0; l < L; ++l) {
+        float c = T.amp[s][i * L + l];
+        fin = fin && isfinite(c);
+        ampc[g * L + l] = c;
+    }
+    const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (!fin) bad |= ST_NONFINITE;
+    else if (!(su > 0.f) || !(sv > 0.f) || !(o >= 0.f && o <= 1.f) || !(qn > 0.0)) bad |= ST_BADVALUE;
+    if (bad) {
+        atomicOr(status, bad);
+        if (!(qn > 0.0) || !isfinite(qn)) {
+            q[0] = 1.0;
+            q[1] = q[2] = q[3] = 0.0;
+        }
+    }
+    GPre r;
+    r.mu[0] = mu[0];
+    r.mu[1] = mu[1];
+    r.mu[2] = mu[2];
+    const double inv = (qn > 0.0 && isfinite(qn)) ? 1.0 / qn : 1.0;
+    for (int k = 0; k < 4; ++k) r.q[k] = (qn > 0.0 && isfinite(qn)) ? q[k] / qn : q[k] * inv;
+    r.su = su;
+    r.sv = sv;
+    r.o = o;
+    r.scene = s;
+    gp[g] = r;
+    dkey[g] = depth_key(mu[2]);
+    dval[g] = (unsigned)g;
+}
+
+// scene id of each depth-sorted entry, for the final (stable) grouping pass
+__global__ void k_scene_key(const GPre *__restrict__ gp, const unsigned *__restrict__ sorted, long long n,
+                            unsigned *__restrict__ skey) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) skey[p] = (unsigned)gp[sorted[p]].scene;
+}
+
+// ---------------------------------------------------------------------------------------
+// transmittance at the centres (depth-sorted)
+// ---------------------------------------------------------------------------------------
+
+__global__ void k_tdata(const GPre *__restrict__ gp, const unsigned *__restrict__ sorted, long long n,
+                        double alpha_min, TData *__restrict__ td) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const GPre &g = gp[sorted[p]];
+    double r1[3], r2[3], r3[3];
+    quat_cols<double>(g.q, r1, r2, r3);
+    TData t;
+    t.mx = g.mu[0];
+    t.my = g.mu[1];
+    t.m00 = (double)g.su * r1[0];
+    t.m01 = (double)g.sv * r2[0];
+    t.m10 = (double)g.su * r1[1];
+    t.m11 = (double)g.sv * r2[1];
+    t.det = t.m00 * t.m11 - t.m01 * t.m10;
+    t.o = g.o;
+    t.pad = 0.f;
+    const bool edge_on = fabs(t.det) < 1e-14 * (double)g.su * (double)g.sv;
+    if (edge_on || !((double)g.o >= alpha_min) || g.o <= 0.f) {
+        t.bx0 = 1.f;
+        t.bx1 = -1.f;
+        t.by0 = 1.f;
+        t.by1 = -1.f;
+    } else {
+        // alpha >= alpha_min  <=>  |M^-1 d|^2 <= 2 ln(o / alpha_min); box of that ellipse
+        const double qmax = 2.0 * log((double)g.o / alpha_min);
+        const double hx = sqrt(fmax(qmax, 0.0) * (t.m00 * t.m00 + t.m01 * t.m01)) * 1.0001 + 1e-12;
+        const double hy = sqrt(fmax(qmax, 0.0) * (t.m10 * t.m10 + t.m11 * t.m11)) * 1.0001 + 1e-12;
+        t.bx0 = __double2float_rd(t.mx - hx);
+        t.bx1 = __double2float_ru(t.mx + hx);
+        t.by0 = __double2float_rd(t.my - hy);
+        t.by1 = __double2float_ru(t.my + hy);
+    }
+    td[p] = t;
+}
+
+constexpr int kTChunk = 128;
+
+// T_p = prod over earlier (front) entries q of the same scene of (1 - alpha_q(mu_p)),
+// alpha below alpha_min dropped.  FP64 like the oracle; boxes cull in FP32 (conservative).
+__global__ void __launch_bounds__(kTChunk) k_transmit(const TData *__restrict__ td, const unsigned *__restrict__ sorted,
+                                                      Segs S, long long n, double alpha_min,
+                                                      double *__restrict__ T_sorted, double *__restrict__ T_g) {
+    __shared__ TData s_td[kTChunk];
+    const long long p = (long long)blockIdx.x * kTChunk + threadIdx.x;
+    const bool active = p < n;
+    const long long pp = active ? p : n - 1;
+    const int sc = scene_of(S.off, S.n_scenes, pp);
+    const long long start = S.off[sc];
+    const double xp = td[pp].mx, yp = td[pp].my;
+    const float xf = (float)xp, yf = (float)yp;
+    // block range of fronts: [min start in block, max p in block)
+    const long long pfirst = (long long)blockIdx.x * kTChunk;
+    const long long plast = min(pfirst + kTChunk, n) - 1;
+    const long long qlo = S.off[scene_of(S.off, S.n_scenes, pfirst)];
+    double T = 1.0;
+    for (long long c0 = qlo; c0 < plast; c0 += kTChunk) {
+        __syncthreads();
+        if (c0 + threadIdx.x < plast) s_td[threadIdx.x] = td[c0 + threadIdx.x];
+        __syncthreads();
+        const long long cend = min((long long)kTChunk, plast - c0);
+        for (int k = 0; k < cend; ++k) {
+            const long long q = c0 + k;
+            if (q < start || q >= pp) continue;
+            const TData &f = s_td[k];
+            if (xf < f.bx0 || xf > f.bx1 || yf < f.by0 || yf > f.by1) continue;
+            const double dx = xp - f.mx, dy = yp - f.my;
+            const double y0 = (f.m11 * dx - f.m01 * dy) / f.det;
+            const double y1 = (-f.m10 * dx + f.m00 * dy) / f.det;
+            const double a = (double)f.o * exp(-0.5 * (y0 * y0 + y1 * y1));
+            if (a >= alpha_min) T *= (1.0 - a);
+        }
+    }
+    if (active) {
+        T_sorted[p] = T;
+        T_g[sorted[p]] = T;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// FP64 path records
+// ---------------------------------------------------------------------------------------
+
+__global__ void k_rec64(const GPre *__restrict__ gp, const float *__restrict__ ampc,
+                        const unsigned *__restrict__ sorted, const double *__restrict__ T_sorted, long long n, int L,
+                        Rec64 *__restrict__ rec, double *__restrict__ w) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const unsigned g = sorted[p];
+    const GPre &G = gp[g];
+    Rec64 r;
+    quat_cols<double>(G.q, r.r1, r.r2, r.r3);
+    r.mu[0] = G.mu[0];
+    r.mu[1] = G.mu[1];
+    r.mu[2] = G.mu[2];
+    r.su = G.su;
+    r.sv = G.sv;
+    rec[p] = r;
+    const double T = T_sorted ? T_sorted[p] : 1.0;
+    for (int l = 0; l < L; ++l) w[p * L + l] = (double)ampc[(size_t)g * L + l] * (double)G.o * T;
+}
+
+// ---------------------------------------------------------------------------------------
+// spectral footprints and footprint-ordered records (the MIXED path's binning)
+// ---------------------------------------------------------------------------------------
+
+struct Foot {
+    float e00, e01, e11, R;
+};
+
+// Frequencies with |M^T f| > rho' have E = 2 pi^2 (s_u^2 a^2 + s_v^2 b^2) > ln(1/eps): with
+// v = (s_u a, s_v b) = M^T f + d_z (s_u r1z, s_v r2z) and |d_z| <= dzmax on the grid,
+// |v| <= rho  implies  |M^T f| <= rho + dzmax |(s_u r1z, s_v r2z)| = rho'.
+// The footprint is the ellipse f^T (M M^T / rho'^2) f <= 1, centred at f = 0 (the
+// reference-wave shift puts every Gaussian's spectral peak at the origin).  R bounds its
+// largest radius.
+__device__ __forceinline__ Foot footprint(const float r1[3], const float r2[3], float su, float sv, float rho,
+                                          float dzmax) {
+    const float m00 = su * r1[0], m01 = sv * r2[0], m10 = su * r1[1], m11 = sv * r2[1];
+    const float a00 = m00 * m00 + m01 * m01, a01 = m00 * m10 + m01 * m11, a11 = m10 * m10 + m11 * m11;
+    float rp = rho + dzmax * sqrtf(su * su * r1[2] * r1[2] + sv * sv * r2[2] * r2[2]);
+    rp *= 1.0005f;
+    const float inv = 1.f / (rp * rp);
+    Foot f;
+    f.e00 = a00 * inv;
+    f.e01 = a01 * inv;
+    f.e11 = a11 * inv;
+    const float det = m00 * m11 - m01 * m10;
+    const float det2 = det * det;
+    const float half = 0.5f * (a00 + a11);
+    const float disc = sqrtf(fmaxf(0.25f * (a00 - a11) * (a00 - a11) + a01 * a01, 0.f));
+    const float lmax = half + disc;
+    const float lmin = lmax > 0.f ? det2 / lmax : 0.f;
+    f.R = (lmin > 1e-30f * lmax && lmin > 0.f) ? 1.002f * rp / sqrtf(lmin) : FLT_MAX;
+    return f;
+}
+
+__device__ __forceinline__ void cols_f32(const double qd[4], float r1[3], float r2[3], float r3[3]) {
+    float q[4] = {(float)qd[0], (float)qd[1], (float)qd[2], (float)qd[3]};
+    quat_cols<float>(q, r1, r2, r3);
+}
+
+// record slot k (segment-major, depth order inside a segment) -> (segment, sorted position)
+__device__ __forceinline__ void slot_decode(const Segs &S, long long k, int &seg, long long &p) {
+    // find scene s with L off[s] <= k < L off[s+1]
+    const int L = S.n_lambda;
+    int lo = 0, hi = S.n_scenes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if ((long long)L * S.off[mid] <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    const long long ns = S.off[lo + 1] - S.off[lo];
+    const long long r = k - (long long)L * S.off[lo];
+    const int l = (int)(r / ns);
+    seg = lo * L + l;
+    p = S.off[lo] + (r - (long long)l * ns);
+}
+
+__device__ __forceinline__ float weight_W(const GPre &G, const float *ampc, unsigned g, int L, int l,
+                                          const double *T_sorted, long long p) {
+    const double T = T_sorted ? T_sorted[p] : 1.0;
+    return (float)(kTwoPi * (double)G.su * (double)G.sv * (double)ampc[(size_t)g * L + l] * (double)G.o * T);
+}
+
+__global__ void k_foot_keys(const GPre *__restrict__ gp, const float *__restrict__ ampc,
+                            const unsigned *__restrict__ sorted, const double *__restrict__ T_sorted, Segs S,
+                            long long n_rec, FootParams F, int drop_zero, unsigned long long *__restrict__ key,
+                            unsigned *__restrict__ val) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_rec) return;
+    int seg;
+    long long p;
+    slot_decode(S, k, seg, p);
+    const int l = seg % S.n_lambda;
+    const unsigned g = sorted[p];
+    const GPre &G = gp[g];
+    float r1[3], r2[3], r3[3];
+    cols_f32(G.q, r1, r2, r3);
+    const Foot f = footprint(r1, r2, G.su, G.sv, F.rho, F.dzmax[l]);
+    const float W = weight_W(G, ampc, g, S.n_lambda, l, T_sorted, p);
+    unsigned rk = 0xFFFFFFFFu - __float_as_uint(f.R);  // decreasing radius
+    if (drop_zero && W == 0.f) rk = 0xFFFFFFFFu;
+    key[k] = ((unsigned long long)seg << 32) | rk;
+    val[k] = (unsigned)p;
+}
+
+__global__ void k_gather(const unsigned long long *__restrict__ key, const unsigned *__restrict__ val,
+                         const GPre *__restrict__ gp, const float *__restrict__ ampc,
+                         const unsigned *__restrict__ sorted, const double *__restrict__ T_sorted, Segs S,
+                         long long n_rec, FootParams F, int drop_zero, int backward, Rec *__restrict__ rec,
+                         float *__restrict__ Rr) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_rec) return;
+    const int seg = (int)(key[k] >> 32);
+    const int l = seg % S.n_lambda;
+    const long long p = val[k];
+    const unsigned g = sorted[p];
+    const GPre &G = gp[g];
+    float r1[3], r2[3], r3[3];
+    cols_f32(G.q, r1, r2, r3);
+    const Foot f = footprint(r1, r2, G.su, G.sv, F.rho, F.dzmax[l]);
+    const float W = weight_W(G, ampc, g, S.n_lambda, l, T_sorted, p);
+    const float ku = (float)(kKappa * (double)G.su), kv = (float)(kKappa * (double)G.sv);
+    const float w3 = backward ? 1.f : W;
+    Rec r;
+    r.r1x = ku * r1[0];
+    r.r1y = ku * r1[1];
+    r.r1z = ku * r1[2];
+    r.r2x = kv * r2[0];
+    r.r2y = kv * r2[1];
+    r.r2z = kv * r2[2];
+    r.r3x = w3 * r3[0];
+    r.r3y = w3 * r3[1];
+    r.r3z = w3 * r3[2];
+    r.mx = (float)(-G.mu[0]);
+    r.my = (float)(-G.mu[1]);
+    r.mz = (float)(-G.mu[2]);
+    r.e00 = f.e00;
+    r.e01 = f.e01;
+    r.e11 = f.e11;
+    r.W = W;
+    r.mux = G.mu[0];
+    r.muy = G.mu[1];
+    r.muz = G.mu[2];
+    r.g = (int)g;
+    r.pad = 0;
+    rec[k] = r;
+    Rr[k] = (drop_zero && W == 0.f) ? -1.f : f.R;
+}
+
+// inspection: footprint ellipse per input Gaussian for wavelength l
+__global__ void k_foot_inspect(const GPre *__restrict__ gp, long long n, float rho, float dzmax,
+                               float *__restrict__ out) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const GPre &G = gp[g];
+    float r1[3], r2[3], r3[3];
+    cols_f32(G.q, r1, r2, r3);
+    const Foot f = footprint(r1, r2, G.su, G.sv, rho, dzmax);
+    out[3 * g] = f.e00;
+    out[3 * g + 1] = f.e01;
+    out[3 * g + 2] = f.e11;
+}
+
+// algorithmic work: grid frequencies inside each (Gaussian, wavelength) footprint ellipse,
+// counted row by row (the ellipse's chord on each row of the grid)
+__global__ void k_count_pairs(const GPre *__restrict__ gp, long long n, int n_lambda, FootParams F, int H, int W,
+                              double dfx, double dfy, unsigned long long *__restrict__ acc) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long cnt = 0;
+    if (t < n * n_lambda) {
+        const long long g = t / n_lambda;
+        const int l = (int)(t % n_lambda);
+        const GPre &G = gp[g];
+        float r1[3], r2[3], r3[3];
+        cols_f32(G.q, r1, r2, r3);
+        const Foot f = footprint(r1, r2, G.su, G.sv, F.rho, F.dzmax[l]);
+        const double e00 = f.e00, e01 = f.e01, e11 = f.e11;
+        for (int r = 0; r < H; ++r) {
+            const double fy = (double)(r - H / 2) * dfy;
+            // e00 fx^2 + 2 e01 fy fx + e11 fy^2 <= 1
+            long long c_lo, c_hi;
+            if (e00 > 0) {
+                const double disc = e01 * e01 * fy * fy - e00 * (e11 * fy * fy - 1.0);
+                if (disc < 0) continue;
+                const double sq = sqrt(disc);
+                const double xa = (-e01 * fy - sq) / e00, xb = (-e01 * fy + sq) / e00;
+                c_lo = (long long)ceil(xa / dfx) + W / 2;
+                c_hi = (long long)floor(xb / dfx) + W / 2;
+            } else {
+                if (e11 * fy * fy > 1.0) continue;
+                c_lo = 0;
+                c_hi = W - 1;
+            }
+            c_lo = c_lo < 0 ? 0 : c_lo;
+            c_hi = c_hi > W - 1 ? W - 1 : c_hi;
+            if (c_hi >= c_lo) cnt += (unsigned long long)(c_hi - c_lo + 1);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(acc, cnt);
+}
+
+// work items: (segment, tile) -> number of leading records whose footprint radius reaches
+// the tile (records are in decreasing-radius order); key orders items by decreasing work
+__global__ void k_items(const float *__restrict__ Rr, Segs S, int n_seg, int H, int W, int tw, int th, int tiles_x,
+                        int n_tiles, double dfx, double dfy, unsigned *__restrict__ ikey,
+                        unsigned *__restrict__ ival, int *__restrict__ icount) {
+    const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= (long long)n_seg * n_tiles) return;
+    const int seg = (int)(it / n_tiles), tile = (int)(it % n_tiles);
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int c_lo = tx * tw, c_hi = min(tx * tw + tw, W) - 1;
+    const int r_lo = ty * th, r_hi = min(ty * th + th, H) - 1;
+    const double x0 = (double)(c_lo - W / 2) * dfx, x1 = (double)(c_hi - W / 2) * dfx;
+    const double y0 = (double)(r_lo - H / 2) * dfy, y1 = (double)(r_hi - H / 2) * dfy;
+    const double nx = fmin(fmax(0.0, x0), x1), ny = fmin(fmax(0.0, y0), y1);
+    const float rt = (float)(sqrt(nx * nx + ny * ny) * (1.0 - 1e-6));
+    const long long base = seg_start(S, seg);
+    long long lo = 0, hi = seg_size(S, seg);  // count of entries with R >= rt (R non-increasing)
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (Rr[base + mid] >= rt) lo = mid + 1;
+        else hi = mid;
+    }
+    icount[it] = (int)lo;
+    ikey[it] = 0xFFFFFFFFu - (unsigned)lo;
+    ival[it] = (unsigned)it;
+}
+
+// ---------------------------------------------------------------------------------------
+// centred inverse DFT around cuFFT:
+//   u[r,c] = dfx dfy e^{j2pi(m0 r0/H + n0 c0/W)} e^{-j2pi(m0 r/H + n0 c/W)}
+//            * IFFT_unnormalised( u_SLM[m,n] e^{-j2pi(m r0/H + n c0/W)} )[r,c],   m0 = r0 = H/2, n0 = c0 = W/2
+// The pre-modulation is fused into the splats; this is the post-modulation, and the
+// adjoint pair used by the backward.
+// ---------------------------------------------------------------------------------------
+
+template <typename R>
+struct Cx;
+template <>
+struct Cx<float> {
+    using T = float2;
+};
+template <>
+struct Cx<double> {
+    using T = double2;
+};
+
+// mode 0: forward post-modulation; 1: backward pre-modulation (conj of the post factor
+// without the constant); 2: backward post-modulation (adjoint of the pre-modulation, with
+// the constant and the scale)
+template <typename R>
+__global__ void k_modulate(typename Cx<R>::T *__restrict__ data, int n_slices, int H, int W, double scale, int mode) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long hw = (long long)H * W;
+    if (idx >= hw * n_slices) return;
+    const long long pix = idx % hw;
+    const int r = (int)(pix / W), c = (int)(pix % W);
+    const int h2 = H / 2, w2 = W / 2;
+    double fr;
+    double sc = 1.0;
+    if (mode == 0) {
+        fr = mod_frac(h2, h2, H) + mod_frac(w2, w2, W) - mod_frac(h2, r, H) - mod_frac(w2, c, W);
+        sc = scale;
+    } else if (mode == 1) {
+        fr = mod_frac(h2, r, H) + mod_frac(w2, c, W);
+    } else {
+        fr = -(mod_frac(h2, h2, H) + mod_frac(w2, w2, W)) + mod_frac(r, h2, H) + mod_frac(c, w2, W);
+        sc = scale;
+    }
+    fr -= rint(fr);
+    typename Cx<R>::T v = data[idx];
+    R sn, cs;
+    if (sizeof(R) == 8) {
+        double s8, c8;
+        sincospi(2.0 * fr, &s8, &c8);
+        sn = (R)s8;
+        cs = (R)c8;
+    } else {
+        float s4, c4;
+        sincospif((float)(2.0 * fr), &s4, &c4);
+        sn = (R)s4;
+        cs = (R)c4;
+    }
+    const R re = (R)sc * (v.x * cs - v.y * sn);
+    const R im = (R)sc * (v.x * sn + v.y * cs);
+    v.x = re;
+    v.y = im;
+    data[idx] = v;
+}
+
+// ---------------------------------------------------------------------------------------
+// double-phase encoding (supplement, phase encoding; the garbled formula read as
+// P1,2 = phi -/+ acos(a))
+// ---------------------------------------------------------------------------------------
+
+template <typename R>
+__global__ void k_amax(const typename Cx<R>::T *__restrict__ f, long long hw, unsigned long long *__restrict__ amax2) {
+    const int l = blockIdx.y;
+    R m = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < hw; i += (long long)gridDim.x * blockDim.x) {
+        const typename Cx<R>::T v = f[(size_t)l * hw + i];
+        const R a = v.x * v.x + v.y * v.y;
+        m = a > m ? a : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        R t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        unsigned long long bits =
+            sizeof(R) == 8 ? (unsigned long long)__double_as_longlong((double)m) : (unsigned long long)__float_as_uint((float)m);
+        atomicMax(&amax2[l], bits);
+    }
+}
+
+template <typename R>
+__global__ void k_dpac(const typename Cx<R>::T *__restrict__ f, int n_lambda, int H, int W,
+                       const unsigned long long *__restrict__ amax2, double amp_scale, float *__restrict__ out) {
+    const long long hw = (long long)H * W;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= hw * n_lambda) return;
+    const int l = (int)(idx / hw);
+    const long long pix = idx % hw;
+    const int r = (int)(pix / W), c = (int)(pix % W);
+    R m2max;
+    if (amp_scale > 0) m2max = (R)(amp_scale * amp_scale);
+    else if (sizeof(R) == 8) m2max = (R)__longlong_as_double((long long)amax2[l]);
+    else m2max = (R)__uint_as_float((unsigned)amax2[l]);
+    const typename Cx<R>::T v = f[idx];
+    const R m2 = v.x * v.x + v.y * v.y;
+    R a = m2max > 0 ? sqrt(m2 / m2max) : (R)0;
+    a = a > (R)1 ? (R)1 : a;
+    const R phi = atan2(v.y, v.x);
+    const R ac = acos(a);
+    R p = ((r + c) & 1) == 0 ? phi - ac : phi + ac;
+    const R pi = (R)kPi, tpi = (R)kTwoPi;
+    p = p - tpi * floor((p + pi) / tpi);
+    if (p < -pi) p += tpi;
+    if (p >= pi) p -= tpi;
+    out[idx] = (float)p;
+}
+
+// ---------------------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------------------
+
+static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t launch_prep(const SceneTable &T, long long n_total, GPre *gp, float *ampc, unsigned long long *dkey,
+                        unsigned *dval, int *status, cudaStream_t s) {
+    if (n_total <= 0) return cudaSuccess;
+    k_prep<<<nblk(n_total, 256), 256, 0, s>>>(T, n_total, gp, ampc, dkey, dval, status);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scene_key(const GPre *gp, const unsigned *sorted, long long n, unsigned *skey, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_scene_key<<<nblk(n, 256), 256, 0, s>>>(gp, sorted, n, skey);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transmittance(const GPre *gp, const unsigned *sorted, const Segs &S, long long n, double alpha_min,
+                                 TData *td, double *T_sorted, double *T_g, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_tdata<<<nblk(n, 256), 256, 0, s>>>(gp, sorted, n, alpha_min, td);
+    k_transmit<<<nblk(n, kTChunk), kTChunk, 0, s>>>(td, sorted, S, n, alpha_min, T_sorted, T_g);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rec64(const GPre *gp, const float *ampc, const unsigned *sorted, const double *T_sorted, long long n,
+                         int L, Rec64 *rec, double *w, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_rec64<<<nblk(n, 256), 256, 0, s>>>(gp, ampc, sorted, T_sorted, n, L, rec, w);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_foot_keys(const GPre *gp, const float *ampc, const unsigned *sorted, const double *T_sorted,
+                             const Segs &S, long long n_rec, const FootParams &F, int drop_zero,
+                             unsigned long long *key, unsigned *val, cudaStream_t s) {
+    if (n_rec <= 0) return cudaSuccess;
+    k_foot_keys<<<nblk(n_rec, 256), 256, 0, s>>>(gp, ampc, sorted, T_sorted, S, n_rec, F, drop_zero, key, val);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const unsigned long long *key, const unsigned *val, const GPre *gp, const float *ampc,
+                          const unsigned *sorted, const double *T_sorted, const Segs &S, long long n_rec,
+                          const FootParams &F, int drop_zero, int backward, Rec *rec, float *Rr, cudaStream_t s) {
+    if (n_rec <= 0) return cudaSuccess;
+    k_gather<<<nblk(n_rec, 256), 256, 0, s>>>(key, val, gp, ampc, sorted, T_sorted, S, n_rec, F, drop_zero, backward,
+                                               rec, Rr);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_foot_inspect(const GPre *gp, long long n, float rho, float dzmax, float *out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_foot_inspect<<<nblk(n, 256), 256, 0, s>>>(gp, n, rho, dzmax, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_items(const float *Rr, const Segs &S, int n_seg, int H, int W, int tw, int th, int tiles_x,
+                         int n_tiles, double dfx, double dfy, unsigned *ikey, unsigned *ival, int *icount,
+                         cudaStream_t s) {
+    const long long n = (long long)n_seg * n_tiles;
+    k_items<<<nblk(n, 256), 256, 0, s>>>(Rr, S, n_seg, H, W, tw, th, tiles_x, n_tiles, dfx, dfy, ikey, ival, icount);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_pairs(const GPre *gp, long long n, int n_lambda, const FootParams &F, int H, int W,
+                               double dfx, double dfy, unsigned long long *acc, cudaStream_t s) {
+    const long long t = n * n_lambda;
+    if (t <= 0) return cudaSuccess;
+    k_count_pairs<<<nblk(t, 256), 256, 0, s>>>(gp, n, n_lambda, F, H, W, dfx, dfy, acc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_modulate(void *data, int prec64, int n_slices, int H, int W, double scale, int mode,
+                            cudaStream_t s) {
+    const long long n = (long long)n_slices * H * W;
+    if (n <= 0) return cudaSuccess;
+    if (prec64)
+        k_modulate<double><<<nblk(n, 256), 256, 0, s>>>((double2 *)data, n_slices, H, W, scale, mode);
+    else
+        k_modulate<float><<<nblk(n, 256), 256, 0, s>>>((float2 *)data, n_slices, H, W, scale, mode);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode(const void *field, int prec64, int n_lambda, int H, int W, unsigned long long *amax2,
+                          double amp_scale, float *out, cudaStream_t s) {
+    const long long hw = (long long)H * W;
+    if (amp_scale <= 0) {
+        cudaError_t e = cudaMemsetAsync(amax2, 0, sizeof(unsigned long long) * n_lambda, s);
+        if (e != cudaSuccess) return e;
+        const unsigned gx = (unsigned)std::min<long long>(nblk(hw, 256), 1024);
+        if (prec64)
+            k_amax<double><<<dim3(gx, n_lambda), 256, 0, s>>>((const double2 *)field, hw, amax2);
+        else
+            k_amax<float><<<dim3(gx, n_lambda), 256, 0, s>>>((const float2 *)field, hw, amax2);
+        count_launches(1);
+    }
+    const long long n = hw * n_lambda;
+    if (prec64)
+        k_dpac<double><<<nblk(n, 256), 256, 0, s>>>((const double2 *)field, n_lambda, H, W, amax2, amp_scale, out);
+    else
+        k_dpac<float><<<nblk(n, 256), 256, 0, s>>>((const float2 *)field, n_lambda, H, W, amax2, amp_scale, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace gws

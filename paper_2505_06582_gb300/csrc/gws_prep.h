@@ -1,0 +1,37 @@
+// gws_prep.h -- host launchers of the non-splat kernels (gws_prep.cu).
+#pragma once
+
+#include "gws_host.h"
+
+namespace gws {
+
+struct FootParams {
+    float rho;                     // sqrt(ln(1/eps) / (2 pi^2))
+    float dzmax[GWS_MAX_LAMBDA];   // max |f_z - 1/lambda| over the grid, per wavelength
+};
+
+cudaError_t launch_prep(const SceneTable &T, long long n_total, GPre *gp, float *ampc, unsigned long long *dkey,
+                        unsigned *dval, int *status, cudaStream_t s);
+cudaError_t launch_scene_key(const GPre *gp, const unsigned *sorted, long long n, unsigned *skey, cudaStream_t s);
+cudaError_t launch_transmittance(const GPre *gp, const unsigned *sorted, const Segs &S, long long n, double alpha_min,
+                                 TData *td, double *T_sorted, double *T_g, cudaStream_t s);
+cudaError_t launch_rec64(const GPre *gp, const float *ampc, const unsigned *sorted, const double *T_sorted, long long n,
+                         int L, Rec64 *rec, double *w, cudaStream_t s);
+cudaError_t launch_foot_keys(const GPre *gp, const float *ampc, const unsigned *sorted, const double *T_sorted,
+                             const Segs &S, long long n_rec, const FootParams &F, int drop_zero,
+                             unsigned long long *key, unsigned *val, cudaStream_t s);
+cudaError_t launch_gather(const unsigned long long *key, const unsigned *val, const GPre *gp, const float *ampc,
+                          const unsigned *sorted, const double *T_sorted, const Segs &S, long long n_rec,
+                          const FootParams &F, int drop_zero, int backward, Rec *rec, float *Rr, cudaStream_t s);
+cudaError_t launch_foot_inspect(const GPre *gp, long long n, float rho, float dzmax, float *out, cudaStream_t s);
+cudaError_t launch_items(const float *Rr, const Segs &S, int n_seg, int H, int W, int tw, int th, int tiles_x,
+                         int n_tiles, double dfx, double dfy, unsigned *ikey, unsigned *ival, int *icount,
+                         cudaStream_t s);
+cudaError_t launch_count_pairs(const GPre *gp, long long n, int n_lambda, const FootParams &F, int H, int W,
+                               double dfx, double dfy, unsigned long long *acc, cudaStream_t s);
+cudaError_t launch_modulate(void *data, int prec64, int n_slices, int H, int W, double scale, int mode,
+                            cudaStream_t s);
+cudaError_t launch_encode(const void *field, int prec64, int n_lambda, int H, int W, unsigned long long *amax2,
+                          double amp_scale, float *out, cudaStream_t s);
+
+}  // namespace gws

@@ -1,0 +1,352 @@
+// gws_splat.cu -- forward splat: u_SLM(f) = sum_i W_i |r3.f|/f_z exp(-2 pi^2 [..]) exp(-j 2 pi f.mu_i)
+// (Eq. 10 summed by Eq. 12, or by Eq. 5-6 with T_i at the centre; the weights arrive in W).
+//
+// Mixed-precision persistent tile splat.  A work item is one (scene, wavelength, frequency
+// tile).  A CTA holds the tile's complex accumulators in registers (PX consecutive pixels
+// of one row per thread) and streams the segment's Gaussian records through shared
+// memory with 1-D bulk copies (cp.async.bulk, mbarrier completion, STAGES-deep ring).
+// Records are ordered by decreasing spectral footprint radius, so a tile only reads the
+// prefix of records whose footprint can reach it (item_count); an exact ellipse-rectangle
+// test then culls per (record, tile).
+//
+// Precision: the phase -f.mu reaches ~2e4 cycles.  Per (record, tile) it is split into an
+// FP64 anchor at the tile's reference frequency f0, reduced mod 1 in FP64, plus FP32
+// deltas (f - f0).mu inside the tile (|.| < ~20 cycles); the FP32 phase is reduced to
+// [-1/2, 1/2] cycle before sin/cos.  f0 is the centre of the tile's valid pixels; f_z and
+// f_z - f0_z are formed in FP64 once per pixel and item.  Per-chunk FP32 sums are merged
+// into a TwoSum-compensated FP32 total.
+#include "gws_host.h"
+
+namespace gws {
+
+// Smallest value of the quadratic form f^T E f over the rectangle [x0,x1] x [y0,y1] is <= 1?
+__device__ __forceinline__ bool ellipse_hits_rect(float e00, float e01, float e11, float x0, float x1, float y0,
+                                                  float y1) {
+    if (x0 <= 0.f && 0.f <= x1 && y0 <= 0.f && 0.f <= y1) return true;
+    float best = 3.0e38f;
+    // vertical edges x = xe, y in [y0, y1]
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        float xe = k ? x1 : x0;
+        float ys = e11 > 0.f ? fminf(fmaxf(-e01 * xe / e11, y0), y1) : y0;
+        best = fminf(best, e00 * xe * xe + 2.f * e01 * xe * ys + e11 * ys * ys);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        float ye = k ? y1 : y0;
+        float xs = e00 > 0.f ? fminf(fmaxf(-e01 * ye / e00, x0), x1) : x0;
+        best = fminf(best, e00 * xs * xs + 2.f * e01 * xs * ye + e11 * ye * ye);
+    }
+    return best <= 1.001f;
+}
+
+__device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
+    float t = s + x;
+    float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+}
+
+template <int TW, int TH, int PX, int CHUNK, int STAGES>
+__global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_constant__ SplatArgs A) {
+    constexpr int NT = (TW / PX) * TH;
+    static_assert(CHUNK % 32 == 0 && CHUNK <= NT && CHUNK <= 64, "chunk");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Rec *s_rec = reinterpret_cast<Rec *>(smem_raw);
+    float4 *s_sv = reinterpret_cast<float4 *>(smem_raw + sizeof(Rec) * STAGES * CHUNK);
+    __shared__ uint64_t s_full[STAGES];
+    __shared__ uint64_t s_never;
+    __shared__ unsigned s_mask[2];
+    __shared__ int s_item;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+#pragma unroll
+        for (int st = 0; st < STAGES; ++st) mbar_init(&s_full[st], 1);
+        mbar_init(&s_never, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t parity = 0;
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(A.queue, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= A.n_items) break;
+        const unsigned item = A.items[it];
+        const int seg = (int)(item / (unsigned)A.n_tiles), tile = (int)(item % (unsigned)A.n_tiles);
+        const int scene = seg / A.segs.n_lambda, l = seg % A.segs.n_lambda;
+        const int count = A.item_count[item];
+        const Rec *rbase = A.rec + seg_start(A.segs, seg);
+        const int tx = tile % A.tiles_x, ty = tile / A.tiles_x;
+        const int c_lo = tx * TW, r_lo = ty * TH;
+        const int c_hi = min(c_lo + TW, A.W) - 1, r_hi = min(r_lo + TH, A.H) - 1;
+        const double inv_lam = A.inv_lam[l];
+        const double k2 = inv_lam * inv_lam;
+        // reference frequency f0 of the tile: the centre of its valid pixels, or -- if that is
+        // evanescent -- its pixel nearest to f = 0, so that every |f - f0| stays within the tile
+        int c_ref = (c_lo + c_hi + 1) / 2, r_ref = (r_lo + r_hi + 1) / 2;
+        {
+            const double fx = (double)(c_ref - A.W / 2) * A.dfx, fy = (double)(r_ref - A.H / 2) * A.dfy;
+            if (fx * fx + fy * fy >= k2) {
+                c_ref = min(max(A.W / 2, c_lo), c_hi);
+                r_ref = min(max(A.H / 2, r_lo), r_hi);
+            }
+        }
+        const double f0x = (double)(c_ref - A.W / 2) * A.dfx, f0y = (double)(r_ref - A.H / 2) * A.dfy;
+        const double f0z = sqrt(fmax(k2 - (f0x * f0x + f0y * f0y), 0.0));
+        const float f0xf = (float)f0x, f0yf = (float)f0y, f0zf = (float)f0z, dz0f = (float)(f0z - inv_lam);
+
+        // this thread's pixels: row prow, columns pcol0 .. pcol0 + PX - 1; f_z and f_z - f0_z in FP64
+        const int prow = r_lo + tid / (TW / PX);
+        const int pcol0 = c_lo + (tid % (TW / PX)) * PX;
+        const float dfxf = (float)A.dfx;
+        const float dy = (float)((double)(prow - r_ref) * A.dfy);
+        const double fyd = (double)(prow - A.H / 2) * A.dfy;
+        float dx[PX], dz[PX], ifz[PX];
+#pragma unroll
+        for (int p = 0; p < PX; ++p) {
+            const int col = pcol0 + p;
+            dx[p] = (float)(col - c_ref) * dfxf;
+            const double fxd = (double)(col - A.W / 2) * A.dfx;
+            const double rho2 = fxd * fxd + fyd * fyd;
+            const bool ok = prow < A.H && col < A.W && rho2 < k2;
+            const double fz = ok ? sqrt(k2 - rho2) : 1.0;
+            ifz[p] = ok ? (float)(1.0 / fz) : 0.f;
+            dz[p] = ok ? (float)(fz - f0z) : 0.f;
+        }
+        // tile rectangle (pixel-centre frequencies of the valid pixels) for the cull
+        const float x0 = (float)((double)(c_lo - A.W / 2) * A.dfx), x1 = (float)((double)(c_hi - A.W / 2) * A.dfx);
+        const float y0 = (float)((double)(r_lo - A.H / 2) * A.dfy), y1 = (float)((double)(r_hi - A.H / 2) * A.dfy);
+
+        const int n_chunks = (count + CHUNK - 1) / CHUNK;
+        int issued = 0, consumed = 0;
+        if (tid == 0) fence_proxy_async();
+        for (; issued < min(STAGES, n_chunks); ++issued) {
+            if (tid == 0) {
+                const int st = issued % STAGES;
+                const int nrec = min(CHUNK, count - issued * CHUNK);
+                mbar_expect_tx(&s_full[st], (uint32_t)(nrec * sizeof(Rec)));
+                bulk_g2s(s_rec + st * CHUNK, rbase + (long long)issued * CHUNK, (uint32_t)(nrec * sizeof(Rec)),
+                         &s_full[st]);
+            }
+        }
+
+        float acc_re[PX], acc_im[PX], sum_re[PX], sum_im[PX], cmp_re[PX], cmp_im[PX];
+#pragma unroll
+        for (int p = 0; p < PX; ++p) acc_re[p] = acc_im[p] = sum_re[p] = sum_im[p] = cmp_re[p] = cmp_im[p] = 0.f;
+
+        bool timed_out = false;
+        if (A.debug & GWS_DEBUG_FORCE_TIMEOUT) {
+            // a barrier nothing arrives on: exercises the bounded wait and the drain
+            bool ok = mbar_wait_bounded(&s_never, 0, A.timeout);
+            timed_out = __syncthreads_or(!ok) != 0;
+        }
+        for (int ch = 0; ch < n_chunks && !timed_out; ++ch) {
+            const int st = ch % STAGES;
+            const bool ok = mbar_wait_bounded(&s_full[st], (parity >> st) & 1u, A.timeout);
+            if (__syncthreads_or(!ok)) {
+                timed_out = true;
+                break;
+            }
+            parity ^= (1u << st);
+            consumed = ch + 1;
+
+            // ---- cull + per-(record, tile) scalars (one thread per record) ----
+            const int nrec = min(CHUNK, count - ch * CHUNK);
+            if (tid < CHUNK) {
+                bool pass = false;
+                if (tid < nrec) {
+                    const Rec &r = s_rec[st * CHUNK + tid];
+                    pass = ellipse_hits_rect(r.e00, r.e01, r.e11, x0, x1, y0, y1);
+                    if (pass) {
+                        double cyc = -(f0x * r.mux + f0y * r.muy + f0z * r.muz);
+                        if (A.phase_match) cyc += r.muz * inv_lam;
+                        cyc -= rint(cyc);
+                        const float a0 = fmaf(r.r1z, dz0f, fmaf(r.r1y, f0yf, r.r1x * f0xf));
+                        const float b0 = fmaf(r.r2z, dz0f, fmaf(r.r2y, f0yf, r.r2x * f0xf));
+                        const float g0 = fmaf(r.r3z, f0zf, fmaf(r.r3y, f0yf, r.r3x * f0xf));
+                        float4 *sv = s_sv + tid * 4;
+                        sv[0] = make_float4(r.r1x, r.r1y, r.r1z, a0);
+                        sv[1] = make_float4(r.r2x, r.r2y, r.r2z, b0);
+                        sv[2] = make_float4(r.r3x, r.r3y, r.r3z, g0);
+                        sv[3] = make_float4(r.mx, r.my, r.mz, (float)cyc);
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, pass);
+                if (lane == 0) s_mask[warp] = bal;
+            }
+            __syncthreads();
+            // the stage is free again: refill it with the chunk STAGES ahead
+            if (issued < n_chunks) {
+                if (tid == 0) {
+                    fence_proxy_async();
+                    const int sti = issued % STAGES;
+                    const int nr = min(CHUNK, count - issued * CHUNK);
+                    mbar_expect_tx(&s_full[sti], (uint32_t)(nr * sizeof(Rec)));
+                    bulk_g2s(s_rec + sti * CHUNK, rbase + (long long)issued * CHUNK, (uint32_t)(nr * sizeof(Rec)),
+                             &s_full[sti]);
+                }
+                ++issued;
+            }
+
+            // ---- the hot loop: every surviving record x this thread's PX pixels ----
+            unsigned long long mask = (unsigned long long)s_mask[0];
+            if (CHUNK > 32) mask |= (unsigned long long)s_mask[1] << 32;
+            while (mask) {
+                const int k = __ffsll((long long)mask) - 1;
+                mask &= mask - 1ull;
+                const float4 Ar = s_sv[k * 4 + 0], Br = s_sv[k * 4 + 1], Gr = s_sv[k * 4 + 2], Mr = s_sv[k * 4 + 3];
+                const float ar = fmaf(Ar.y, dy, Ar.w), br = fmaf(Br.y, dy, Br.w);
+                const float gr = fmaf(Gr.y, dy, Gr.w), tr = fmaf(Mr.y, dy, Mr.w);
+#pragma unroll
+                for (int p = 0; p < PX; ++p) {
+                    const float a = fmaf(Ar.z, dz[p], fmaf(Ar.x, dx[p], ar));
+                    const float b = fmaf(Br.z, dz[p], fmaf(Br.x, dx[p], br));
+                    const float g = fmaf(Gr.z, dz[p], fmaf(Gr.x, dx[p], gr));
+                    const float t = fmaf(Mr.z, dz[p], fmaf(Mr.x, dx[p], tr));
+                    const float e = ex2_approx(-fmaf(a, a, b * b));
+                    const float amp = fabsf(g) * ifz[p] * e;
+                    // t - round(t) on the FP32 pipe (|t| < 2^22): adding and removing 1.5 * 2^23
+                    const float ang = (t - (__fadd_rn(t, 12582912.0f) - 12582912.0f)) * 6.28318530717958647692f;
+                    acc_re[p] = fmaf(amp, cos_approx(ang), acc_re[p]);
+                    acc_im[p] = fmaf(amp, sin_approx(ang), acc_im[p]);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < PX; ++p) {
+                two_sum_acc(sum_re[p], cmp_re[p], acc_re[p]);
+                two_sum_acc(sum_im[p], cmp_im[p], acc_im[p]);
+                acc_re[p] = acc_im[p] = 0.f;
+            }
+            __syncthreads();
+        }
+
+        if (timed_out) {
+            if (tid == 0) atomicOr(A.status, ST_TIMEOUT);
+            // wait (bounded) for this CTA's own copies still in flight, then leave
+            for (int ch = consumed; ch < issued; ++ch) {
+                const int st = ch % STAGES;
+                mbar_wait_bounded(&s_full[st], (parity >> st) & 1u, 4ull * A.timeout + 100000ull);
+                parity ^= (1u << st);
+            }
+            return;
+        }
+
+        // ---- epilogue: compensated total, centred-DFT pre-modulation, store ----
+        if (prow < A.H) {
+            float2 *out = reinterpret_cast<float2 *>(A.out[scene]) + (size_t)l * A.H * A.W + (size_t)prow * A.W;
+            const double frow = mod_frac(prow, A.H / 2, A.H);
+#pragma unroll
+            for (int p = 0; p < PX; ++p) {
+                const int col = pcol0 + p;
+                if (col < A.W) {
+                    float re = sum_re[p] + cmp_re[p], im = sum_im[p] + cmp_im[p];
+                    if (A.field_mode) {
+                        double fr = frow + mod_frac(col, A.W / 2, A.W);
+                        fr -= rint(fr);
+                        float sn, cs;
+                        sincospif(-2.0f * (float)fr, &sn, &cs);
+                        const float r2 = re * cs - im * sn;
+                        im = re * sn + im * cs;
+                        re = r2;
+                    }
+                    out[col] = make_float2(re, im);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- tile configurations (autotuned) ----------------------------------------------------
+
+template <int TW, int TH, int PX>
+static cudaError_t launch_cfg(const SplatArgs &a, int grid, cudaStream_t s) {
+    constexpr int CHUNK = 64, STAGES = 3;
+    constexpr int NT = (TW / PX) * TH;
+    const size_t smem = sizeof(Rec) * STAGES * CHUNK + sizeof(float4) * 4 * CHUNK;
+    auto kern = k_splat_mixed<TW, TH, PX, CHUNK, STAGES>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, NT, smem, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+static const TileCfg kCfgs[] = {{1, 64, 32}, {2, 32, 32}, {3, 128, 16}};
+
+int n_tile_cfgs() { return (int)(sizeof(kCfgs) / sizeof(kCfgs[0])); }
+TileCfg tile_cfg(int id) {
+    if (id < 1 || id > n_tile_cfgs()) id = 1;
+    return kCfgs[id - 1];
+}
+int splat_mixed_ctas_per_sm(int cfg) {
+    (void)cfg;
+    return 2;
+}
+
+cudaError_t launch_splat_mixed(int cfg, const SplatArgs &a, int grid, cudaStream_t s) {
+    switch (cfg) {
+        case 2: return launch_cfg<32, 32, 4>(a, grid, s);
+        case 3: return launch_cfg<128, 16, 8>(a, grid, s);
+        default: return launch_cfg<64, 32, 8>(a, grid, s);
+    }
+}
+
+// ---- plain FP64 path: one thread per frequency pixel, every Gaussian, no truncation ----
+
+__global__ void __launch_bounds__(256) k_splat_fp64(const __grid_constant__ Splat64Args A) {
+    const int c = blockIdx.x * 16 + threadIdx.x;
+    const int r = blockIdx.y * 16 + threadIdx.y;
+    const int seg = blockIdx.z;
+    const int scene = seg / A.segs.n_lambda, l = seg % A.segs.n_lambda;
+    if (r >= A.H || c >= A.W) return;
+    const double inv_lam = A.inv_lam[l];
+    const double fx = (double)(c - A.W / 2) * A.dfx, fy = (double)(r - A.H / 2) * A.dfy;
+    const double rho2 = fx * fx + fy * fy, k2 = inv_lam * inv_lam;
+    double sre = 0.0, sim = 0.0;
+    if (rho2 < k2) {
+        const double fz = sqrt(k2 - rho2);
+        const double dz = fz - inv_lam;
+        const long long p0 = A.segs.off[scene], p1 = A.segs.off[scene + 1];
+        const int L = A.segs.n_lambda;
+        for (long long p = p0; p < p1; ++p) {
+            const Rec64 &g = A.rec[p];
+            const double w = A.w[p * L + l];
+            const double a = g.r1[0] * fx + g.r1[1] * fy + g.r1[2] * dz;
+            const double b = g.r2[0] * fx + g.r2[1] * fy + g.r2[2] * dz;
+            const double gg = g.r3[0] * fx + g.r3[1] * fy + g.r3[2] * fz;
+            const double amp = w * kTwoPi * g.su * g.sv * fabs(gg) / fz *
+                               exp(-2.0 * kPi * kPi * (g.su * g.su * a * a + g.sv * g.sv * b * b));
+            double cyc = -(fx * g.mu[0] + fy * g.mu[1] + fz * g.mu[2]);
+            if (A.phase_match) cyc += g.mu[2] * inv_lam;
+            cyc -= rint(cyc);
+            double sn, cs;
+            sincospi(2.0 * cyc, &sn, &cs);
+            sre += amp * cs;
+            sim += amp * sn;
+        }
+    }
+    if (A.field_mode) {
+        double fr = mod_frac(r, A.H / 2, A.H) + mod_frac(c, A.W / 2, A.W);
+        fr -= rint(fr);
+        double sn, cs;
+        sincospi(-2.0 * fr, &sn, &cs);
+        const double t = sre * cs - sim * sn;
+        sim = sre * sn + sim * cs;
+        sre = t;
+    }
+    double2 *out = reinterpret_cast<double2 *>(A.out[scene]) + (size_t)l * A.H * A.W + (size_t)r * A.W + c;
+    *out = make_double2(sre, sim);
+}
+
+cudaError_t launch_splat_fp64(const Splat64Args &a, cudaStream_t s) {
+    dim3 grid((a.W + 15) / 16, (a.H + 15) / 16, a.segs.n_scenes * a.segs.n_lambda);
+    k_splat_fp64<<<grid, dim3(16, 16), 0, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace gws

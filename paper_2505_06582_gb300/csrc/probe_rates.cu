@@ -1,0 +1,55 @@
+// probe_rates.cu -- unit-rate microbenchmarks for the roofline denominators: FP32 FMA, MUFU ex2 / sin, FP64 DFMA
+// (CUDA events; every access in bounds, no waits).  Build: nvcc -O3 -gencode arch=compute_103a,code=sm_103a probe_rates.cu
+#include <cstdio>
+#include <cuda_runtime.h>
+#define CK(x) do{cudaError_t e=(x); if(e!=cudaSuccess){printf("CUDA %s @%d\n",cudaGetErrorString(e),__LINE__); return 1;}}while(0)
+constexpr int ITERS=4096;
+__global__ void k_fma(float* out, float a, float b){
+  float x0=threadIdx.x, x1=x0+1, x2=x0+2, x3=x0+3, x4=x0+4, x5=x0+5, x6=x0+6, x7=x0+7;
+  for(int i=0;i<ITERS;i++){ x0=fmaf(x0,a,b); x1=fmaf(x1,a,b); x2=fmaf(x2,a,b); x3=fmaf(x3,a,b);
+    x4=fmaf(x4,a,b); x5=fmaf(x5,a,b); x6=fmaf(x6,a,b); x7=fmaf(x7,a,b);}
+  out[blockIdx.x*blockDim.x+threadIdx.x]=x0+x1+x2+x3+x4+x5+x6+x7;
+}
+__device__ __forceinline__ float ex2(float x){float y; asm volatile("ex2.approx.ftz.f32 %0, %1;":"=f"(y):"f"(x)); return y;}
+__device__ __forceinline__ float sn(float x){float y; asm volatile("sin.approx.ftz.f32 %0, %1;":"=f"(y):"f"(x)); return y;}
+__global__ void k_ex2(float* out, float a){
+  float x0=threadIdx.x*1e-3f, x1=x0+.1f, x2=x0+.2f, x3=x0+.3f, x4=x0+.4f, x5=x0+.5f, x6=x0+.6f, x7=x0+.7f;
+  for(int i=0;i<ITERS;i++){ x0=ex2(x0)*a; x1=ex2(x1)*a; x2=ex2(x2)*a; x3=ex2(x3)*a; x4=ex2(x4)*a; x5=ex2(x5)*a; x6=ex2(x6)*a; x7=ex2(x7)*a;}
+  out[blockIdx.x*blockDim.x+threadIdx.x]=x0+x1+x2+x3+x4+x5+x6+x7;
+}
+__global__ void k_ex2only(float* out){
+  float x0=threadIdx.x*1e-3f, x1=x0+.1f, x2=x0+.2f, x3=x0+.3f, x4=x0+.4f, x5=x0+.5f, x6=x0+.6f, x7=x0+.7f;
+  for(int i=0;i<ITERS;i++){ x0=ex2(x0); x1=ex2(x1); x2=ex2(x2); x3=ex2(x3); x4=ex2(x4); x5=ex2(x5); x6=ex2(x6); x7=ex2(x7);}
+  out[blockIdx.x*blockDim.x+threadIdx.x]=x0+x1+x2+x3+x4+x5+x6+x7;
+}
+__global__ void k_sin(float* out){
+  float x0=threadIdx.x*1e-3f, x1=x0+.1f, x2=x0+.2f, x3=x0+.3f, x4=x0+.4f, x5=x0+.5f, x6=x0+.6f, x7=x0+.7f;
+  for(int i=0;i<ITERS;i++){ x0=sn(x0); x1=sn(x1); x2=sn(x2); x3=sn(x3); x4=sn(x4); x5=sn(x5); x6=sn(x6); x7=sn(x7);}
+  out[blockIdx.x*blockDim.x+threadIdx.x]=x0+x1+x2+x3+x4+x5+x6+x7;
+}
+__global__ void k_dfma(double* out, double a, double b){
+  double x0=threadIdx.x, x1=x0+1, x2=x0+2, x3=x0+3;
+  for(int i=0;i<ITERS/8;i++){ x0=fma(x0,a,b); x1=fma(x1,a,b); x2=fma(x2,a,b); x3=fma(x3,a,b);}
+  out[blockIdx.x*blockDim.x+threadIdx.x]=x0+x1+x2+x3;
+}
+int main(){
+  cudaDeviceProp p; CK(cudaGetDeviceProperties(&p,0));
+  int clk=0, memclk=0; cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, 0); cudaDeviceGetAttribute(&memclk, cudaDevAttrMemoryClockRate, 0);
+  printf("{\"name\":\"%s\",\"sms\":%d,\"cc\":\"%d.%d\",\"clock_khz\":%d,\"smem_optin\":%zu,\"regs_per_sm\":%d,\"l2\":%d}\n", p.name, p.multiProcessorCount, p.major,p.minor, clk, p.sharedMemPerBlockOptin, p.regsPerMultiprocessor, p.l2CacheSize);
+  int blocks=p.multiProcessorCount*8, threads=256; size_t n=(size_t)blocks*threads;
+  float* o; double* od; CK(cudaMalloc(&o,n*4)); CK(cudaMalloc(&od,n*8));
+  cudaEvent_t e0,e1; cudaEventCreate(&e0); cudaEventCreate(&e1); float ms;
+  for(int rep=0;rep<3;rep++){
+    k_fma<<<blocks,threads>>>(o,0.999f,0.001f); CK(cudaEventRecord(e0)); k_fma<<<blocks,threads>>>(o,0.999f,0.001f); CK(cudaEventRecord(e1)); CK(cudaEventSynchronize(e1)); cudaEventElapsedTime(&ms,e0,e1);
+    double fma_rate = (double)n*ITERS*8/(ms*1e-3); printf("fp32 fma/s %.4g  per SM per clk(at %d kHz) %.2f\n", fma_rate, clk, fma_rate/p.multiProcessorCount/(clk*1e3));
+    k_ex2<<<blocks,threads>>>(o,0.5f); CK(cudaEventRecord(e0)); k_ex2<<<blocks,threads>>>(o,0.5f); CK(cudaEventRecord(e1)); CK(cudaEventSynchronize(e1)); cudaEventElapsedTime(&ms,e0,e1);
+    double ex2_rate=(double)n*ITERS*8/(ms*1e-3); printf("ex2+fmul pairs/s %.4g per SM per clk %.2f\n", ex2_rate, ex2_rate/p.multiProcessorCount/(clk*1e3));
+    k_ex2only<<<blocks,threads>>>(o); CK(cudaEventRecord(e0)); k_ex2only<<<blocks,threads>>>(o); CK(cudaEventRecord(e1)); CK(cudaEventSynchronize(e1)); cudaEventElapsedTime(&ms,e0,e1);
+    ex2_rate=(double)n*ITERS*8/(ms*1e-3); printf("ex2 only /s %.4g per SM per clk %.2f\n", ex2_rate, ex2_rate/p.multiProcessorCount/(clk*1e3));
+    k_sin<<<blocks,threads>>>(o); CK(cudaEventRecord(e0)); k_sin<<<blocks,threads>>>(o); CK(cudaEventRecord(e1)); CK(cudaEventSynchronize(e1)); cudaEventElapsedTime(&ms,e0,e1);
+    double sin_rate=(double)n*ITERS*8/(ms*1e-3); printf("sin.approx /s %.4g per SM per clk %.2f\n", sin_rate, sin_rate/p.multiProcessorCount/(clk*1e3));
+    k_dfma<<<blocks,threads>>>(od,0.999,0.001); CK(cudaEventRecord(e0)); k_dfma<<<blocks,threads>>>(od,0.999,0.001); CK(cudaEventRecord(e1)); CK(cudaEventSynchronize(e1)); cudaEventElapsedTime(&ms,e0,e1);
+    double d_rate=(double)n*(ITERS/8)*4/(ms*1e-3); printf("fp64 dfma/s %.4g per SM per clk %.3f\n", d_rate, d_rate/p.multiProcessorCount/(clk*1e3));
+  }
+  CK(cudaDeviceSynchronize()); printf("ok\n"); return 0;
+}

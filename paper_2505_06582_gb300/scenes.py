@@ -133,6 +133,10 @@ def surface_scene(seed: int, n: int, slm: SLM, n_surfaces=8, scale_median_px=2.0
                   opacity_range=(0.05, 1.0), z_clip=(2e-3, 10e-3)) -> Scene:
     """Gaussians on random spheres (SLM-facing hemispheres) and tilted planes."""
     rng = np.random.default_rng(seed)
+    if n == 0:
+        z = np.zeros
+        return Scene(z((0, 3)), z((0, 4), np.float32), z((0, 2), np.float32), z(0, np.float32),
+                     z((0, slm.n_lambda), np.float32), {"kind": "surface", "seed": seed, "surfaces": n_surfaces})
     ax, ay = slm.W * slm.pitch_x, slm.H * slm.pitch_y
     counts = np.full(n_surfaces, n // n_surfaces)
     counts[: n - counts.sum()] += 1

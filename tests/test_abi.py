@@ -1,0 +1,125 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, exports every symbol
+include/gws.h declares, and rejects bad arguments on the host (no GPU calls)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2505_06582_gb300 import _build, gws
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gws.h")).read()
+    return sorted(set(re.findall(r"^GWS_API [^(]*?\b(gws_\w+)\(", src, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = gws.load()
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(gws.EXPORTS)
+
+
+def test_library_is_built_for_sm_103a_only():
+    out = os.popen(f"{_build.NVCC} --version").read()
+    assert "release" in out
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.exists(_build.LIB)
+
+
+def test_status_strings_and_version():
+    lib = gws.load()
+    assert lib.gws_version() == 1
+    for code, name in gws.STATUS.items():
+        assert lib.gws_status_string(code).decode() == name
+
+
+def test_defaults():
+    lib = gws.load()
+    o = gws._Opts()
+    lib.gws_opts_default(C.byref(o))
+    assert (o.blend, o.prec, o.domain, o.phase_match) == (0, 1, 0, 0)
+    assert abs(o.trunc_eps - 1e-5) < 1e-12 and abs(o.alpha_min - 1 / 255) < 1e-9
+    assert o.timeout_cycles > 0 and not o.workspace
+
+
+def _opts(**kw):
+    lib = gws.load()
+    o = gws._Opts()
+    lib.gws_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+@pytest.mark.parametrize("bad", [
+    dict(H=0), dict(W=-1), dict(pitch_x=0.0), dict(pitch_y=float("nan")), dict(n_lambda=0), dict(n_lambda=17),
+    dict(wl=-5e-7), dict(wl=float("inf")),
+])
+def test_bad_slm_rejected_on_host(bad):
+    lib = gws.load()
+    wl = (C.c_double * 16)(*([bad.get("wl", 5e-7)] * 16))
+    s = gws._Slm(bad.get("H", 8), bad.get("W", 8), bad.get("pitch_x", 8e-6), bad.get("pitch_y", 8e-6),
+                 bad.get("n_lambda", 1), wl)
+    n = (C.c_int64 * 1)(4)
+    out = C.c_size_t(0)
+    o = _opts(domain=1)
+    assert lib.gws_workspace_size(n, 1, C.byref(s), C.byref(o), C.byref(out)) == 1
+
+
+@pytest.mark.parametrize("bad", [dict(blend=5), dict(prec=2), dict(domain=9), dict(trunc_eps=0.0),
+                                 dict(trunc_eps=1.5), dict(alpha_min=-0.1), dict(timeout_cycles=0),
+                                 dict(tile_cfg=99)])
+def test_bad_options_rejected_on_host(bad):
+    lib = gws.load()
+    wl = (C.c_double * 1)(5e-7)
+    s = gws._Slm(8, 8, 8e-6, 8e-6, 1, wl)
+    n = (C.c_int64 * 1)(4)
+    out = C.c_size_t(0)
+    o = _opts(domain=1)
+    for k, v in bad.items():
+        setattr(o, k, v)
+    assert lib.gws_workspace_size(n, 1, C.byref(s), C.byref(o), C.byref(out)) == 1
+
+
+def test_workspace_size_grows_with_n_and_covers_layout():
+    lib = gws.load()
+    wl = (C.c_double * 3)(6.38e-7, 5.2e-7, 4.5e-7)
+    s = gws._Slm(64, 96, 8e-6, 8e-6, 3, wl)
+    sizes = []
+    for n in (0, 10, 1000, 100000):
+        arr = (C.c_int64 * 1)(n)
+        out = C.c_size_t(0)
+        assert lib.gws_workspace_size(arr, 1, C.byref(s), C.byref(_opts(domain=1)), C.byref(out)) == 0
+        sizes.append(out.value)
+    assert sizes == sorted(sizes) and sizes[-1] > 100000 * 3 * 96
+    # too many scenes / negative sizes
+    arr = (C.c_int64 * 2)(5, -1)
+    out = C.c_size_t(0)
+    assert lib.gws_workspace_size(arr, 2, C.byref(s), C.byref(_opts(domain=1)), C.byref(out)) == 1
+    assert lib.gws_workspace_size(arr, 0, C.byref(s), C.byref(_opts(domain=1)), C.byref(out)) == 1
+
+
+def test_null_arguments_rejected_before_any_launch():
+    lib = gws.load()
+    wl = (C.c_double * 1)(5e-7)
+    s = gws._Slm(8, 8, 8e-6, 8e-6, 1, wl)
+    o = _opts(domain=1)
+    g = gws._Gaussians(0, 0, 0, 0, 0)
+    # null Gaussian arrays with n > 0
+    assert lib.gws_forward(C.byref(g), C.c_int64(3), C.byref(s), C.byref(o), C.c_void_p(16)) == 1
+    # null output
+    assert lib.gws_forward(C.byref(g), C.c_int64(0), C.byref(s), C.byref(o), None) == 1
+    # missing workspace
+    ok = gws._Gaussians(256, 256, 256, 256, 256)
+    assert lib.gws_forward(C.byref(ok), C.c_int64(3), C.byref(s), C.byref(o), C.c_void_p(256)) == 2
+    # misaligned workspace
+    o.workspace, o.workspace_bytes = C.c_void_p(256 + 8), 1 << 30
+    assert lib.gws_forward(C.byref(ok), C.c_int64(3), C.byref(s), C.byref(o), C.c_void_p(256)) == 2
+    # encode: null field
+    assert lib.gws_encode(None, C.byref(s), C.byref(o), C.c_void_p(256), C.c_float(0)) == 1

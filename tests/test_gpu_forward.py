@@ -1,0 +1,278 @@
+"""GPU parity: the CUDA forward path (through the C ABI) against the FP64 oracle.
+
+Bars (relative L2 over each wavelength's field or spectrum):
+  FP64 GPU path <= 1e-6, mixed-precision path <= 2e-4.
+Depth order: bit-exact.  Transmittance: FP64 both sides (the 1/255 decisions are taken
+in FP64 on both sides), 1e-12.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2505_06582_gb300 import gws
+from paper_2505_06582_gb300.scenes import SLM, config_scene, surface_scene, uniform_scene
+from tests.helpers import make_scene, qaxis, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL64, TOLMX = 1e-6, 2e-4
+
+
+def per_lambda_rel(a, b):
+    return [rel_l2(a[l], b[l]) for l in range(b.shape[0])]
+
+
+def dev(sc):
+    return gws.Gaussians.from_scene(sc, "cuda")
+
+
+# ---------------------------------------------------------------------------------------
+# element-wise parity at oracle-sized workloads (several tiles, ragged tails)
+# ---------------------------------------------------------------------------------------
+
+CASES = [
+    ("c0", SLM(128, 128, 8e-6, 8e-6, (520e-9,)), "uniform", 0, 64),
+    ("ragged", SLM(100, 150, 8e-6, 6e-6, (638e-9, 450e-9)), "uniform", 3, 40),
+    ("odd", SLM(77, 99, 8e-6, 8e-6, (520e-9,)), "surface", 4, 60),
+    ("tiny", SLM(9, 7, 8e-6, 8e-6, (520e-9,)), "uniform", 5, 3),
+    ("onecol", SLM(33, 1, 8e-6, 8e-6, (520e-9,)), "uniform", 6, 4),
+]
+
+
+def _scene(kind, seed, n, slm):
+    if kind == "uniform":
+        return uniform_scene(seed, n, slm)
+    return surface_scene(seed, n, slm, n_surfaces=4)
+
+
+@pytest.mark.parametrize("name,slm,kind,seed,n", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("blend", [gws.BLEND_OIT, gws.BLEND_SORTED_T], ids=["oit", "sortedT"])
+def test_forward_field_matches_oracle(name, slm, kind, seed, n, blend):
+    sc = _scene(kind, seed, n, slm)
+    ref = O.field(sc, slm, blend=blend)
+    g = dev(sc)
+    f64 = gws.forward(g, slm, prec=gws.PREC_FP64, blend=blend).cpu().numpy()
+    fmx = gws.forward(g, slm, prec=gws.PREC_MIXED, blend=blend).cpu().numpy()
+    assert max(per_lambda_rel(f64, ref)) < TOL64
+    assert max(per_lambda_rel(fmx, ref)) < TOLMX
+
+
+@pytest.mark.parametrize("tile_cfg", [1, 2, 3])
+def test_spectrum_domain_and_every_tile_config(tile_cfg):
+    slm = SLM(96, 160, 8e-6, 8e-6, (638e-9, 520e-9, 450e-9))
+    sc = surface_scene(7, 120, slm, n_surfaces=3)
+    ref = O.spectrum(sc, slm)
+    g = dev(sc)
+    u = gws.forward(g, slm, prec=gws.PREC_MIXED, domain=gws.DOMAIN_SPECTRUM, tile_cfg=tile_cfg).cpu().numpy()
+    assert max(per_lambda_rel(u, ref)) < TOLMX
+    u64 = gws.forward(g, slm, prec=gws.PREC_FP64, domain=gws.DOMAIN_SPECTRUM).cpu().numpy()
+    assert max(per_lambda_rel(u64, ref)) < TOL64
+
+
+def test_phase_match_option():
+    slm = SLM(64, 64, 8e-6, 8e-6, (520e-9,))
+    sc = uniform_scene(8, 20, slm)
+    ref = O.spectrum(sc, slm, phase_match=True)
+    g = dev(sc)
+    for prec, tol in ((gws.PREC_FP64, TOL64), (gws.PREC_MIXED, TOLMX)):
+        u = gws.forward(g, slm, prec=prec, domain=gws.DOMAIN_SPECTRUM, phase_match=True).cpu().numpy()
+        assert rel_l2(u, ref) < tol
+
+
+def test_empty_and_single_gaussian():
+    slm = SLM(40, 56, 8e-6, 8e-6, (520e-9, 450e-9))
+    sc = uniform_scene(9, 1, slm)
+    empty = sc.subset(np.arange(0))
+    for prec in (gws.PREC_FP64, gws.PREC_MIXED):
+        z = gws.forward(dev(empty), slm, prec=prec).cpu().numpy()
+        assert np.array_equal(z, np.zeros_like(z))
+        u = gws.forward(dev(sc), slm, prec=prec).cpu().numpy()
+        assert max(per_lambda_rel(u, O.field(sc, slm))) < (TOL64 if prec == gws.PREC_FP64 else TOLMX)
+
+
+def test_evanescent_band_is_zero():
+    # pitch below lambda/2: the corners of the grid are evanescent (Eq. 4 cuts them)
+    slm = SLM(32, 32, 0.2e-6, 0.2e-6, (520e-9,))
+    sc = make_scene([[0, 0, 2e-6]], [qaxis([1, 0, 0], 0.4)], [[0.3e-6, 0.4e-6]], [1.0], [[1.0]])
+    ref = O.spectrum(sc, slm)
+    assert (ref == 0).any() and (ref != 0).any()
+    for prec, tol in ((gws.PREC_FP64, TOL64), (gws.PREC_MIXED, TOLMX)):
+        u = gws.forward(dev(sc), slm, prec=prec, domain=gws.DOMAIN_SPECTRUM).cpu().numpy()
+        assert rel_l2(u, ref) < tol
+        assert np.all(u[ref == 0] == 0)
+
+
+def test_full_occlusion_sorted_t():
+    slm = SLM(64, 64, 8e-6, 8e-6, (520e-9,))
+    front = make_scene([[0, 0, 2e-3]], [[1, 0, 0, 0]], [[80e-6, 60e-6]], [1.0], [[0.7]])
+    rear = make_scene([[0, 0, 4e-3]], [qaxis([1, 0, 0], 0.5)], [[20e-6, 20e-6]], [0.8], [[0.9]])
+    both = rear.concat(front)
+    for prec in (gws.PREC_FP64, gws.PREC_MIXED):
+        u = gws.forward(dev(both), slm, prec=prec, blend=gws.BLEND_SORTED_T, domain=gws.DOMAIN_SPECTRUM)
+        uf = gws.forward(dev(front), slm, prec=prec, domain=gws.DOMAIN_SPECTRUM)
+        assert torch.equal(u, uf)
+
+
+# ---------------------------------------------------------------------------------------
+# depth sort, transmittance, footprints
+# ---------------------------------------------------------------------------------------
+
+def test_depth_order_bit_exact_with_ties():
+    slm = SLM(8, 8, 8e-6, 8e-6, (520e-9,))
+    sc = uniform_scene(10, 5000, slm)
+    sc.mean[::7, 2] = 3e-3
+    sc.mean[3, 2] = -0.0
+    sc.mean[4, 2] = 0.0
+    sc.mean[5, 2] = -1e-3
+    order = gws.depth_order(dev(sc)).cpu().numpy()
+    assert np.array_equal(order, O.depth_order(sc.mean))
+
+
+def test_transmittance_matches_oracle():
+    slm = SLM(64, 64, 8e-6, 8e-6, (520e-9,))
+    sc = surface_scene(11, 3000, slm, n_surfaces=3, scale_median_px=6.0)
+    T = gws.transmittance(dev(sc)).cpu().numpy()
+    Tr = O.transmittance(sc)
+    assert (Tr < 0.99).mean() > 0.2  # the scene really occludes
+    assert np.abs(T - Tr).max() < 1e-12
+
+
+def test_footprints_bound_the_truncated_spectrum():
+    """Outside each footprint ellipse the oracle's Gaussian factor exp(-E) is below eps."""
+    slm = SLM(128, 160, 8e-6, 8e-6, (638e-9, 450e-9))
+    sc = surface_scene(12, 40, slm, n_surfaces=2)
+    eps = 1e-5
+    fx = (np.arange(slm.W) - slm.W // 2) / (slm.W * slm.pitch_x)
+    fy = (np.arange(slm.H) - slm.H // 2) / (slm.H * slm.pitch_y)
+    FX, FY = np.meshgrid(fx, fy)
+    for l, lam in enumerate(slm.wavelengths):
+        ell = gws.footprints(dev(sc), slm, l, trunc_eps=eps).cpu().numpy().astype(np.float64)
+        for i in range(sc.n):
+            _, E = O.single_terms(sc.mean[i], sc.quat[i], sc.scale[i], lam, slm.H, slm.W, slm.pitch_x, slm.pitch_y)
+            q = ell[i, 0] * FX ** 2 + 2 * ell[i, 1] * FX * FY + ell[i, 2] * FY ** 2
+            outside = q > 1.0
+            assert np.all(E[outside] >= math.log(1 / eps) * (1 - 1e-6))
+
+
+# ---------------------------------------------------------------------------------------
+# batching, device status
+# ---------------------------------------------------------------------------------------
+
+def test_batched_equals_individual_calls_bitwise():
+    slm = SLM(72, 96, 8e-6, 8e-6, (638e-9, 520e-9))
+    scenes = [surface_scene(20 + k, n, slm, n_surfaces=2) for k, n in enumerate([30, 1, 75, 0, 12])]
+    gs = [dev(s) for s in scenes]
+    for prec in (gws.PREC_MIXED, gws.PREC_FP64):
+        for blend in (gws.BLEND_OIT, gws.BLEND_SORTED_T):
+            outs = gws.forward_batched(gs, slm, prec=prec, blend=blend)
+            for g, o in zip(gs, outs):
+                single = gws.forward(g, slm, prec=prec, blend=blend)
+                assert torch.equal(o, single)
+
+
+def test_device_status_reports_bad_inputs_and_timeouts():
+    slm = SLM(32, 32, 8e-6, 8e-6, (520e-9,))
+    sc = uniform_scene(13, 10, slm)
+    ws = torch.empty(gws.workspace_size([10], gws.Slm.of(slm), gws.make_opts()) + 4096, dtype=torch.uint8,
+                     device="cuda")
+    gws.forward(dev(sc), slm, workspace=ws)
+    assert gws.device_status([10], slm, workspace=ws) == 0
+    bad = sc.subset(np.arange(10))
+    bad.mean[3, 1] = np.nan
+    gws.forward(dev(bad), slm, workspace=ws)
+    assert gws.device_status([10], slm, workspace=ws) == 4
+    bad = sc.subset(np.arange(10))
+    bad.opacity[2] = 1.5
+    gws.forward(dev(bad), slm, workspace=ws)
+    assert gws.device_status([10], slm, workspace=ws) == 1
+    # a bounded wait that nothing completes: the kernel records TIMEOUT and returns
+    gws.forward(dev(sc), slm, workspace=ws, debug_flags=gws.DEBUG_FORCE_TIMEOUT, timeout_cycles=200_000)
+    assert gws.device_status([10], slm, workspace=ws) == 5
+    # the context is intact: a normal call afterwards is correct
+    u = gws.forward(dev(sc), slm, workspace=ws).cpu().numpy()
+    assert gws.device_status([10], slm, workspace=ws) == 0
+    assert rel_l2(u, O.field(sc, slm)) < TOLMX
+
+
+# ---------------------------------------------------------------------------------------
+# full-size workloads: sampled spectra (the oracle computes each sample over all Gaussians)
+# ---------------------------------------------------------------------------------------
+
+def _samples(slm, k, seed):
+    rng = np.random.default_rng(seed)
+    lam = rng.integers(0, slm.n_lambda, k).astype(np.int32)
+    # half near DC (where every Gaussian contributes), half anywhere
+    r = np.where(np.arange(k) % 2 == 0, rng.integers(0, slm.H, k),
+                 slm.H // 2 + rng.integers(-slm.H // 8, slm.H // 8, k)).astype(np.int32)
+    c = np.where(np.arange(k) % 2 == 0, rng.integers(0, slm.W, k),
+                 slm.W // 2 + rng.integers(-slm.W // 8, slm.W // 8, k)).astype(np.int32)
+    return lam, r, c
+
+
+@pytest.mark.parametrize("cfg,n,k", [("c1_slm_size", None, 400), ("headline_1m_1080p_3l", None, 120)])
+def test_full_size_sampled_spectrum(cfg, n, k):
+    sc, slm = config_scene(cfg, n=n)
+    g = dev(sc)
+    u = gws.forward(g, slm, prec=gws.PREC_MIXED, domain=gws.DOMAIN_SPECTRUM)
+    lam, r, c = _samples(slm, k, 99)
+    got = u[torch.as_tensor(lam, dtype=torch.long), torch.as_tensor(r, dtype=torch.long),
+            torch.as_tensor(c, dtype=torch.long)].cpu().numpy()
+    ref = O.spectrum_at(sc, slm, lam, r, c)
+    for l in range(slm.n_lambda):
+        m = lam == l
+        assert rel_l2(got[m], ref[m]) < TOLMX, (l, rel_l2(got[m], ref[m]))
+    # the field of the same call equals torch's FFT of the spectrum (the IDFT stage at full size)
+    f = gws.forward(g, slm, prec=gws.PREC_MIXED)
+    dfx, dfy = 1 / (slm.W * slm.pitch_x), 1 / (slm.H * slm.pitch_y)
+    uu = u.to(torch.complex128)
+    ref_f = dfx * dfy * slm.H * slm.W * torch.fft.fftshift(torch.fft.ifft2(torch.fft.ifftshift(uu, dim=(-2, -1))),
+                                                           dim=(-2, -1))
+    for l in range(slm.n_lambda):
+        e = (torch.linalg.norm(f[l].to(torch.complex128) - ref_f[l]) / torch.linalg.norm(ref_f[l])).item()
+        assert e < 1e-5, e
+
+
+def test_fp64_path_at_slm_size_sampled():
+    sc, slm = config_scene("c1_slm_size", n=2000)
+    u = gws.forward(dev(sc), slm, prec=gws.PREC_FP64, domain=gws.DOMAIN_SPECTRUM)
+    lam, r, c = _samples(slm, 300, 5)
+    got = u[torch.as_tensor(lam, dtype=torch.long), torch.as_tensor(r, dtype=torch.long),
+            torch.as_tensor(c, dtype=torch.long)].cpu().numpy()
+    ref = O.spectrum_at(sc, slm, lam, r, c)
+    assert rel_l2(got, ref) < TOL64
+
+
+# ---------------------------------------------------------------------------------------
+# encoding
+# ---------------------------------------------------------------------------------------
+
+def _circ(a, b):
+    return np.abs(np.angle(np.exp(1j * (a - b))))
+
+
+@pytest.mark.parametrize("shape", [(1, 64, 64), (3, 37, 53), (2, 1080, 1920)])
+def test_encode_matches_oracle(shape):
+    from paper_2505_06582_gb300.scenes import random_field
+    f = random_field(17, shape, zero_frac=0.01)
+    slm = SLM(shape[1], shape[2], 8e-6, 8e-6, tuple([520e-9] * shape[0]))
+    # FP64 field: FP64 encode, written as float32 phases: half an ulp of |P| <= pi is 1.2e-7 rad
+    p64 = gws.encode(torch.as_tensor(f, device="cuda"), slm).cpu().numpy()
+    ref = O.encode(f)
+    assert _circ(p64, ref).max() < 2.5e-7
+    # complex64 field: FP32 encode.  acos is ill-conditioned near a = 1 (d acos = -da / sqrt(1 - a^2)),
+    # so the bound is sqrt(2 * 4 ulp(1)) ~ 1e-3 rad at the maximum pixel, 1e-5 elsewhere (a <= 0.999)
+    f32 = f.astype(np.complex64)
+    p32 = gws.encode(torch.as_tensor(f32, device="cuda"), slm).cpu().numpy()
+    ref32 = O.encode(f32.astype(np.complex128))
+    d = _circ(p32, ref32)
+    a = np.abs(f32) / np.abs(f32).reshape(shape[0], -1).max(1)[:, None, None]
+    assert d.max() < 2e-3
+    assert d[a < 0.999].max() < 2e-5
+    # fixed amplitude scale (clamped above it)
+    s = float(np.abs(f32).max() / 3)
+    d = _circ(gws.encode(torch.as_tensor(f32, device="cuda"), slm, amp_scale=s).cpu().numpy(),
+              O.encode(f32.astype(np.complex128), amp_scale=s))
+    assert d.max() < 2e-3
