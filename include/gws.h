@@ -192,6 +192,24 @@ GWS_API gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm
 GWS_API gws_status gws_encode(const void *field, const gws_slm *slm, const gws_opts *opts, float *phase_out,
                       float amp_scale);
 
+/* Double-phase encoding for callers that cannot allocate device memory: code hosted inside
+ * another application that owns every device allocation, or a real-time display loop that
+ * fixes its memory at start-up and must not call cudaMalloc (which can synchronise the
+ * device) mid-frame.  The paper has no counterpart; this is a deployment variant of
+ * gws_encode with the same arguments and the same result.
+ *   - opts->workspace is not used; prec selects complex64 / complex128 input as in gws_encode.
+ *   - Its scratch (one slot per wavelength for the maximum amplitude) is a fixed array of
+ *     GWS_NOALLOC_MAX_LAMBDA slots inside the library; every GPU that loads the library holds
+ *     it until the process exits.  More wavelengths -> GWS_ERR_INVALID_ARG.
+ *   - The first call on a device looks up the array's device address (set-up, once per
+ *     device, with that device current): make that first call before any stream capture.
+ *   - All calls share the array and each clears it before use: calls that overlap on the GPU
+ *     (other streams, other host threads) race and must be serialised by the caller.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
+#define GWS_NOALLOC_MAX_LAMBDA 16
+GWS_API gws_status gws_encode_noalloc(const void *field, const gws_slm *slm, const gws_opts *opts, float *phase_out,
+                                      float amp_scale);
+
 /* Synchronises opts->stream and returns the device status word of the last call that
  * used this workspace (GWS_OK, GWS_ERR_NONFINITE, GWS_ERR_INVALID_ARG, GWS_ERR_TIMEOUT),
  * then clears it. */

@@ -59,7 +59,7 @@ _lib_lock = threading.Lock()
 EXPORTS = ["gws_opts_default", "gws_status_string", "gws_version", "gws_workspace_size", "gws_prepare",
            "gws_forward", "gws_forward_batched", "gws_backward", "gws_encode", "gws_get_device_status",
            "gws_depth_order", "gws_transmittance", "gws_footprints", "gws_last_launch_count", "gws_autotune",
-           "gws_kernel_time_ms", "gws_footprint_pairs"]
+           "gws_kernel_time_ms", "gws_footprint_pairs", "gws_encode_noalloc"]
 
 
 def lib_path() -> str:
@@ -277,6 +277,20 @@ def encode(field: torch.Tensor, slm: Slm, amp_scale: float = 0.0, out=None, work
     opts.workspace_bytes = ws.numel()
     _check(lib.gws_encode(C.c_void_p(field.data_ptr()), C.byref(slm._c()), C.byref(opts),
                           C.c_void_p(out.data_ptr()), C.c_float(amp_scale)), "gws_encode")
+    return out
+
+
+def encode_noalloc(field: torch.Tensor, slm: Slm, amp_scale: float = 0.0, out=None, **kw) -> torch.Tensor:
+    """gws_encode_noalloc: the same encoding without a caller workspace (fixed in-library scratch)."""
+    lib = load()
+    slm = Slm.of(slm)
+    kw.setdefault("prec", PREC_FP64 if field.dtype == torch.complex128 else PREC_MIXED)
+    opts = make_opts(**kw)
+    field = field.contiguous()
+    if out is None:
+        out = torch.empty((slm.n_lambda, slm.H, slm.W), dtype=torch.float32, device=field.device)
+    _check(lib.gws_encode_noalloc(C.c_void_p(field.data_ptr()), C.byref(slm._c()), C.byref(opts),
+                                  C.c_void_p(out.data_ptr()), C.c_float(amp_scale)), "gws_encode_noalloc")
     return out
 
 
