@@ -638,6 +638,59 @@ void gwso_backward_spectrum(int64_t n, const double *mean, const double *quat, c
     free(T);
 }
 
+/* Order-invariant gradients (Eq. 12) of a subset of Gaussians only: for each input index in
+ * `which`, the same per-Gaussian sums as gwso_backward_spectrum (every frequency of every
+ * wavelength), O(H W L) per Gaussian.  Outputs are per entry of `which`. */
+void gwso_backward_spectrum_at(int64_t n, const double *mean, const double *quat, const double *scale,
+                               const double *opacity, const double *amp, int n_lambda, const double *wavelengths,
+                               int H, int W, double px, double py, int phase_match, const double *gspec,
+                               int64_t n_which, const int64_t *which, double *dmean, double *dquat, double *dscale,
+                               double *dopacity, double *damp) {
+    (void)n;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < n_which; ++q) {
+        const int64_t i = which[q];
+        gauss_t G;
+        load_gaussian(i, mean, quat, scale, opacity, &G);
+        double dmu[3] = {0, 0, 0}, dsu = 0, dsv = 0, G1[3] = {0, 0, 0}, G2[3] = {0, 0, 0}, G3[3] = {0, 0, 0};
+        double dopa = 0.0;
+        for (int l = 0; l < n_lambda; ++l) {
+            double wi = amp[i * n_lambda + l] * opacity[i];
+            double dwl = 0.0;
+            for (int r = 0; r < H; ++r)
+                for (int c = 0; c < W; ++c) {
+                    freq_t f = grid_freq(r, c, H, W, px, py, wavelengths[l]);
+                    if (!f.propagating) continue;
+                    term_t t = gaussian_term(&G, &f, phase_match);
+                    size_t o = ((size_t)l * H + r) * W + c;
+                    double gr = gspec[2 * o], gi = gspec[2 * o + 1];
+                    double kr = gr * t.re + gi * t.im;
+                    double ki = gr * t.im - gi * t.re;
+                    dwl += kr;
+                    double zr = wi * kr, zi = wi * ki;
+                    double fv[3] = {f.fx, f.fy, f.fz};
+                    double d[3] = {f.fx, f.fy, f.fz - f.inv_lam};
+                    for (int k = 0; k < 3; ++k) dmu[k] += TWO_PI * fv[k] * zi;
+                    if (phase_match) dmu[2] -= TWO_PI * f.inv_lam * zi;
+                    dsu += zr * (1.0 / G.su - 4.0 * PI * PI * G.su * t.a * t.a);
+                    dsv += zr * (1.0 / G.sv - 4.0 * PI * PI * G.sv * t.b * t.b);
+                    for (int k = 0; k < 3; ++k) {
+                        G1[k] += zr * (-4.0 * PI * PI * G.su * G.su * t.a) * d[k];
+                        G2[k] += zr * (-4.0 * PI * PI * G.sv * G.sv * t.b) * d[k];
+                        if (t.g != 0.0) G3[k] += zr * fv[k] / t.g;
+                    }
+                }
+            damp[q * n_lambda + l] = opacity[i] * dwl;
+            dopa += amp[i * n_lambda + l] * dwl;
+        }
+        for (int k = 0; k < 3; ++k) dmean[3 * q + k] = dmu[k];
+        dscale[2 * q] = dsu;
+        dscale[2 * q + 1] = dsv;
+        dopacity[q] = dopa;
+        quat_chain(G.qhat, G.qnorm, G1, G2, G3, dquat + 4 * q);
+    }
+}
+
 int gwso_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

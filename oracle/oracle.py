@@ -194,3 +194,21 @@ def backward_field(scene, slm, gfield, blend=BLEND_OIT, phase_match=False, alpha
     """Gradients given dL/d(field): the adjoint DFT, then ``backward_spectrum``."""
     return backward_spectrum(scene, slm, idft_adjoint(gfield, slm.pitch_x, slm.pitch_y), blend, phase_match,
                              alpha_min)
+
+
+def backward_spectrum_at(scene, slm, gspec, which, phase_match=False):
+    """Order-invariant gradients of the Gaussians in `which` only (per entry of `which`)."""
+    mean, quat, scale, opa, amp = _scene_arrays(scene)
+    n = mean.shape[0]
+    wl = _d(slm.wavelengths)
+    g = _cplx(gspec)
+    which = np.ascontiguousarray(which, dtype=np.int64)
+    k = which.shape[0]
+    out = dict(mean=np.zeros((k, 3)), quat=np.zeros((k, 4)), scale=np.zeros((k, 2)), opacity=np.zeros(k),
+               amp=np.zeros((k, slm.n_lambda)))
+    lib().gwso_backward_spectrum_at(C.c_int64(n), _p(mean), _p(quat), _p(scale), _p(opa), _p(amp),
+                                    C.c_int(slm.n_lambda), _p(wl), C.c_int(slm.H), C.c_int(slm.W),
+                                    C.c_double(slm.pitch_x), C.c_double(slm.pitch_y), C.c_int(int(phase_match)),
+                                    _p(g), C.c_int64(k), _p(which), _p(out["mean"]), _p(out["quat"]),
+                                    _p(out["scale"]), _p(out["opacity"]), _p(out["amp"]))
+    return out

@@ -98,6 +98,7 @@ static gws_status exec_fft(const Plan &p, void *data, void *work, int dbl, int d
 struct Layout {
     size_t status, queue, amax, gpre, ampc, dkey0, dkey1, dval0, dval1, skey0, skey1, hist, tsorted, tg, tdata;
     size_t rec64, w64, fkey0, fkey1, fval0, fval1, rec, Rr, ikey0, ikey1, ival0, ival1, icount, invrec, gspec, bacc;
+    size_t pixtab, dT;
     size_t cufft, total;
     int tiles_x, tiles_y, n_tiles, cfg;
 };
@@ -153,6 +154,7 @@ static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *sl
         L->w64 = P.take(8 * n * nl);
         L->fkey0 = L->fkey1 = L->fval0 = L->fval1 = L->rec = L->Rr = 0;
         L->ikey0 = L->ikey1 = L->ival0 = L->ival1 = L->icount = L->invrec = L->gspec = L->bacc = 0;
+        L->pixtab = L->dT = 0;
     } else {
         L->rec64 = L->w64 = 0;
         L->fkey0 = P.take(8 * n_rec);
@@ -169,6 +171,8 @@ static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *sl
         L->invrec = P.take(4 * n_rec);
         L->gspec = P.take(sizeof(float) * 2 * (size_t)nl * slm->H * slm->W);
         L->bacc = P.take(sizeof(double) * 13 * n_rec);
+        L->pixtab = P.take(sizeof(float) * 2 * (size_t)nl * slm->H * slm->W);
+        L->dT = P.take(sizeof(double) * n);
     }
     size_t fft_work = 0;
     if (need_fft_plans) {
@@ -330,7 +334,7 @@ static gws_status run_records(const Front &F, const gws_slm *slm, const gws_opts
     CU(radix_sort<unsigned long long>(k0, k1, v0, v1, n_rec, 0, 32 + seg_bits(n_seg), at<unsigned>(o, L.hist), s));
     Rec *rec = at<Rec>(o, L.rec);
     CU(launch_gather(k0, v0, gp, at<float>(o, L.ampc), F.sorted, F.T_sorted, F.S, n_rec, FP, drop, backward, rec,
-                     at<float>(o, L.Rr), s));
+                     at<float>(o, L.Rr), backward ? at<int>(o, L.invrec) : nullptr, s));
     *rec_out = rec;
     return GWS_OK;
 }
@@ -678,13 +682,87 @@ gws_status gws_footprint_pairs(const gws_gaussians *g, int64_t n, const gws_slm 
 
 gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
                         const void *grad_field, gws_gaussians_grad *out) {
-    (void)g;
-    (void)n;
-    (void)slm;
-    (void)grad_field;
-    (void)out;
+    t_launches = 0;
+    GS(check_slm(slm));
     GS(check_opts(opts));
-    return GWS_ERR_UNSUPPORTED;
+    GS(check_gaussians(g, n));
+    if (!grad_field || !out) return GWS_ERR_INVALID_ARG;
+    if (n > 0 && (!out->mean || !out->quat || !out->scale || !out->opacity || !out->amp)) return GWS_ERR_INVALID_ARG;
+    if (opts->prec != GWS_PREC_MIXED) return GWS_ERR_UNSUPPORTED;
+    if (opts->blend != GWS_BLEND_OIT) return GWS_ERR_UNSUPPORTED;
+    const bool fft = opts->domain == GWS_DOMAIN_FIELD;
+    Layout L;
+    GS(plan_layout(n, 1, slm, opts, &L, fft));
+    GS(check_workspace(opts, L));
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    timers_reset(opts);
+    timer_mark(opts, GWS_TIMER_TOTAL, 0, s);
+    CU(cudaMemsetAsync(at<char>(opts, L.status), 0, 16, s));
+    if (n == 0) return GWS_OK;
+    const int nl = slm->n_lambda, H = slm->H, W = slm->W;
+    const double dfx = 1.0 / (W * slm->pitch_x), dfy = 1.0 / (H * slm->pitch_y);
+    Front F;
+    int64_t ns[1] = {n};
+    GS(run_front(g, ns, 1, slm, opts, L, opts->blend == GWS_BLEND_SORTED_T, &F, s));
+    Rec *rec = nullptr;
+    GS(run_records(F, slm, opts, L, 1, s, &rec));
+    // dL/du_SLM: the adjoint of the centred inverse DFT (dfx dfy x centred forward DFT)
+    const float2 *gsrc = static_cast<const float2 *>(grad_field);
+    if (fft) {
+        float2 *gs = at<float2>(opts, L.gspec);
+        CU(cudaMemcpyAsync(gs, grad_field, sizeof(float2) * (size_t)nl * H * W, cudaMemcpyDeviceToDevice, s));
+        CU(launch_modulate(gs, 0, nl, H, W, 1.0, 1, s));
+        Plan p;
+        GS(get_plan(H, W, nl, 0, &p));
+        timer_mark(opts, GWS_TIMER_FFT, 0, s);
+        GS(exec_fft(p, gs, at<char>(opts, L.cufft), 0, CUFFT_FORWARD, s));
+        timer_mark(opts, GWS_TIMER_FFT, 1, s);
+        CU(launch_modulate(gs, 0, nl, H, W, dfx * dfy, 2, s));
+        gsrc = gs;
+    }
+    InvLam il;
+    std::memset(&il, 0, sizeof il);
+    for (int l = 0; l < nl; ++l) il.v[l] = 1.0 / slm->wavelengths[l];
+    float2 *pixtab = at<float2>(opts, L.pixtab);
+    CU(launch_pixtab(nl, H, W, dfx, dfy, il, pixtab, s));
+    CU(cudaMemsetAsync(at<int>(opts, L.queue), 0, 16, s));
+    BwdArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.rec = rec;
+    a.gspec = gsrc;
+    a.pixtab = pixtab;
+    a.acc = at<double>(opts, L.bacc);
+    a.queue = at<int>(opts, L.queue);
+    a.status = at<int>(opts, L.status);
+    a.segs = F.S;
+    a.H = H;
+    a.W = W;
+    a.tiles_x = bwd_tiles_x(W);
+    a.tiles_y = bwd_tiles_y(H);
+    a.dfx = dfx;
+    a.dfy = dfy;
+    for (int l = 0; l < nl; ++l) a.inv_lam[l] = il.v[l];
+    a.phase_match = opts->phase_match ? 1 : 0;
+    const int B = bwd_block_size();
+    a.n_items = (int)(nl * ((n + B - 1) / B));
+    const int grid = (int)std::min<long long>(a.n_items, (long long)num_sms() * 2);
+    timer_mark(opts, GWS_TIMER_SPLAT_BWD, 0, s);
+    CU(launch_splat_bwd(a, grid, s));
+    timer_mark(opts, GWS_TIMER_SPLAT_BWD, 1, s);
+    GradArgs G;
+    std::memset(&G, 0, sizeof G);
+    G.mean = out->mean;
+    G.quat = out->quat;
+    G.scale = out->scale;
+    G.opacity = out->opacity;
+    G.amp = out->amp;
+    G.dT = nullptr;
+    G.phase_match = opts->phase_match ? 1 : 0;
+    for (int l = 0; l < nl; ++l) G.inv_lam[l] = il.v[l];
+    CU(launch_grad_assemble(at<GPre>(opts, L.gpre), at<float>(opts, L.ampc), F.T_g, at<int>(opts, L.invrec),
+                            at<double>(opts, L.bacc), g->quat, n, nl, G, s));
+    timer_mark(opts, GWS_TIMER_TOTAL, 1, s);
+    return GWS_OK;
 }
 
 gws_status gws_autotune(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,

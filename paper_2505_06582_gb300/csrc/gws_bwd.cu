@@ -1,2 +1,420 @@
-// gws_bwd.cu -- backward splat (placeholder translation unit; filled in by the backward kernels).
-#include "gws_host.h"
+// gws_bwd.cu -- backward of the splat: dL/d(mu, q, s, o, c) from G = dL/du_SLM (PyTorch's
+// complex convention), for the order-invariant sum of Eq. 12 (and the depth-sorted weights
+// with T_i held fixed; the cross terms through T_i are added by gws_tgrad kernels).
+//
+//   dL/dtheta = sum_f Re(conj(G(f)) d u_SLM(f) / dtheta)
+//
+// The spectra are recomputed, never stored.  A work item is a block of BB consecutive
+// records of one wavelength (footprint order, so a block's footprints are alike).  The CTA
+// walks the frequency tiles of the block's footprint union; per tile it stages G and a
+// per-pixel table (f_z - f0_z, log2(1/f_z)) in shared memory with cp.async (zero fill past
+// the grid), culls each record exactly, and one warp takes one record over the tile's
+// 2048 pixels (lanes over pixels), accumulating 16 FP32 partial sums; these are reduced
+// across the warp and merged per tile into 13 FP64 totals per record in shared memory:
+//   TA = sum R a' d,  TB = sum R b' d,  TG = sum sign(g) Re(P0) f,  TI = sum I f,  SI = sum I,
+// with P0 = conj(G) f_z^-1 2^-(a'^2+b'^2) e^{j phi},  R = |g| Re(P0),  I = |g| Im(P0),
+// g = r3.f, d = f - f_r.  A record's totals are only touched by the warp holding it in the
+// current tile, and tiles are visited in a fixed order, so the result is deterministic.
+#include <float.h>
+
+#include "gws_prep.h"
+
+namespace gws {
+
+constexpr int BTW = 64, BTH = 32, BPX = BTW * BTH;
+constexpr int BB = 64;    // records per work item
+constexpr int BNT = 256;  // threads per CTA
+constexpr int NTOT = 13;
+
+int bwd_block_size() { return BB; }
+
+struct BwdShared {
+    float2 g[2][BPX];
+    float2 px[2][BPX];
+    Rec rec[BB];
+    float4 sv[BB][4];
+    double tot[BB][NTOT];
+    float red[BNT / 32][16];
+    unsigned mask[2];
+    int tx0, tx1, ty0, ty1;
+    int item;
+};
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(smem)), "l"(gmem),
+                 "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ bool ellipse_hits_rect_b(float e00, float e01, float e11, float x0, float x1, float y0,
+                                                    float y1) {
+    if (x0 <= 0.f && 0.f <= x1 && y0 <= 0.f && 0.f <= y1) return true;
+    float best = 3.0e38f;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float xe = k ? x1 : x0;
+        const float ys = e11 > 0.f ? fminf(fmaxf(-e01 * xe / e11, y0), y1) : y0;
+        best = fminf(best, e00 * xe * xe + 2.f * e01 * xe * ys + e11 * ys * ys);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float ye = k ? y1 : y0;
+        const float xs = e00 > 0.f ? fminf(fmaxf(-e01 * ye / e00, x0), x1) : x0;
+        best = fminf(best, e00 * xs * xs + 2.f * e01 * xs * ye + e11 * ye * ye);
+    }
+    return best <= 1.001f;
+}
+
+// Sum of v[0..15] over the warp; afterwards lane l holds the total of value l >> 1.
+__device__ __forceinline__ float warp_transpose_reduce16(float v[16], int lane) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool hi = lane & 16;
+        const float send = hi ? v[i] : v[i + 8];
+        const float keep = hi ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool hi = lane & 8;
+        const float send = hi ? v[i] : v[i + 4];
+        const float keep = hi ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool hi = lane & 4;
+        const float send = hi ? v[i] : v[i + 2];
+        const float keep = hi ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool hi = lane & 2;
+        const float send = hi ? v[0] : v[1];
+        const float keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// per-pixel table of the backward tiles: (f_z - f0_z, log2(1 / f_z)); (0, -inf) where evanescent
+__global__ void k_pixtab(int n_lambda, int H, int W, double dfx, double dfy, InvLam inv_lam, float2 *__restrict__ tab) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long hw = (long long)H * W;
+    if (idx >= hw * n_lambda) return;
+    const int l = (int)(idx / hw);
+    const long long pix = idx % hw;
+    const int r = (int)(pix / W), c = (int)(pix % W);
+    const int tx = c / BTW, ty = r / BTH;
+    const int c_lo = tx * BTW, r_lo = ty * BTH;
+    const int c_hi = min(c_lo + BTW, W) - 1, r_hi = min(r_lo + BTH, H) - 1;
+    const double k2 = inv_lam.v[l] * inv_lam.v[l];
+    int c_ref, r_ref;
+    tile_ref(c_lo, c_hi, r_lo, r_hi, H, W, dfx, dfy, k2, c_ref, r_ref);
+    const double f0x = (double)(c_ref - W / 2) * dfx, f0y = (double)(r_ref - H / 2) * dfy;
+    const double f0z = sqrt(fmax(k2 - (f0x * f0x + f0y * f0y), 0.0));
+    const double fx = (double)(c - W / 2) * dfx, fy = (double)(r - H / 2) * dfy;
+    const double rho2 = fx * fx + fy * fy;
+    float2 v;
+    if (rho2 < k2) {
+        const double fz = sqrt(k2 - rho2);
+        v.x = (float)(fz - f0z);
+        v.y = (float)(-log2(fz));
+    } else {
+        v.x = 0.f;
+        v.y = -INFINITY;
+    }
+    tab[idx] = v;
+}
+
+__global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ BwdArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BwdShared &S = *reinterpret_cast<BwdShared *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int L = A.segs.n_lambda;
+    const long long n = A.segs.off[1];  // single scene
+
+    for (;;) {
+        if (tid == 0) S.item = atomicAdd(A.queue, 1);
+        __syncthreads();
+        const int it = S.item;
+        if (it >= A.n_items) break;
+        const int l = it % L, blk = it / L;
+        const long long seg_base = (long long)l * n;
+        const long long k0 = (long long)blk * BB;
+        const int nrec = (int)min((long long)BB, n - k0);
+        const double inv_lam = A.inv_lam[l];
+        const double k2 = inv_lam * inv_lam;
+        {
+            const float4 *src = reinterpret_cast<const float4 *>(A.rec + seg_base + k0);
+            float4 *dst = reinterpret_cast<float4 *>(S.rec);
+            for (int i = tid; i < nrec * 6; i += BNT) dst[i] = src[i];
+        }
+        for (int i = tid; i < BB * NTOT; i += BNT) (&S.tot[0][0])[i] = 0.0;
+        if (tid == 0) {
+            S.tx0 = A.tiles_x;
+            S.tx1 = -1;
+            S.ty0 = A.tiles_y;
+            S.ty1 = -1;
+        }
+        __syncthreads();
+        if (tid < nrec) {
+            const Rec &r = S.rec[tid];
+            const double det = (double)r.e00 * r.e11 - (double)r.e01 * r.e01;
+            int c0 = 0, c1 = A.W - 1, q0 = 0, q1 = A.H - 1;
+            if (det > 0.0) {
+                const double hx = sqrt((double)r.e11 / det) * 1.001, hy = sqrt((double)r.e00 / det) * 1.001;
+                const double cx = hx / A.dfx + 1.0, cy = hy / A.dfy + 1.0;
+                c0 = (int)fmax(0.0, floor(A.W / 2 - cx));
+                c1 = (int)fmin((double)(A.W - 1), ceil(A.W / 2 + cx));
+                q0 = (int)fmax(0.0, floor(A.H / 2 - cy));
+                q1 = (int)fmin((double)(A.H - 1), ceil(A.H / 2 + cy));
+            }
+            atomicMin(&S.tx0, c0 / BTW);
+            atomicMax(&S.tx1, c1 / BTW);
+            atomicMin(&S.ty0, q0 / BTH);
+            atomicMax(&S.ty1, q1 / BTH);
+        }
+        __syncthreads();
+        const int ntx = S.tx1 - S.tx0 + 1, nty = S.ty1 - S.ty0 + 1;
+        const int n_t = (ntx > 0 && nty > 0) ? ntx * nty : 0;
+        const float2 *gsl = A.gspec + (size_t)l * A.H * A.W;
+        const float2 *tsl = A.pixtab + (size_t)l * A.H * A.W;
+
+        auto issue = [&](int t, int buf) {
+            const int tx = S.tx0 + t % ntx, ty = S.ty0 + t / ntx;
+            const int c_lo = tx * BTW, r_lo = ty * BTH;
+#pragma unroll
+            for (int i = 0; i < BPX / BNT; ++i) {
+                const int e = tid + BNT * i;
+                const int r = r_lo + (e >> 6), c = c_lo + (e & 63);
+                const bool ok = r < A.H && c < A.W;
+                const size_t off = ok ? (size_t)r * A.W + c : 0;
+                cp_async8(&S.g[buf][e], gsl + off, ok);
+                cp_async8(&S.px[buf][e], tsl + off, ok);
+            }
+        };
+        if (n_t > 0) issue(0, 0);
+        cp_async_commit();
+        for (int t = 0; t < n_t; ++t) {
+            const int buf = t & 1;
+            if (t + 1 < n_t) issue(t + 1, buf ^ 1);
+            cp_async_commit();
+            cp_async_wait1();
+            __syncthreads();
+            const int tx = S.tx0 + t % ntx, ty = S.ty0 + t / ntx;
+            const int c_lo = tx * BTW, r_lo = ty * BTH;
+            const int c_hi = min(c_lo + BTW, A.W) - 1, r_hi = min(r_lo + BTH, A.H) - 1;
+            int c_ref, r_ref;
+            tile_ref(c_lo, c_hi, r_lo, r_hi, A.H, A.W, A.dfx, A.dfy, k2, c_ref, r_ref);
+            const double f0x = (double)(c_ref - A.W / 2) * A.dfx, f0y = (double)(r_ref - A.H / 2) * A.dfy;
+            const double f0z = sqrt(fmax(k2 - (f0x * f0x + f0y * f0y), 0.0));
+            const double dz0 = f0z - inv_lam;
+            // cull + per-(record, tile) scalars
+            if (tid < BB) {
+                bool pass = false;
+                if (tid < nrec) {
+                    const Rec &r = S.rec[tid];
+                    const float x0 = (float)((double)(c_lo - A.W / 2) * A.dfx);
+                    const float x1 = (float)((double)(c_hi - A.W / 2) * A.dfx);
+                    const float y0 = (float)((double)(r_lo - A.H / 2) * A.dfy);
+                    const float y1 = (float)((double)(r_hi - A.H / 2) * A.dfy);
+                    pass = ellipse_hits_rect_b(r.e00, r.e01, r.e11, x0, x1, y0, y1);
+                    if (pass) {
+                        double cyc = -(f0x * r.mux + f0y * r.muy + f0z * r.muz);
+                        if (A.phase_match) cyc += r.muz * inv_lam;
+                        cyc -= rint(cyc);
+                        cyc *= kTwoPi;
+                        const float fxf = (float)f0x, fyf = (float)f0y, fzf = (float)f0z, dzf = (float)dz0;
+                        S.sv[tid][0] = make_float4(r.r1x, r.r1y, r.r1z, fmaf(r.r1z, dzf, fmaf(r.r1y, fyf, r.r1x * fxf)));
+                        S.sv[tid][1] = make_float4(r.r2x, r.r2y, r.r2z, fmaf(r.r2z, dzf, fmaf(r.r2y, fyf, r.r2x * fxf)));
+                        S.sv[tid][2] = make_float4(r.r3x, r.r3y, r.r3z, fmaf(r.r3z, fzf, fmaf(r.r3y, fyf, r.r3x * fxf)));
+                        S.sv[tid][3] = make_float4(r.mx, r.my, r.mz, (float)cyc);
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, pass);
+                if (lane == 0) S.mask[warp] = bal;
+            }
+            __syncthreads();
+            const float dfxf = (float)A.dfx, dfyf = (float)A.dfy;
+            const float dx0 = (float)(c_lo + lane - c_ref) * dfxf;
+            const float dx1 = (float)(c_lo + lane + 32 - c_ref) * dfxf;
+            const float dyb = (float)(r_lo - r_ref) * dfyf;
+            unsigned long long m = (unsigned long long)S.mask[0] | ((unsigned long long)S.mask[1] << 32);
+            int q = 0;
+            while (m) {
+                const int k = __ffsll((long long)m) - 1;
+                m &= m - 1ull;
+                if ((q++ & (BNT / 32 - 1)) != warp) continue;
+                const float4 Ar = S.sv[k][0], Br = S.sv[k][1], Gr = S.sv[k][2], Mr = S.sv[k][3];
+                const float ac[2] = {fmaf(Ar.x, dx0, Ar.w), fmaf(Ar.x, dx1, Ar.w)};
+                const float bc[2] = {fmaf(Br.x, dx0, Br.w), fmaf(Br.x, dx1, Br.w)};
+                const float gc[2] = {fmaf(Gr.x, dx0, Gr.w), fmaf(Gr.x, dx1, Gr.w)};
+                const float tc[2] = {fmaf(Mr.x, dx0, Mr.w), fmaf(Mr.x, dx1, Mr.w)};
+                float sp[4][2], sz[4], sy[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) sp[u][0] = sp[u][1] = sz[u] = sy[u] = 0.f;
+#pragma unroll 2
+                for (int j = 0; j < 2 * BTH; ++j) {
+                    const int par = j & 1;
+                    const float dy = fmaf((float)(j >> 1), dfyf, dyb);
+                    const float2 gg = S.g[buf][32 * j + lane];
+                    const float2 pt = S.px[buf][32 * j + lane];
+                    const float a = fmaf(Ar.z, pt.x, fmaf(Ar.y, dy, ac[par]));
+                    const float b = fmaf(Br.z, pt.x, fmaf(Br.y, dy, bc[par]));
+                    const float g = fmaf(Gr.z, pt.x, fmaf(Gr.y, dy, gc[par]));
+                    const float tt = fmaf(Mr.z, pt.x, fmaf(Mr.y, dy, tc[par]));
+                    const float e = ex2_approx(-fmaf(a, a, fmaf(b, b, -pt.y)));
+                    const float kr = __fadd_rn(fmaf(tt, 0.15915494309189535f, 12582912.0f), -12582912.0f);
+                    const float ang = fmaf(kr, -6.28318530717958647692f, tt);
+                    const float kc = e * cos_approx(ang), ks = e * sin_approx(ang);
+                    const float p0r = fmaf(gg.x, kc, gg.y * ks);
+                    const float p0i = fmaf(gg.x, ks, -gg.y * kc);
+                    const float ag = fabsf(g);
+                    const float R = ag * p0r, I = ag * p0i;
+                    const float Rg = __int_as_float(__float_as_int(p0r) ^ (__float_as_int(g) & 0x80000000));  // sign(g) p0r
+                    const float Ra = R * a, Rb = R * b;
+                    sp[0][par] += Ra;
+                    sp[1][par] += Rb;
+                    sp[2][par] += Rg;
+                    sp[3][par] += I;
+                    sz[0] = fmaf(Ra, pt.x, sz[0]);
+                    sz[1] = fmaf(Rb, pt.x, sz[1]);
+                    sz[2] = fmaf(Rg, pt.x, sz[2]);
+                    sz[3] = fmaf(I, pt.x, sz[3]);
+                    sy[0] = fmaf(Ra, dy, sy[0]);
+                    sy[1] = fmaf(Rb, dy, sy[1]);
+                    sy[2] = fmaf(Rg, dy, sy[2]);
+                    sy[3] = fmaf(I, dy, sy[3]);
+                }
+                float v[16];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    v[4 * u + 0] = sp[u][0] + sp[u][1];
+                    v[4 * u + 1] = fmaf(dx0, sp[u][0], dx1 * sp[u][1]);
+                    v[4 * u + 2] = sy[u];
+                    v[4 * u + 3] = sz[u];
+                }
+                const float tot = warp_transpose_reduce16(v, lane);
+                if ((lane & 1) == 0) S.red[warp][lane >> 1] = tot;
+                __syncwarp();
+                if (lane < NTOT) {
+                    double add;
+                    if (lane == 12) {
+                        add = (double)S.red[warp][12];
+                    } else {
+                        const int vec = lane / 3, comp = lane % 3;
+                        const double ref = comp == 0 ? f0x : (comp == 1 ? f0y : (vec < 2 ? dz0 : f0z));
+                        add = ref * (double)S.red[warp][4 * vec] + (double)S.red[warp][4 * vec + 1 + comp];
+                    }
+                    S.tot[k][lane] += add;
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+        }
+        cp_async_wait0();
+        __syncthreads();
+        for (int i = tid; i < nrec * NTOT; i += BNT)
+            A.acc[(size_t)(seg_base + k0 + i / NTOT) * NTOT + i % NTOT] = S.tot[i / NTOT][i % NTOT];
+        __syncthreads();
+    }
+}
+
+// dL/d(parameters) per Gaussian from the per-(Gaussian, wavelength) totals
+__global__ void k_grad_assemble(const GPre *__restrict__ gp, const float *__restrict__ ampc,
+                                const double *__restrict__ T_g, const int *__restrict__ invrec,
+                                const double *__restrict__ acc, const float *__restrict__ quat_in, long long n, int L,
+                                GradArgs G) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const GPre &P = gp[g];
+    double r1[3], r2[3], r3[3];
+    quat_cols<double>(P.q, r1, r2, r3);
+    const double su = P.su, sv = P.sv, o = P.o;
+    const double T = T_g ? T_g[g] : 1.0;
+    const double ln2 = 0.69314718055994530942;
+    double dmu[3] = {0, 0, 0}, G1[3] = {0, 0, 0}, G2[3] = {0, 0, 0}, G3[3] = {0, 0, 0};
+    double dsu = 0, dsv = 0, dop = 0, dT = 0;
+    for (int l = 0; l < L; ++l) {
+        const double *t = acc + (size_t)invrec[g * L + l] * NTOT;
+        const double c = ampc[g * L + l];
+        const double Wl = kTwoPi * su * sv * c * o * T;
+        double dr1p[3], dr2p[3], dW = 0;
+        for (int k = 0; k < 3; ++k) {
+            dr1p[k] = -2.0 * ln2 * Wl * t[k];
+            dr2p[k] = -2.0 * ln2 * Wl * t[3 + k];
+            G3[k] += Wl * t[6 + k];
+            dW += r3[k] * t[6 + k];
+            dmu[k] += kTwoPi * Wl * t[9 + k];
+        }
+        if (G.phase_match) dmu[2] -= kTwoPi * G.inv_lam[l] * Wl * t[12];
+        const double ku = kKappa * su, kv = kKappa * sv;
+        for (int k = 0; k < 3; ++k) {
+            G1[k] += ku * dr1p[k];
+            G2[k] += kv * dr2p[k];
+        }
+        dsu += kKappa * (r1[0] * dr1p[0] + r1[1] * dr1p[1] + r1[2] * dr1p[2]);
+        dsv += kKappa * (r2[0] * dr2p[0] + r2[1] * dr2p[1] + r2[2] * dr2p[2]);
+        const double base = kTwoPi * su * sv;  // W = base * c * o * T
+        dsu += kTwoPi * sv * c * o * T * dW;
+        dsv += kTwoPi * su * c * o * T * dW;
+        G.amp[g * L + l] = (float)(base * o * T * dW);
+        dop += base * c * T * dW;
+        dT += base * c * o * dW;
+    }
+    // quaternion: R(qhat), qhat = q / |q|
+    const double w = P.q[0], x = P.q[1], y = P.q[2], z = P.q[3];
+    const double dr1[4][3] = {{0, 2 * z, -2 * y}, {0, 2 * y, 2 * z}, {-4 * y, 2 * x, -2 * w}, {-4 * z, 2 * w, 2 * x}};
+    const double dr2[4][3] = {{-2 * z, 0, 2 * x}, {2 * y, -4 * x, 2 * w}, {2 * x, 0, 2 * z}, {-2 * w, -4 * z, 2 * y}};
+    const double dr3[4][3] = {{2 * y, -2 * x, 0}, {2 * z, -2 * w, -4 * x}, {2 * w, 2 * z, -4 * y}, {2 * x, 2 * y, 0}};
+    double gh[4];
+    for (int m = 0; m < 4; ++m) {
+        gh[m] = 0;
+        for (int k = 0; k < 3; ++k) gh[m] += G1[k] * dr1[m][k] + G2[k] * dr2[m][k] + G3[k] * dr3[m][k];
+    }
+    const double qi[4] = {quat_in[4 * g], quat_in[4 * g + 1], quat_in[4 * g + 2], quat_in[4 * g + 3]};
+    const double qn = sqrt(qi[0] * qi[0] + qi[1] * qi[1] + qi[2] * qi[2] + qi[3] * qi[3]);
+    const double proj = gh[0] * w + gh[1] * x + gh[2] * y + gh[3] * z;
+    const double qh[4] = {w, x, y, z};
+    for (int m = 0; m < 4; ++m) G.quat[4 * g + m] = (float)((gh[m] - proj * qh[m]) / qn);
+    for (int k = 0; k < 3; ++k) G.mean[3 * g + k] = dmu[k];
+    G.scale[2 * g] = (float)dsu;
+    G.scale[2 * g + 1] = (float)dsv;
+    G.opacity[g] = (float)dop;
+    if (G.dT) G.dT[g] = dT;
+}
+
+cudaError_t launch_pixtab(int n_lambda, int H, int W, double dfx, double dfy, const InvLam &il, float2 *tab,
+                          cudaStream_t s) {
+    const long long n = (long long)n_lambda * H * W;
+    k_pixtab<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n_lambda, H, W, dfx, dfy, il, tab);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+int bwd_tiles_x(int W) { return (W + BTW - 1) / BTW; }
+int bwd_tiles_y(int H) { return (H + BTH - 1) / BTH; }
+
+cudaError_t launch_splat_bwd(const BwdArgs &a, int grid, cudaStream_t s) {
+    const size_t smem = sizeof(BwdShared);
+    cudaError_t e = cudaFuncSetAttribute(k_splat_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_splat_bwd<<<grid, BNT, smem, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_assemble(const GPre *gp, const float *ampc, const double *T_g, const int *invrec,
+                                 const double *acc, const float *quat_in, long long n, int L, const GradArgs &G,
+                                 cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_grad_assemble<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(gp, ampc, T_g, invrec, acc, quat_in, n, L, G);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace gws

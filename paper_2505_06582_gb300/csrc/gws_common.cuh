@@ -38,7 +38,8 @@ struct alignas(16) GPre {
 // multiple of 16 so that 1-D bulk copies of whole chunks stay 16-byte aligned).
 //   r1' = kappa s_u r1, r2' = kappa s_v r2 (so that 2^-(a'^2 + b'^2) is the Gaussian factor),
 //   r3' = W r3 (forward) or r3 (backward), W = 2 pi s_u s_v c o T (Eq. 10 amplitude x Eq. 12 weight),
-//   m = -mu in FP32 for the in-tile phase deltas, mu in FP64 for the per-tile phase anchor,
+//   m = -2 pi mu in FP32 for the in-tile phase deltas (radians), mu in FP64 for the per-tile
+//   phase anchor,
 //   e = footprint ellipse normalised to 1.
 struct alignas(16) Rec {
     float r1x, r1y, r1z, r2x;
@@ -175,6 +176,19 @@ __device__ __forceinline__ void bulk_g2s(void *smem_dst, const void *gmem_src, u
             smem_u32(smem_dst)),
         "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Reference frequency of a tile: the centre of its valid pixels, or -- when that is
+// evanescent -- its pixel nearest to f = 0, so that |f - f0| stays within the tile.
+__host__ __device__ __forceinline__ void tile_ref(int c_lo, int c_hi, int r_lo, int r_hi, int H, int W, double dfx,
+                                                  double dfy, double k2, int &c_ref, int &r_ref) {
+    c_ref = (c_lo + c_hi + 1) / 2;
+    r_ref = (r_lo + r_hi + 1) / 2;
+    const double fx = (double)(c_ref - W / 2) * dfx, fy = (double)(r_ref - H / 2) * dfy;
+    if (fx * fx + fy * fy >= k2) {
+        c_ref = W / 2 < c_lo ? c_lo : (W / 2 > c_hi ? c_hi : W / 2);
+        r_ref = H / 2 < r_lo ? r_lo : (H / 2 > r_hi ? r_hi : H / 2);
+    }
 }
 
 // Centred-DFT modulation angle, in cycles: ((a * b) mod n) / n, exact integer reduction.

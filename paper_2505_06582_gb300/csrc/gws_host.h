@@ -80,9 +80,10 @@ cudaError_t launch_splat_fp64(const Splat64Args &a, cudaStream_t s);
 // ---- backward ---------------------------------------------------------------------------
 
 struct BwdArgs {
-    const Rec *rec;      // backward records (r3 unit, W separate), segment-major
-    const float2 *gspec; // dL/du_SLM per scene [scene][lambda][H][W] (contiguous, natural layout)
-    double *acc;         // [n_records][13] totals
+    const Rec *rec;         // backward records (r3 unit, W separate), segment-major (single scene)
+    const float2 *gspec;    // dL/du_SLM [lambda][H][W], natural layout
+    const float2 *pixtab;   // [lambda][H][W]: (f_z - f0_z of the pixel's tile, log2(1/f_z))
+    double *acc;            // [n_records][13] totals
     int *queue;
     int *status;
     Segs segs;
@@ -90,12 +91,29 @@ struct BwdArgs {
     double dfx, dfy;
     double inv_lam[GWS_MAX_LAMBDA];
     int phase_match;
-    int n_items;        // (segment, block) work items
-    const int *item_seg;
-    const int *item_first;
-    unsigned long long timeout;
+    int n_items;            // (wavelength, block of records) work items
 };
+
+struct GradArgs {
+    double *mean;
+    float *quat, *scale, *opacity, *amp;
+    double *dT;             // optional dL/dT_i (depth-sorted mode)
+    int phase_match;
+    double inv_lam[GWS_MAX_LAMBDA];
+};
+
+struct InvLam {
+    double v[GWS_MAX_LAMBDA];
+};
+
+cudaError_t launch_pixtab(int n_lambda, int H, int W, double dfx, double dfy, const InvLam &il, float2 *tab,
+                          cudaStream_t s);
 cudaError_t launch_splat_bwd(const BwdArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_grad_assemble(const GPre *gp, const float *ampc, const double *T_g, const int *invrec,
+                                 const double *acc, const float *quat_in, long long n, int L, const GradArgs &G,
+                                 cudaStream_t s);
 int bwd_block_size();
+int bwd_tiles_x(int W);
+int bwd_tiles_y(int H);
 
 }  // namespace gws

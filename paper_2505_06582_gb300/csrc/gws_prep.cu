@@ -267,7 +267,7 @@ __global__ void k_gather(const unsigned long long *__restrict__ key, const unsig
                          const GPre *__restrict__ gp, const float *__restrict__ ampc,
                          const unsigned *__restrict__ sorted, const double *__restrict__ T_sorted, Segs S,
                          long long n_rec, FootParams F, int drop_zero, int backward, Rec *__restrict__ rec,
-                         float *__restrict__ Rr) {
+                         float *__restrict__ Rr, int *__restrict__ invrec) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_rec) return;
     const int seg = (int)(key[k] >> 32);
@@ -291,9 +291,9 @@ __global__ void k_gather(const unsigned long long *__restrict__ key, const unsig
     r.r3x = w3 * r3[0];
     r.r3y = w3 * r3[1];
     r.r3z = w3 * r3[2];
-    r.mx = (float)(-G.mu[0]);
-    r.my = (float)(-G.mu[1]);
-    r.mz = (float)(-G.mu[2]);
+    r.mx = (float)(-kTwoPi * G.mu[0]);  // phase deltas in radians: -2 pi mu . (f - f0)
+    r.my = (float)(-kTwoPi * G.mu[1]);
+    r.mz = (float)(-kTwoPi * G.mu[2]);
     r.e00 = f.e00;
     r.e01 = f.e01;
     r.e11 = f.e11;
@@ -305,6 +305,7 @@ __global__ void k_gather(const unsigned long long *__restrict__ key, const unsig
     r.pad = 0;
     rec[k] = r;
     Rr[k] = (drop_zero && W == 0.f) ? -1.f : f.R;
+    if (invrec) invrec[(size_t)g * S.n_lambda + l] = (int)k;
 }
 
 // inspection: footprint ellipse per input Gaussian for wavelength l
@@ -550,10 +551,11 @@ cudaError_t launch_foot_keys(const GPre *gp, const float *ampc, const unsigned *
 
 cudaError_t launch_gather(const unsigned long long *key, const unsigned *val, const GPre *gp, const float *ampc,
                           const unsigned *sorted, const double *T_sorted, const Segs &S, long long n_rec,
-                          const FootParams &F, int drop_zero, int backward, Rec *rec, float *Rr, cudaStream_t s) {
+                          const FootParams &F, int drop_zero, int backward, Rec *rec, float *Rr, int *invrec,
+                          cudaStream_t s) {
     if (n_rec <= 0) return cudaSuccess;
     k_gather<<<nblk(n_rec, 256), 256, 0, s>>>(key, val, gp, ampc, sorted, T_sorted, S, n_rec, F, drop_zero, backward,
-                                               rec, Rr);
+                                               rec, Rr, invrec);
     count_launches(1);
     return cudaGetLastError();
 }

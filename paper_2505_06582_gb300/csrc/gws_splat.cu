@@ -12,9 +12,10 @@
 // Precision: the phase -f.mu reaches ~2e4 cycles.  Per (record, tile) it is split into an
 // FP64 anchor at the tile's reference frequency f0, reduced mod 1 in FP64, plus FP32
 // deltas (f - f0).mu inside the tile (|.| < ~20 cycles); the FP32 phase is reduced to
-// [-1/2, 1/2] cycle before sin/cos.  f0 is the centre of the tile's valid pixels; f_z and
-// f_z - f0_z are formed in FP64 once per pixel and item.  Per-chunk FP32 sums are merged
-// into a TwoSum-compensated FP32 total.
+// [-pi, pi] before sin/cos (the record carries -2 pi mu, the anchor is in radians).  f0 is
+// the centre of the tile's valid pixels; f_z and f_z - f0_z are formed in FP64 once per pixel
+// and item, and 1/f_z enters as log2(1/f_z) inside the exponent.  Per-chunk FP32 sums are
+// merged into a TwoSum-compensated FP32 total.
 #include "gws_host.h"
 
 namespace gws {
@@ -86,14 +87,8 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
         const double k2 = inv_lam * inv_lam;
         // reference frequency f0 of the tile: the centre of its valid pixels, or -- if that is
         // evanescent -- its pixel nearest to f = 0, so that every |f - f0| stays within the tile
-        int c_ref = (c_lo + c_hi + 1) / 2, r_ref = (r_lo + r_hi + 1) / 2;
-        {
-            const double fx = (double)(c_ref - A.W / 2) * A.dfx, fy = (double)(r_ref - A.H / 2) * A.dfy;
-            if (fx * fx + fy * fy >= k2) {
-                c_ref = min(max(A.W / 2, c_lo), c_hi);
-                r_ref = min(max(A.H / 2, r_lo), r_hi);
-            }
-        }
+        int c_ref, r_ref;
+        tile_ref(c_lo, c_hi, r_lo, r_hi, A.H, A.W, A.dfx, A.dfy, k2, c_ref, r_ref);
         const double f0x = (double)(c_ref - A.W / 2) * A.dfx, f0y = (double)(r_ref - A.H / 2) * A.dfy;
         const double f0z = sqrt(fmax(k2 - (f0x * f0x + f0y * f0y), 0.0));
         const float f0xf = (float)f0x, f0yf = (float)f0y, f0zf = (float)f0z, dz0f = (float)(f0z - inv_lam);
@@ -104,7 +99,7 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
         const float dfxf = (float)A.dfx;
         const float dy = (float)((double)(prow - r_ref) * A.dfy);
         const double fyd = (double)(prow - A.H / 2) * A.dfy;
-        float dx[PX], dz[PX], ifz[PX];
+        float dx[PX], dz[PX], lfz[PX];
 #pragma unroll
         for (int p = 0; p < PX; ++p) {
             const int col = pcol0 + p;
@@ -113,7 +108,7 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
             const double rho2 = fxd * fxd + fyd * fyd;
             const bool ok = prow < A.H && col < A.W && rho2 < k2;
             const double fz = ok ? sqrt(k2 - rho2) : 1.0;
-            ifz[p] = ok ? (float)(1.0 / fz) : 0.f;
+            lfz[p] = ok ? (float)(-log2(fz)) : -INFINITY;  // log2(1 / f_z), folded into the exponent
             dz[p] = ok ? (float)(fz - f0z) : 0.f;
         }
         // tile rectangle (pixel-centre frequencies of the valid pixels) for the cull
@@ -164,6 +159,7 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
                         double cyc = -(f0x * r.mux + f0y * r.muy + f0z * r.muz);
                         if (A.phase_match) cyc += r.muz * inv_lam;
                         cyc -= rint(cyc);
+                        cyc *= kTwoPi;  // radians
                         const float a0 = fmaf(r.r1z, dz0f, fmaf(r.r1y, f0yf, r.r1x * f0xf));
                         const float b0 = fmaf(r.r2z, dz0f, fmaf(r.r2y, f0yf, r.r2x * f0xf));
                         const float g0 = fmaf(r.r3z, f0zf, fmaf(r.r3y, f0yf, r.r3x * f0xf));
@@ -206,10 +202,11 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
                     const float b = fmaf(Br.z, dz[p], fmaf(Br.x, dx[p], br));
                     const float g = fmaf(Gr.z, dz[p], fmaf(Gr.x, dx[p], gr));
                     const float t = fmaf(Mr.z, dz[p], fmaf(Mr.x, dx[p], tr));
-                    const float e = ex2_approx(-fmaf(a, a, b * b));
-                    const float amp = fabsf(g) * ifz[p] * e;
-                    // t - round(t) on the FP32 pipe (|t| < 2^22): adding and removing 1.5 * 2^23
-                    const float ang = (t - (__fadd_rn(t, 12582912.0f) - 12582912.0f)) * 6.28318530717958647692f;
+                    // |g| / f_z 2^-(a^2 + b^2) = |g| 2^-(a^2 + b^2 - log2(1/f_z))
+                    const float amp = fabsf(g) * ex2_approx(-fmaf(a, a, fmaf(b, b, -lfz[p])));
+                    // t (radians) minus 2 pi round(t / 2 pi), rounding on the FP32 pipe (+-1.5 * 2^23)
+                    const float kr = __fadd_rn(fmaf(t, 0.15915494309189535f, 12582912.0f), -12582912.0f);
+                    const float ang = fmaf(kr, -6.28318530717958647692f, t);
                     acc_re[p] = fmaf(amp, cos_approx(ang), acc_re[p]);
                     acc_im[p] = fmaf(amp, sin_approx(ang), acc_im[p]);
                 }

@@ -477,3 +477,13 @@ def test_t13_gradients_agree_with_torch_autograd_restatement():
     L.backward()
     for k in t:
         assert rel_l2(g[k], t[k].grad.numpy()) < 1e-9, k
+
+
+def test_subset_backward_equals_full_backward():
+    slm = SLM(18, 22, 8e-6, 8e-6, (638e-9, 450e-9))
+    sc = uniform_scene(41, 6, slm, scale_median_px=2.0)
+    G = random_field(6, (2, 18, 22))
+    full = O.backward_spectrum(sc, slm, G)
+    sub = O.backward_spectrum_at(sc, slm, G, [4, 1])
+    for k in full:
+        assert np.allclose(sub[k], full[k][[4, 1]], rtol=1e-13, atol=0), k
