@@ -191,6 +191,9 @@ def run_ours(args):
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     gws.prepare(S)
     ws = torch.empty(gws.workspace_size([g.n], S, gws.make_opts()), dtype=torch.uint8, device=dev)
+    # autotune the splat tile on a strided 10% sample of the scene (outside the timed region)
+    sub = gws.Gaussians(*(getattr(g, k)[::10].contiguous() for k in ("mean", "quat", "scale", "opacity", "amp")))
+    tile_cfg = gws.autotune(sub, S, workspace=ws)
     field = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.complex64, device=dev)
     phase = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.float32, device=dev)
     timers = dict(debug_flags=gws.DEBUG_TIME_KERNELS)
@@ -301,7 +304,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_gaussians": g.n, "H": S.H, "W": S.W, "n_lambda": S.n_lambda,
                        "pitch_m": S.pitch_x, "blend": "oit", "precision": "mixed", "trunc_eps": 1e-5,
-                       "step": "forward+encode" + ("+backward" if have_bwd else ""),
+                       "step": "forward+encode" + ("+backward" if have_bwd else ""), "tile_cfg": tile_cfg,
                        "l2": "flushed before each timed step (512 MB write)", "parallelism": f"replicas x{world}"},
             "fwd_holograms_per_s": world * 1000.0 / fwd_ms if have_bwd else value,
             "pairs": {"dense_per_hologram": dense, "algorithmic_per_hologram": pairs,

@@ -161,9 +161,10 @@ GWS_API int gws_version(void);
 GWS_API gws_status gws_workspace_size(const int64_t *n, int n_scenes, const gws_slm *slm, const gws_opts *opts,
                               size_t *bytes);
 
-/* Creates the cuFFT plans for this grid (batch n_lambda and n_lambda * n_scenes) and
- * selects the CUDA device of the current context.  May allocate (inside cuFFT).  Call it
- * before capturing gws_* calls into a CUDA graph. */
+/* Per-device set-up for this grid on the current device: creates the cuFFT plans (batch
+ * n_lambda; complex64 and, for FP64, complex128) and sets the kernels' shared-memory
+ * attributes.  May allocate (inside cuFFT).  Call it before capturing gws_* calls into a
+ * CUDA graph. */
 GWS_API gws_status gws_prepare(const gws_slm *slm, const gws_opts *opts, int n_scenes);
 
 /* Forward [Eq. 10, Eq. 12 or Eq. 5-6, Eq. 3]: field_out = centred inverse DFT of u_SLM
@@ -181,7 +182,9 @@ GWS_API gws_status gws_forward_batched(const gws_gaussians *scenes, const int64_
 /* Backward (MIXED only): given grad_field = dL/d(field) in PyTorch's complex convention
  * (dL/dRe + j dL/dIm), complex64 [n_lambda][H][W] (or dL/du_SLM with domain SPECTRUM),
  * writes dL/d(mean, quat, scale, opacity, amp) into out (device, same layout as the
- * inputs; every array is overwritten).  The spectra are recomputed, never stored. */
+ * inputs; every array is overwritten).  The spectra are recomputed, never stored.  In
+ * SORTED_T mode the gradients include the cross terms through T_i = prod (1 - alpha_j(mu_i))
+ * (Eq. 5-6 with Eq. 2; the set of factors above t_eps is held fixed). */
 GWS_API gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
                         const void *grad_field, gws_gaussians_grad *out);
 
@@ -244,9 +247,11 @@ GWS_API gws_status gws_footprint_pairs(const gws_gaussians *g, int64_t n, const 
 /* Number of kernel launches the last forward / backward / encode issued (host counter). */
 GWS_API int gws_last_launch_count(void);
 
-/* Runs each splat tile configuration on this problem, keeps the fastest for this
- * (H, W, n_lambda, n) class in an in-process table and returns its id in *best_cfg.
- * Synchronises the stream; not capturable. */
+/* Autotuner of the MIXED splat: runs each tile configuration (64x32, 32x32, 128x16
+ * frequencies per CTA tile) twice on this scene with field_scratch (complex64
+ * [n_lambda][H][W]) as output, times the splat with CUDA events, and keeps the fastest for
+ * this (H, W, n_lambda) in an in-process table used whenever opts.tile_cfg == 0.  Returns
+ * its id in *best_cfg.  Synchronises the stream; not capturable. */
 GWS_API gws_status gws_autotune(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
                         void *field_scratch, int *best_cfg);
 

@@ -98,7 +98,7 @@ static gws_status exec_fft(const Plan &p, void *data, void *work, int dbl, int d
 struct Layout {
     size_t status, queue, amax, gpre, ampc, dkey0, dkey1, dval0, dval1, skey0, skey1, hist, tsorted, tg, tdata;
     size_t rec64, w64, fkey0, fkey1, fval0, fval1, rec, Rr, ikey0, ikey1, ival0, ival1, icount, invrec, gspec, bacc;
-    size_t pixtab, dT;
+    size_t pixtab, dT, tq;
     size_t cufft, total;
     int tiles_x, tiles_y, n_tiles, cfg;
 };
@@ -114,10 +114,16 @@ struct Planner {
     }
 };
 
-static int default_cfg(const gws_opts *o) {
+// tile configuration chosen by gws_autotune per grid class (H, W, n_lambda)
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, int> g_tuned;
+
+static int default_cfg(const gws_opts *o, const gws_slm *slm) {
     int c = o->tile_cfg;
-    if (c < 1 || c > n_tile_cfgs()) c = 1;
-    return c;
+    if (c >= 1 && c <= n_tile_cfgs()) return c;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(std::make_tuple(slm->H, slm->W, slm->n_lambda));
+    return it != g_tuned.end() ? it->second : 1;
 }
 
 static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *slm, const gws_opts *o, Layout *L,
@@ -126,12 +132,19 @@ static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *sl
     const int nl = slm->n_lambda;
     const long long n = std::max<long long>(n_total, 1);
     const long long n_rec = n * nl;
-    L->cfg = default_cfg(o);
+    L->cfg = default_cfg(o, slm);
     const TileCfg tc = tile_cfg(L->cfg);
     L->tiles_x = (slm->W + tc.tw - 1) / tc.tw;
     L->tiles_y = (slm->H + tc.th - 1) / tc.th;
     L->n_tiles = L->tiles_x * L->tiles_y;
-    const long long n_items = (long long)n_scenes * nl * L->n_tiles;
+    // item arrays sized for the configuration with the most tiles, so that a later tuning
+    // never outgrows a workspace sized earlier
+    long long max_tiles = 0;
+    for (int c = 1; c <= n_tile_cfgs(); ++c) {
+        const TileCfg t = tile_cfg(c);
+        max_tiles = std::max(max_tiles, (long long)((slm->W + t.tw - 1) / t.tw) * ((slm->H + t.th - 1) / t.th));
+    }
+    const long long n_items = (long long)n_scenes * nl * max_tiles;
 
     L->status = P.take(16);
     L->queue = P.take(16);
@@ -147,6 +160,7 @@ static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *sl
     L->tsorted = P.take(8 * n);
     L->tg = P.take(8 * n);
     L->tdata = P.take(sizeof(TData) * n);
+    L->tq = P.take(sizeof(TQuery) * n);
     size_t hist_words = std::max(sort_hist_words(n), sort_hist_words(std::max(n_rec, n_items)));
     L->hist = P.take(4 * hist_words);
     if (o->prec == GWS_PREC_FP64) {
@@ -301,7 +315,7 @@ static gws_status run_front(const gws_gaussians *scenes, const int64_t *n, int n
         F->T_sorted = at<double>(o, L.tsorted);
         F->T_g = at<double>(o, L.tg);
         CU(launch_transmittance(gp, dv0, F->S, nt, (double)o->alpha_min, at<TData>(o, L.tdata), F->T_sorted, F->T_g,
-                                s));
+                                at<TQuery>(o, L.tq), s));
     }
     return GWS_OK;
 }
@@ -510,7 +524,10 @@ gws_status gws_prepare(const gws_slm *slm, const gws_opts *opts, int n_scenes) {
     if (n_scenes < 1 || n_scenes > GWS_MAX_SCENES) return GWS_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return GWS_ERR_CUDA;
+    CU(prepare_splat_kernels());
+    CU(prepare_bwd_kernels());
     Plan p;
+    GS(get_plan(slm->H, slm->W, slm->n_lambda, 0, &p));
     return get_plan(slm->H, slm->W, slm->n_lambda, opts->prec == GWS_PREC_FP64, &p);
 }
 
@@ -689,7 +706,7 @@ gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, c
     if (!grad_field || !out) return GWS_ERR_INVALID_ARG;
     if (n > 0 && (!out->mean || !out->quat || !out->scale || !out->opacity || !out->amp)) return GWS_ERR_INVALID_ARG;
     if (opts->prec != GWS_PREC_MIXED) return GWS_ERR_UNSUPPORTED;
-    if (opts->blend != GWS_BLEND_OIT) return GWS_ERR_UNSUPPORTED;
+    const bool sorted_t = opts->blend == GWS_BLEND_SORTED_T;
     const bool fft = opts->domain == GWS_DOMAIN_FIELD;
     Layout L;
     GS(plan_layout(n, 1, slm, opts, &L, fft));
@@ -756,24 +773,55 @@ gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, c
     G.scale = out->scale;
     G.opacity = out->opacity;
     G.amp = out->amp;
-    G.dT = nullptr;
+    G.dT = sorted_t ? at<double>(opts, L.dT) : nullptr;
     G.phase_match = opts->phase_match ? 1 : 0;
     for (int l = 0; l < nl; ++l) G.inv_lam[l] = il.v[l];
     CU(launch_grad_assemble(at<GPre>(opts, L.gpre), at<float>(opts, L.ampc), F.T_g, at<int>(opts, L.invrec),
                             at<double>(opts, L.bacc), g->quat, n, nl, G, s));
+    if (sorted_t)  // cross terms through T_i (Eq. 5-6 reading): on the query's mean and on every front Gaussian
+        CU(launch_tgrad(at<TData>(opts, L.tdata), at<TQuery>(opts, L.tq), at<GPre>(opts, L.gpre), F.sorted,
+                        at<double>(opts, L.dT), g->quat, F.S, n, (double)opts->alpha_min, out->mean, out->quat,
+                        out->scale, out->opacity, s));
     timer_mark(opts, GWS_TIMER_TOTAL, 1, s);
     return GWS_OK;
 }
 
 gws_status gws_autotune(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
                         void *field_scratch, int *best_cfg) {
-    (void)g;
-    (void)n;
-    (void)slm;
-    (void)field_scratch;
-    if (!best_cfg) return GWS_ERR_INVALID_ARG;
+    if (!best_cfg || !field_scratch) return GWS_ERR_INVALID_ARG;
+    GS(check_slm(slm));
     GS(check_opts(opts));
-    *best_cfg = 1;
+    GS(check_gaussians(g, n));
+    if (opts->prec != GWS_PREC_MIXED || n == 0) {
+        *best_cfg = 1;
+        return GWS_OK;
+    }
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    float best_ms = 3.0e38f;
+    int best = 1;
+    for (int c = 1; c <= n_tile_cfgs(); ++c) {
+        gws_opts o = *opts;
+        o.tile_cfg = c;
+        o.domain = GWS_DOMAIN_SPECTRUM;
+        o.debug_flags = GWS_DEBUG_TIME_KERNELS;
+        float ms = 3.0e38f;
+        for (int rep = 0; rep < 2; ++rep) {  // the first run warms caches and the instruction cache
+            GS(gws_forward(g, n, slm, &o, field_scratch));
+            const float t = gws_kernel_time_ms(GWS_TIMER_SPLAT_FWD);
+            if (t < 0) return GWS_ERR_CUDA;
+            ms = t;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    CU(cudaStreamSynchronize(s));
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[std::make_tuple(slm->H, slm->W, slm->n_lambda)] = best;
+    }
+    *best_cfg = best;
     return GWS_OK;
 }
 

@@ -22,20 +22,28 @@
 namespace gws {
 
 constexpr int BTW = 64, BTH = 32, BPX = BTW * BTH;
-constexpr int BB = 64;    // records per work item
+constexpr int BB = 128;   // records per work item
 constexpr int BNT = 256;  // threads per CTA
 constexpr int NTOT = 13;
 
 int bwd_block_size() { return BB; }
+
+struct TileConst {  // geometry of the current tile, computed once by thread 0
+    double f0x, f0y, f0z, dz0;
+    float x0, x1, y0, y1;
+    int c_lo, r_lo, c_ref, r_ref;
+};
 
 struct BwdShared {
     float2 g[2][BPX];
     float2 px[2][BPX];
     Rec rec[BB];
     float4 sv[BB][4];
+    int2 rows[BB];  // per surviving record: the tile rows [x, y] its footprint's bounding box reaches
     double tot[BB][NTOT];
     float red[BNT / 32][16];
-    unsigned mask[2];
+    unsigned mask[BB / 32];
+    TileConst tc;
     int tx0, tx1, ty0, ty1;
     int item;
 };
@@ -203,27 +211,43 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
             const int buf = t & 1;
             if (t + 1 < n_t) issue(t + 1, buf ^ 1);
             cp_async_commit();
+            if (tid == 0) {
+                TileConst &T = S.tc;
+                const int tx = S.tx0 + t % ntx, ty = S.ty0 + t / ntx;
+                T.c_lo = tx * BTW;
+                T.r_lo = ty * BTH;
+                const int c_hi = min(T.c_lo + BTW, A.W) - 1, r_hi = min(T.r_lo + BTH, A.H) - 1;
+                tile_ref(T.c_lo, c_hi, T.r_lo, r_hi, A.H, A.W, A.dfx, A.dfy, k2, T.c_ref, T.r_ref);
+                T.f0x = (double)(T.c_ref - A.W / 2) * A.dfx;
+                T.f0y = (double)(T.r_ref - A.H / 2) * A.dfy;
+                T.f0z = sqrt(fmax(k2 - (T.f0x * T.f0x + T.f0y * T.f0y), 0.0));
+                T.dz0 = T.f0z - inv_lam;
+                T.x0 = (float)((double)(T.c_lo - A.W / 2) * A.dfx);
+                T.x1 = (float)((double)(c_hi - A.W / 2) * A.dfx);
+                T.y0 = (float)((double)(T.r_lo - A.H / 2) * A.dfy);
+                T.y1 = (float)((double)(r_hi - A.H / 2) * A.dfy);
+            }
             cp_async_wait1();
             __syncthreads();
-            const int tx = S.tx0 + t % ntx, ty = S.ty0 + t / ntx;
-            const int c_lo = tx * BTW, r_lo = ty * BTH;
-            const int c_hi = min(c_lo + BTW, A.W) - 1, r_hi = min(r_lo + BTH, A.H) - 1;
-            int c_ref, r_ref;
-            tile_ref(c_lo, c_hi, r_lo, r_hi, A.H, A.W, A.dfx, A.dfy, k2, c_ref, r_ref);
-            const double f0x = (double)(c_ref - A.W / 2) * A.dfx, f0y = (double)(r_ref - A.H / 2) * A.dfy;
-            const double f0z = sqrt(fmax(k2 - (f0x * f0x + f0y * f0y), 0.0));
-            const double dz0 = f0z - inv_lam;
+            const int c_lo = S.tc.c_lo, r_lo = S.tc.r_lo, c_ref = S.tc.c_ref, r_ref = S.tc.r_ref;
             // cull + per-(record, tile) scalars
             if (tid < BB) {
                 bool pass = false;
                 if (tid < nrec) {
                     const Rec &r = S.rec[tid];
-                    const float x0 = (float)((double)(c_lo - A.W / 2) * A.dfx);
-                    const float x1 = (float)((double)(c_hi - A.W / 2) * A.dfx);
-                    const float y0 = (float)((double)(r_lo - A.H / 2) * A.dfy);
-                    const float y1 = (float)((double)(r_hi - A.H / 2) * A.dfy);
-                    pass = ellipse_hits_rect_b(r.e00, r.e01, r.e11, x0, x1, y0, y1);
+                    const double f0x = S.tc.f0x, f0y = S.tc.f0y, f0z = S.tc.f0z, dz0 = S.tc.dz0;
+                    pass = ellipse_hits_rect_b(r.e00, r.e01, r.e11, S.tc.x0, S.tc.x1, S.tc.y0, S.tc.y1);
                     if (pass) {
+                        // rows of the tile inside the footprint's bounding box
+                        const float det = r.e00 * r.e11 - r.e01 * r.e01;
+                        int rlo = 0, rhi = BTH - 1;
+                        if (det > 0.f) {
+                            const float hy = sqrtf(r.e00 / det) * 1.001f + 1e-3f * (float)A.dfy;
+                            const float dfyf = (float)A.dfy;
+                            rlo = max(0, (int)ceilf((-hy - S.tc.y0) / dfyf));
+                            rhi = min(BTH - 1, (int)floorf((hy - S.tc.y0) / dfyf));
+                        }
+                        S.rows[tid] = make_int2(rlo, rhi);
                         double cyc = -(f0x * r.mux + f0y * r.muy + f0z * r.muz);
                         if (A.phase_match) cyc += r.muz * inv_lam;
                         cyc -= rint(cyc);
@@ -243,12 +267,15 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
             const float dx0 = (float)(c_lo + lane - c_ref) * dfxf;
             const float dx1 = (float)(c_lo + lane + 32 - c_ref) * dfxf;
             const float dyb = (float)(r_lo - r_ref) * dfyf;
-            unsigned long long m = (unsigned long long)S.mask[0] | ((unsigned long long)S.mask[1] << 32);
             int q = 0;
-            while (m) {
-                const int k = __ffsll((long long)m) - 1;
-                m &= m - 1ull;
+            for (int wi = 0; wi < BB / 32; ++wi) {
+              unsigned m = S.mask[wi];
+              while (m) {
+                const int k = wi * 32 + __ffs(m) - 1;
+                m &= m - 1u;
                 if ((q++ & (BNT / 32 - 1)) != warp) continue;
+                const int2 rr = S.rows[k];
+                const int row_lo = rr.x & 0xffff, row_hi = rr.y;
                 const float4 Ar = S.sv[k][0], Br = S.sv[k][1], Gr = S.sv[k][2], Mr = S.sv[k][3];
                 const float ac[2] = {fmaf(Ar.x, dx0, Ar.w), fmaf(Ar.x, dx1, Ar.w)};
                 const float bc[2] = {fmaf(Br.x, dx0, Br.w), fmaf(Br.x, dx1, Br.w)};
@@ -257,38 +284,43 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                 float sp[4][2], sz[4], sy[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) sp[u][0] = sp[u][1] = sz[u] = sy[u] = 0.f;
+                // one row = two pixels per lane (columns lane and lane + 32): a static two-pixel
+                // body, unrolled over rows for four independent pixels in flight
 #pragma unroll 2
-                for (int j = 0; j < 2 * BTH; ++j) {
-                    const int par = j & 1;
-                    const float dy = fmaf((float)(j >> 1), dfyf, dyb);
-                    const float2 gg = S.g[buf][32 * j + lane];
-                    const float2 pt = S.px[buf][32 * j + lane];
-                    const float a = fmaf(Ar.z, pt.x, fmaf(Ar.y, dy, ac[par]));
-                    const float b = fmaf(Br.z, pt.x, fmaf(Br.y, dy, bc[par]));
-                    const float g = fmaf(Gr.z, pt.x, fmaf(Gr.y, dy, gc[par]));
-                    const float tt = fmaf(Mr.z, pt.x, fmaf(Mr.y, dy, tc[par]));
-                    const float e = ex2_approx(-fmaf(a, a, fmaf(b, b, -pt.y)));
-                    const float kr = __fadd_rn(fmaf(tt, 0.15915494309189535f, 12582912.0f), -12582912.0f);
-                    const float ang = fmaf(kr, -6.28318530717958647692f, tt);
-                    const float kc = e * cos_approx(ang), ks = e * sin_approx(ang);
-                    const float p0r = fmaf(gg.x, kc, gg.y * ks);
-                    const float p0i = fmaf(gg.x, ks, -gg.y * kc);
-                    const float ag = fabsf(g);
-                    const float R = ag * p0r, I = ag * p0i;
-                    const float Rg = __int_as_float(__float_as_int(p0r) ^ (__float_as_int(g) & 0x80000000));  // sign(g) p0r
-                    const float Ra = R * a, Rb = R * b;
-                    sp[0][par] += Ra;
-                    sp[1][par] += Rb;
-                    sp[2][par] += Rg;
-                    sp[3][par] += I;
-                    sz[0] = fmaf(Ra, pt.x, sz[0]);
-                    sz[1] = fmaf(Rb, pt.x, sz[1]);
-                    sz[2] = fmaf(Rg, pt.x, sz[2]);
-                    sz[3] = fmaf(I, pt.x, sz[3]);
-                    sy[0] = fmaf(Ra, dy, sy[0]);
-                    sy[1] = fmaf(Rb, dy, sy[1]);
-                    sy[2] = fmaf(Rg, dy, sy[2]);
-                    sy[3] = fmaf(I, dy, sy[3]);
+                for (int row = row_lo; row <= row_hi; ++row) {
+                    const float dy = fmaf((float)row, dfyf, dyb);
+#pragma unroll
+                    for (int par = 0; par < 2; ++par) {
+                        const int j = 2 * row + par;
+                        const float2 gg = S.g[buf][32 * j + lane];
+                        const float2 pt = S.px[buf][32 * j + lane];
+                        const float a = fmaf(Ar.z, pt.x, fmaf(Ar.y, dy, ac[par]));
+                        const float b = fmaf(Br.z, pt.x, fmaf(Br.y, dy, bc[par]));
+                        const float g = fmaf(Gr.z, pt.x, fmaf(Gr.y, dy, gc[par]));
+                        const float tt = fmaf(Mr.z, pt.x, fmaf(Mr.y, dy, tc[par]));
+                        const float e = ex2_approx(-fmaf(a, a, fmaf(b, b, -pt.y)));
+                        const float kr = __fadd_rn(fmaf(tt, 0.15915494309189535f, 12582912.0f), -12582912.0f);
+                        const float ang = fmaf(kr, -6.28318530717958647692f, tt);
+                        const float kc = e * cos_approx(ang), ks = e * sin_approx(ang);
+                        const float p0r = fmaf(gg.x, kc, gg.y * ks);
+                        const float p0i = fmaf(gg.x, ks, -gg.y * kc);
+                        const float ag = fabsf(g);
+                        const float R = ag * p0r, I = ag * p0i;
+                        const float Rg = __int_as_float(__float_as_int(p0r) ^ (__float_as_int(g) & 0x80000000));  // sign(g) p0r
+                        const float Ra = R * a, Rb = R * b;
+                        sp[0][par] += Ra;
+                        sp[1][par] += Rb;
+                        sp[2][par] += Rg;
+                        sp[3][par] += I;
+                        sz[0] = fmaf(Ra, pt.x, sz[0]);
+                        sz[1] = fmaf(Rb, pt.x, sz[1]);
+                        sz[2] = fmaf(Rg, pt.x, sz[2]);
+                        sz[3] = fmaf(I, pt.x, sz[3]);
+                        sy[0] = fmaf(Ra, dy, sy[0]);
+                        sy[1] = fmaf(Rb, dy, sy[1]);
+                        sy[2] = fmaf(Rg, dy, sy[2]);
+                        sy[3] = fmaf(I, dy, sy[3]);
+                    }
                 }
                 float v[16];
 #pragma unroll
@@ -307,12 +339,13 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                         add = (double)S.red[warp][12];
                     } else {
                         const int vec = lane / 3, comp = lane % 3;
-                        const double ref = comp == 0 ? f0x : (comp == 1 ? f0y : (vec < 2 ? dz0 : f0z));
+                        const double ref = comp == 0 ? S.tc.f0x : (comp == 1 ? S.tc.f0y : (vec < 2 ? S.tc.dz0 : S.tc.f0z));
                         add = ref * (double)S.red[warp][4 * vec] + (double)S.red[warp][4 * vec + 1 + comp];
                     }
                     S.tot[k][lane] += add;
                 }
                 __syncwarp();
+              }
             }
             __syncthreads();
         }
@@ -399,9 +432,20 @@ cudaError_t launch_pixtab(int n_lambda, int H, int W, double dfx, double dfy, co
 int bwd_tiles_x(int W) { return (W + BTW - 1) / BTW; }
 int bwd_tiles_y(int H) { return (H + BTH - 1) / BTH; }
 
+cudaError_t prepare_bwd_kernels() {
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_splat_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdShared));
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+    return e;
+}
+
 cudaError_t launch_splat_bwd(const BwdArgs &a, int grid, cudaStream_t s) {
     const size_t smem = sizeof(BwdShared);
-    cudaError_t e = cudaFuncSetAttribute(k_splat_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = prepare_bwd_kernels();
     if (e != cudaSuccess) return e;
     k_splat_bwd<<<grid, BNT, smem, s>>>(a);
     count_launches(1);

@@ -62,6 +62,15 @@ struct alignas(16) TData {
     float pad;
 };
 
+// Per depth-sorted Gaussian: the product of its non-unit front factors (1 - alpha) and the
+// number of factors equal to 0 (alpha = 1), so that T = n1 ? 0 : Tnz, and dL/dT.
+struct alignas(16) TQuery {
+    double Tnz;
+    double dT;
+    int n1;
+    int pad;
+};
+
 // FP64 path record (per depth-sorted Gaussian).
 struct alignas(16) Rec64 {
     double r1[3], r2[3], r3[3];
@@ -196,6 +205,18 @@ __device__ __forceinline__ double mod_frac(long long a, long long b, long long n
     long long m = (a * b) % n;
     if (m < 0) m += n;
     return (double)m / (double)n;
+}
+
+// The same angles combined over both axes as one integer numerator of the denominator H W:
+//   (sh * ((a * b) mod H) * W + sw * ((c * d) mod W) * H) mod (H W),  sh, sw in {-1, +1};
+// the angle in cycles is num / (H W) (exact integers; one multiply by 1/(H W) afterwards).
+__device__ __forceinline__ long long mod_num2(long long a, long long b, int sh, long long c, long long d, int sw,
+                                              long long H, long long W) {
+    long long mh = (a * b) % H, mw = (c * d) % W;
+    if (mh < 0) mh += H;
+    if (mw < 0) mw += W;
+    long long num = (sh * mh * W + sw * mw * H) % (H * W);
+    return num < 0 ? num + H * W : num;
 }
 
 }  // namespace gws

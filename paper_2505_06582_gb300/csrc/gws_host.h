@@ -62,6 +62,8 @@ struct SplatArgs {
 };
 
 cudaError_t launch_splat_mixed(int cfg, const SplatArgs &a, int grid, cudaStream_t s);
+cudaError_t prepare_splat_kernels();
+cudaError_t prepare_bwd_kernels();
 int splat_mixed_ctas_per_sm(int cfg);
 
 struct Splat64Args {

@@ -118,7 +118,8 @@ constexpr int kTChunk = 128;
 // alpha below alpha_min dropped.  FP64 like the oracle; boxes cull in FP32 (conservative).
 __global__ void __launch_bounds__(kTChunk) k_transmit(const TData *__restrict__ td, const unsigned *__restrict__ sorted,
                                                       Segs S, long long n, double alpha_min,
-                                                      double *__restrict__ T_sorted, double *__restrict__ T_g) {
+                                                      double *__restrict__ T_sorted, double *__restrict__ T_g,
+                                                      TQuery *__restrict__ tq) {
     __shared__ TData s_td[kTChunk];
     const long long p = (long long)blockIdx.x * kTChunk + threadIdx.x;
     const bool active = p < n;
@@ -131,7 +132,8 @@ __global__ void __launch_bounds__(kTChunk) k_transmit(const TData *__restrict__ 
     const long long pfirst = (long long)blockIdx.x * kTChunk;
     const long long plast = min(pfirst + kTChunk, n) - 1;
     const long long qlo = S.off[scene_of(S.off, S.n_scenes, pfirst)];
-    double T = 1.0;
+    double T = 1.0, Tnz = 1.0;
+    int n1 = 0;
     for (long long c0 = qlo; c0 < plast; c0 += kTChunk) {
         __syncthreads();
         if (c0 + threadIdx.x < plast) s_td[threadIdx.x] = td[c0 + threadIdx.x];
@@ -146,13 +148,175 @@ __global__ void __launch_bounds__(kTChunk) k_transmit(const TData *__restrict__ 
             const double y0 = (f.m11 * dx - f.m01 * dy) / f.det;
             const double y1 = (-f.m10 * dx + f.m00 * dy) / f.det;
             const double a = (double)f.o * exp(-0.5 * (y0 * y0 + y1 * y1));
-            if (a >= alpha_min) T *= (1.0 - a);
+            if (a >= alpha_min) {
+                T *= (1.0 - a);
+                if (a == 1.0) ++n1;
+                else Tnz *= (1.0 - a);
+            }
         }
     }
     if (active) {
         T_sorted[p] = T;
         T_g[sorted[p]] = T;
+        if (tq) {
+            TQuery q;
+            q.Tnz = Tnz;
+            q.dT = 0.0;
+            q.n1 = n1;
+            q.pad = 0;
+            tq[p] = q;
+        }
     }
+}
+
+// ---------------------------------------------------------------------------------------
+// backward cross terms through the transmittance (depth-sorted mode)
+//   T_i = prod_{j front of i, alpha_j(mu_i) >= alpha_min} (1 - alpha_j(mu_i)),
+//   alpha_j(x) = o_j exp(-Q/2),  Q = |M_j^-1 (x - mu_j)_xy|^2,  M_j = [s_u r1_xy, s_v r2_xy];
+//   dL/dalpha_j(mu_i) = -dL/dT_i prod_{k != j} (1 - alpha_k(mu_i))  (the threshold set held fixed)
+// ---------------------------------------------------------------------------------------
+
+__device__ __forceinline__ double others_product(const TQuery &q, double a) {
+    if (q.n1 == 0) return q.Tnz / (1.0 - a);
+    if (q.n1 == 1 && a == 1.0) return q.Tnz;
+    return 0.0;
+}
+
+__global__ void k_tq_dT(const unsigned *__restrict__ sorted, const double *__restrict__ dT_g, long long n,
+                        TQuery *__restrict__ tq) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) tq[p].dT = dT_g[sorted[p]];
+}
+
+// pass A: per Gaussian i (sorted position p), the terms on its own mean (d = mu_i - mu_j)
+__global__ void __launch_bounds__(kTChunk) k_tgrad_query(const TData *__restrict__ td, const TQuery *__restrict__ tq,
+                                                         const unsigned *__restrict__ sorted, Segs S, long long n,
+                                                         double alpha_min, double *__restrict__ dmean) {
+    __shared__ TData s_td[kTChunk];
+    const long long p = (long long)blockIdx.x * kTChunk + threadIdx.x;
+    const bool active = p < n;
+    const long long pp = active ? p : n - 1;
+    const long long start = S.off[scene_of(S.off, S.n_scenes, pp)];
+    const double xp = td[pp].mx, yp = td[pp].my;
+    const float xf = (float)xp, yf = (float)yp;
+    const TQuery Q = tq[pp];
+    const long long pfirst = (long long)blockIdx.x * kTChunk;
+    const long long plast = min(pfirst + kTChunk, n) - 1;
+    const long long qlo = S.off[scene_of(S.off, S.n_scenes, pfirst)];
+    double gx = 0.0, gy = 0.0;
+    for (long long c0 = qlo; c0 < plast; c0 += kTChunk) {
+        __syncthreads();
+        if (c0 + threadIdx.x < plast) s_td[threadIdx.x] = td[c0 + threadIdx.x];
+        __syncthreads();
+        const long long cend = min((long long)kTChunk, plast - c0);
+        if (Q.dT == 0.0) continue;
+        for (int k = 0; k < cend; ++k) {
+            const long long q = c0 + k;
+            if (q < start || q >= pp) continue;
+            const TData &f = s_td[k];
+            if (xf < f.bx0 || xf > f.bx1 || yf < f.by0 || yf > f.by1) continue;
+            const double dx = xp - f.mx, dy = yp - f.my;
+            const double y0 = (f.m11 * dx - f.m01 * dy) / f.det;
+            const double y1 = (-f.m10 * dx + f.m00 * dy) / f.det;
+            const double a = (double)f.o * exp(-0.5 * (y0 * y0 + y1 * y1));
+            if (a < alpha_min) continue;
+            const double dA = -Q.dT * others_product(Q, a);
+            const double dQ = dA * (-0.5 * a);
+            const double mty0 = (f.m11 * y0 - f.m10 * y1) / f.det;
+            const double mty1 = (-f.m01 * y0 + f.m00 * y1) / f.det;
+            gx += dQ * 2.0 * mty0;
+            gy += dQ * 2.0 * mty1;
+        }
+    }
+    if (active) {
+        const unsigned g = sorted[p];
+        dmean[3 * (size_t)g] += gx;
+        dmean[3 * (size_t)g + 1] += gy;
+    }
+}
+
+// pass B: per front Gaussian j (sorted position q), the terms on its mean, scales, rotation
+// and opacity, summed over the Gaussians i behind it
+__global__ void __launch_bounds__(kTChunk) k_tgrad_front(const TData *__restrict__ td, const TQuery *__restrict__ tq,
+                                                         const GPre *__restrict__ gp, const unsigned *__restrict__ sorted,
+                                                         const float *__restrict__ quat_in, Segs S, long long n,
+                                                         double alpha_min, double *__restrict__ dmean,
+                                                         float *__restrict__ dquat, float *__restrict__ dscale,
+                                                         float *__restrict__ dopacity) {
+    __shared__ double s_x[kTChunk], s_y[kTChunk];
+    __shared__ TQuery s_q[kTChunk];
+    const long long q = (long long)blockIdx.x * kTChunk + threadIdx.x;
+    const bool active = q < n;
+    const long long qq = active ? q : n - 1;
+    const int sc = scene_of(S.off, S.n_scenes, qq);
+    const long long end = S.off[sc + 1];
+    const TData f = td[qq];
+    const long long qfirst = (long long)blockIdx.x * kTChunk;
+    const long long plo = qfirst + 1;
+    const long long phi = S.off[scene_of(S.off, S.n_scenes, min(qfirst + kTChunk, n) - 1) + 1];
+    double go = 0.0, gmx = 0.0, gmy = 0.0, gM00 = 0.0, gM01 = 0.0, gM10 = 0.0, gM11 = 0.0;
+    const bool has_box = !(f.bx0 > f.bx1);
+    for (long long c0 = plo; c0 < phi; c0 += kTChunk) {
+        __syncthreads();
+        if (c0 + threadIdx.x < phi) {
+            s_x[threadIdx.x] = td[c0 + threadIdx.x].mx;
+            s_y[threadIdx.x] = td[c0 + threadIdx.x].my;
+            s_q[threadIdx.x] = tq[c0 + threadIdx.x];
+        }
+        __syncthreads();
+        if (!has_box) continue;
+        const long long cend = min((long long)kTChunk, phi - c0);
+        for (int k = 0; k < cend; ++k) {
+            const long long p = c0 + k;
+            if (p <= qq || p >= end) continue;
+            const float xf = (float)s_x[k], yf = (float)s_y[k];
+            if (xf < f.bx0 || xf > f.bx1 || yf < f.by0 || yf > f.by1) continue;
+            const TQuery &Q = s_q[k];
+            if (Q.dT == 0.0) continue;
+            const double dx = s_x[k] - f.mx, dy = s_y[k] - f.my;
+            const double y0 = (f.m11 * dx - f.m01 * dy) / f.det;
+            const double y1 = (-f.m10 * dx + f.m00 * dy) / f.det;
+            const double a = (double)f.o * exp(-0.5 * (y0 * y0 + y1 * y1));
+            if (a < alpha_min) continue;
+            const double dA = -Q.dT * others_product(Q, a);
+            if (f.o > 0.f) go += dA * a / (double)f.o;
+            const double dQ = dA * (-0.5 * a);
+            const double mty0 = (f.m11 * y0 - f.m10 * y1) / f.det;
+            const double mty1 = (-f.m01 * y0 + f.m00 * y1) / f.det;
+            gmx -= dQ * 2.0 * mty0;
+            gmy -= dQ * 2.0 * mty1;
+            gM00 += dQ * -2.0 * mty0 * y0;
+            gM01 += dQ * -2.0 * mty0 * y1;
+            gM10 += dQ * -2.0 * mty1 * y0;
+            gM11 += dQ * -2.0 * mty1 * y1;
+        }
+    }
+    if (!active) return;
+    const unsigned g = sorted[q];
+    const GPre &P = gp[g];
+    double r1[3], r2[3], r3[3];
+    quat_cols<double>(P.q, r1, r2, r3);
+    const double su = P.su, sv = P.sv;
+    const double dsu = gM00 * r1[0] + gM10 * r1[1], dsv = gM01 * r2[0] + gM11 * r2[1];
+    const double G1[3] = {gM00 * su, gM10 * su, 0.0}, G2[3] = {gM01 * sv, gM11 * sv, 0.0};
+    const double w = P.q[0], x = P.q[1], y = P.q[2], z = P.q[3];
+    const double dr1[4][3] = {{0, 2 * z, -2 * y}, {0, 2 * y, 2 * z}, {-4 * y, 2 * x, -2 * w}, {-4 * z, 2 * w, 2 * x}};
+    const double dr2[4][3] = {{-2 * z, 0, 2 * x}, {2 * y, -4 * x, 2 * w}, {2 * x, 0, 2 * z}, {-2 * w, -4 * z, 2 * y}};
+    double gh[4];
+    for (int m = 0; m < 4; ++m) {
+        gh[m] = 0;
+        for (int k = 0; k < 3; ++k) gh[m] += G1[k] * dr1[m][k] + G2[k] * dr2[m][k];
+    }
+    const double qi[4] = {quat_in[4 * g], quat_in[4 * g + 1], quat_in[4 * g + 2], quat_in[4 * g + 3]};
+    const double qn = sqrt(qi[0] * qi[0] + qi[1] * qi[1] + qi[2] * qi[2] + qi[3] * qi[3]);
+    const double proj = gh[0] * w + gh[1] * x + gh[2] * y + gh[3] * z;
+    const double qh[4] = {w, x, y, z};
+    for (int m = 0; m < 4; ++m) dquat[4 * (size_t)g + m] = (float)((double)dquat[4 * (size_t)g + m] + (gh[m] - proj * qh[m]) / qn);
+    dmean[3 * (size_t)g] += gmx;
+    dmean[3 * (size_t)g + 1] += gmy;
+    dscale[2 * (size_t)g] = (float)((double)dscale[2 * (size_t)g] + dsu);
+    dscale[2 * (size_t)g + 1] = (float)((double)dscale[2 * (size_t)g + 1] + dsv);
+    dopacity[g] = (float)((double)dopacity[g] + go);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -418,28 +582,30 @@ __global__ void k_modulate(typename Cx<R>::T *__restrict__ data, int n_slices, i
     const long long pix = idx % hw;
     const int r = (int)(pix / W), c = (int)(pix % W);
     const int h2 = H / 2, w2 = W / 2;
-    double fr;
+    // angle = num / (H W) cycles, num an exact integer (see mod_num2)
+    long long num;
     double sc = 1.0;
-    if (mode == 0) {
-        fr = mod_frac(h2, h2, H) + mod_frac(w2, w2, W) - mod_frac(h2, r, H) - mod_frac(w2, c, W);
+    if (mode == 0) {  // e^{j2pi(m0 r0/H + n0 c0/W)} e^{-j2pi(m0 r/H + n0 c/W)}
+        num = mod_num2(h2, h2, 1, w2, w2, 1, H, W) - mod_num2(h2, r, 1, w2, c, 1, H, W);
         sc = scale;
-    } else if (mode == 1) {
-        fr = mod_frac(h2, r, H) + mod_frac(w2, c, W);
-    } else {
-        fr = -(mod_frac(h2, h2, H) + mod_frac(w2, w2, W)) + mod_frac(r, h2, H) + mod_frac(c, w2, W);
+    } else if (mode == 1) {  // e^{+j2pi(m0 r/H + n0 c/W)}
+        num = mod_num2(h2, r, 1, w2, c, 1, H, W);
+    } else {  // e^{-j2pi(m0 r0/H + n0 c0/W)} e^{+j2pi(m r0/H + n c0/W)}
+        num = mod_num2(r, h2, 1, c, w2, 1, H, W) - mod_num2(h2, h2, 1, w2, w2, 1, H, W);
         sc = scale;
     }
-    fr -= rint(fr);
+    if (num < 0) num += hw;
+    if (2 * num > hw) num -= hw;  // |angle| <= 1/2 cycle
     typename Cx<R>::T v = data[idx];
     R sn, cs;
     if (sizeof(R) == 8) {
         double s8, c8;
-        sincospi(2.0 * fr, &s8, &c8);
+        sincospi(2.0 * (double)num / (double)hw, &s8, &c8);
         sn = (R)s8;
         cs = (R)c8;
     } else {
         float s4, c4;
-        sincospif((float)(2.0 * fr), &s4, &c4);
+        sincospif(2.0f * (float)num * (1.0f / (float)hw), &s4, &c4);
         sn = (R)s4;
         cs = (R)c4;
     }
@@ -479,27 +645,31 @@ template <typename R>
 __global__ void k_dpac(const typename Cx<R>::T *__restrict__ f, int n_lambda, int H, int W,
                        const unsigned long long *__restrict__ amax2, double amp_scale, float *__restrict__ out) {
     const long long hw = (long long)H * W;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= hw * n_lambda) return;
-    const int l = (int)(idx / hw);
-    const long long pix = idx % hw;
-    const int r = (int)(pix / W), c = (int)(pix % W);
-    R m2max;
-    if (amp_scale > 0) m2max = (R)(amp_scale * amp_scale);
-    else if (sizeof(R) == 8) m2max = (R)__longlong_as_double((long long)amax2[l]);
-    else m2max = (R)__uint_as_float((unsigned)amax2[l]);
-    const typename Cx<R>::T v = f[idx];
-    const R m2 = v.x * v.x + v.y * v.y;
-    R a = m2max > 0 ? sqrt(m2 / m2max) : (R)0;
-    a = a > (R)1 ? (R)1 : a;
-    const R phi = atan2(v.y, v.x);
-    const R ac = acos(a);
-    R p = ((r + c) & 1) == 0 ? phi - ac : phi + ac;
-    const R pi = (R)kPi, tpi = (R)kTwoPi;
-    p = p - tpi * floor((p + pi) / tpi);
-    if (p < -pi) p += tpi;
-    if (p >= pi) p -= tpi;
-    out[idx] = (float)p;
+    const long long total = hw * n_lambda;
+    const R pi = (R)kPi, tpi = (R)kTwoPi, inv_tpi = (R)(1.0 / kTwoPi);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const long long idx = ((long long)blockIdx.x * 4 + u) * blockDim.x + threadIdx.x;
+        if (idx >= total) break;
+        const int l = (int)(idx / hw);
+        const long long pix = idx % hw;
+        const int r = (int)(pix / W), c = (int)(pix % W);
+        R m2max;
+        if (amp_scale > 0) m2max = (R)(amp_scale * amp_scale);
+        else if (sizeof(R) == 8) m2max = (R)__longlong_as_double((long long)amax2[l]);
+        else m2max = (R)__uint_as_float((unsigned)amax2[l]);
+        const typename Cx<R>::T v = f[idx];
+        const R m2 = v.x * v.x + v.y * v.y;
+        R a = m2max > 0 ? sqrt(m2 / m2max) : (R)0;
+        a = a > (R)1 ? (R)1 : a;
+        const R phi = atan2(v.y, v.x);
+        const R ac = acos(a);
+        R p = ((r + c) & 1) == 0 ? phi - ac : phi + ac;
+        p = p - tpi * floor((p + pi) * inv_tpi);
+        if (p < -pi) p += tpi;
+        if (p >= pi) p -= tpi;
+        out[idx] = (float)p;
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -524,11 +694,23 @@ cudaError_t launch_scene_key(const GPre *gp, const unsigned *sorted, long long n
 }
 
 cudaError_t launch_transmittance(const GPre *gp, const unsigned *sorted, const Segs &S, long long n, double alpha_min,
-                                 TData *td, double *T_sorted, double *T_g, cudaStream_t s) {
+                                 TData *td, double *T_sorted, double *T_g, TQuery *tq, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_tdata<<<nblk(n, 256), 256, 0, s>>>(gp, sorted, n, alpha_min, td);
-    k_transmit<<<nblk(n, kTChunk), kTChunk, 0, s>>>(td, sorted, S, n, alpha_min, T_sorted, T_g);
+    k_transmit<<<nblk(n, kTChunk), kTChunk, 0, s>>>(td, sorted, S, n, alpha_min, T_sorted, T_g, tq);
     count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tgrad(const TData *td, TQuery *tq, const GPre *gp, const unsigned *sorted, const double *dT_g,
+                         const float *quat_in, const Segs &S, long long n, double alpha_min, double *dmean,
+                         float *dquat, float *dscale, float *dopacity, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_tq_dT<<<nblk(n, 256), 256, 0, s>>>(sorted, dT_g, n, tq);
+    k_tgrad_query<<<nblk(n, kTChunk), kTChunk, 0, s>>>(td, tq, sorted, S, n, alpha_min, dmean);
+    k_tgrad_front<<<nblk(n, kTChunk), kTChunk, 0, s>>>(td, tq, gp, sorted, quat_in, S, n, alpha_min, dmean, dquat,
+                                                         dscale, dopacity);
+    count_launches(3);
     return cudaGetLastError();
 }
 
@@ -603,7 +785,7 @@ cudaError_t launch_encode(const void *field, int prec64, int n_lambda, int H, in
     if (amp_scale <= 0) {
         cudaError_t e = cudaMemsetAsync(amax2, 0, sizeof(unsigned long long) * n_lambda, s);
         if (e != cudaSuccess) return e;
-        const unsigned gx = (unsigned)std::min<long long>(nblk(hw, 256), 1024);
+        const unsigned gx = (unsigned)std::min<long long>(nblk(hw, 256), 608);
         if (prec64)
             k_amax<double><<<dim3(gx, n_lambda), 256, 0, s>>>((const double2 *)field, hw, amax2);
         else
@@ -612,9 +794,9 @@ cudaError_t launch_encode(const void *field, int prec64, int n_lambda, int H, in
     }
     const long long n = hw * n_lambda;
     if (prec64)
-        k_dpac<double><<<nblk(n, 256), 256, 0, s>>>((const double2 *)field, n_lambda, H, W, amax2, amp_scale, out);
+        k_dpac<double><<<nblk(n, 1024), 256, 0, s>>>((const double2 *)field, n_lambda, H, W, amax2, amp_scale, out);
     else
-        k_dpac<float><<<nblk(n, 256), 256, 0, s>>>((const float2 *)field, n_lambda, H, W, amax2, amp_scale, out);
+        k_dpac<float><<<nblk(n, 1024), 256, 0, s>>>((const float2 *)field, n_lambda, H, W, amax2, amp_scale, out);
     count_launches(1);
     return cudaGetLastError();
 }

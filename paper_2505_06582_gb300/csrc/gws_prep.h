@@ -14,7 +14,10 @@ cudaError_t launch_prep(const SceneTable &T, long long n_total, GPre *gp, float 
                         unsigned *dval, int *status, cudaStream_t s);
 cudaError_t launch_scene_key(const GPre *gp, const unsigned *sorted, long long n, unsigned *skey, cudaStream_t s);
 cudaError_t launch_transmittance(const GPre *gp, const unsigned *sorted, const Segs &S, long long n, double alpha_min,
-                                 TData *td, double *T_sorted, double *T_g, cudaStream_t s);
+                                 TData *td, double *T_sorted, double *T_g, TQuery *tq, cudaStream_t s);
+cudaError_t launch_tgrad(const TData *td, TQuery *tq, const GPre *gp, const unsigned *sorted, const double *dT_g,
+                         const float *quat_in, const Segs &S, long long n, double alpha_min, double *dmean,
+                         float *dquat, float *dscale, float *dopacity, cudaStream_t s);
 cudaError_t launch_rec64(const GPre *gp, const float *ampc, const unsigned *sorted, const double *T_sorted, long long n,
                          int L, Rec64 *rec, double *w, cudaStream_t s);
 cudaError_t launch_foot_keys(const GPre *gp, const float *ampc, const unsigned *sorted, const double *T_sorted,

@@ -4,7 +4,8 @@
 // Mixed-precision persistent tile splat.  A work item is one (scene, wavelength, frequency
 // tile).  A CTA holds the tile's complex accumulators in registers (PX consecutive pixels
 // of one row per thread) and streams the segment's Gaussian records through shared
-// memory with 1-D bulk copies (cp.async.bulk, mbarrier completion, STAGES-deep ring).
+// memory with 1-D bulk copies (cp.async.bulk, mbarrier completion, STAGES-deep ring of
+// one-record-per-thread chunks).
 // Records are ordered by decreasing spectral footprint radius, so a tile only reads the
 // prefix of records whose footprint can reach it (item_count); an exact ellipse-rectangle
 // test then culls per (record, tile).
@@ -51,13 +52,19 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
 template <int TW, int TH, int PX, int CHUNK, int STAGES>
 __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_constant__ SplatArgs A) {
     constexpr int NT = (TW / PX) * TH;
-    static_assert(CHUNK % 32 == 0 && CHUNK <= NT && CHUNK <= 64, "chunk");
+    constexpr int NW = NT / 32;          // warps = row bands of the tile
+    constexpr int RPW = 32 / (TW / PX);  // tile rows per warp
+    static_assert(CHUNK == NT && CHUNK % 32 == 0 && (TW / PX) <= 32 && 32 % (TW / PX) == 0, "chunk / tile shape");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Rec *s_rec = reinterpret_cast<Rec *>(smem_raw);
     float4 *s_sv = reinterpret_cast<float4 *>(smem_raw + sizeof(Rec) * STAGES * CHUNK);
+    // per consumer warp w and source warp v: the chunk slots culled in by warp v that warp w
+    // evaluates (records whose footprint meets w's band of rows)
+    unsigned char *s_list =
+        reinterpret_cast<unsigned char *>(smem_raw + sizeof(Rec) * STAGES * CHUNK + sizeof(float4) * 4 * CHUNK);
     __shared__ uint64_t s_full[STAGES];
     __shared__ uint64_t s_never;
-    __shared__ unsigned s_mask[2];
+    __shared__ unsigned char s_cnt[NW][NW];
     __shared__ int s_item;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -96,7 +103,7 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
         // this thread's pixels: row prow, columns pcol0 .. pcol0 + PX - 1; f_z and f_z - f0_z in FP64
         const int prow = r_lo + tid / (TW / PX);
         const int pcol0 = c_lo + (tid % (TW / PX)) * PX;
-        const float dfxf = (float)A.dfx;
+        const float dfxf = (float)A.dfx, dfyf = (float)A.dfy;
         const float dy = (float)((double)(prow - r_ref) * A.dfy);
         const double fyd = (double)(prow - A.H / 2) * A.dfy;
         float dx[PX], dz[PX], lfz[PX];
@@ -149,13 +156,23 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
             consumed = ch + 1;
 
             // ---- cull + per-(record, tile) scalars (one thread per record) ----
+            // A record survives if its footprint ellipse meets the tile; it is then tested
+            // against each warp's band of RPW rows (FP32, from the tile's edges), and only the
+            // warps whose band it meets evaluate it.
             const int nrec = min(CHUNK, count - ch * CHUNK);
-            if (tid < CHUNK) {
-                bool pass = false;
+            {
+                unsigned bands = 0;
                 if (tid < nrec) {
                     const Rec &r = s_rec[st * CHUNK + tid];
-                    pass = ellipse_hits_rect(r.e00, r.e01, r.e11, x0, x1, y0, y1);
-                    if (pass) {
+                    if (ellipse_hits_rect(r.e00, r.e01, r.e11, x0, x1, y0, y1)) {
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) {
+                            const float yb0 = fmaf((float)(w * RPW), dfyf, y0);
+                            const float yb1 = fminf(fmaf((float)(RPW - 1), dfyf, yb0), y1);
+                            if (yb0 <= y1 && ellipse_hits_rect(r.e00, r.e01, r.e11, x0, x1, yb0, yb1)) bands |= 1u << w;
+                        }
+                    }
+                    if (bands) {
                         double cyc = -(f0x * r.mux + f0y * r.muy + f0z * r.muz);
                         if (A.phase_match) cyc += r.muz * inv_lam;
                         cyc -= rint(cyc);
@@ -170,8 +187,14 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
                         sv[3] = make_float4(r.mx, r.my, r.mz, (float)cyc);
                     }
                 }
-                const unsigned bal = __ballot_sync(0xffffffffu, pass);
-                if (lane == 0) s_mask[warp] = bal;
+                const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    const bool mine = (bands >> w) & 1u;
+                    const unsigned bal = __ballot_sync(0xffffffffu, mine);
+                    if (mine) s_list[(w * NW + warp) * 32 + __popc(bal & lt)] = (unsigned char)(tid & 255);
+                    if (lane == 0) s_cnt[w][warp] = (unsigned char)__popc(bal);
+                }
             }
             __syncthreads();
             // the stage is free again: refill it with the chunk STAGES ahead
@@ -188,27 +211,28 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
             }
 
             // ---- the hot loop: every surviving record x this thread's PX pixels ----
-            unsigned long long mask = (unsigned long long)s_mask[0];
-            if (CHUNK > 32) mask |= (unsigned long long)s_mask[1] << 32;
-            while (mask) {
-                const int k = __ffsll((long long)mask) - 1;
-                mask &= mask - 1ull;
-                const float4 Ar = s_sv[k * 4 + 0], Br = s_sv[k * 4 + 1], Gr = s_sv[k * 4 + 2], Mr = s_sv[k * 4 + 3];
-                const float ar = fmaf(Ar.y, dy, Ar.w), br = fmaf(Br.y, dy, Br.w);
-                const float gr = fmaf(Gr.y, dy, Gr.w), tr = fmaf(Mr.y, dy, Mr.w);
+            for (int v = 0; v < NW; ++v) {
+                const int cnt = s_cnt[warp][v];
+                const unsigned char *lst = s_list + (warp * NW + v) * 32;
+                for (int i = 0; i < cnt; ++i) {
+                    const int k = lst[i];
+                    const float4 Ar = s_sv[k * 4 + 0], Br = s_sv[k * 4 + 1], Gr = s_sv[k * 4 + 2], Mr = s_sv[k * 4 + 3];
+                    const float ar = fmaf(Ar.y, dy, Ar.w), br = fmaf(Br.y, dy, Br.w);
+                    const float gr = fmaf(Gr.y, dy, Gr.w), tr = fmaf(Mr.y, dy, Mr.w);
 #pragma unroll
-                for (int p = 0; p < PX; ++p) {
-                    const float a = fmaf(Ar.z, dz[p], fmaf(Ar.x, dx[p], ar));
-                    const float b = fmaf(Br.z, dz[p], fmaf(Br.x, dx[p], br));
-                    const float g = fmaf(Gr.z, dz[p], fmaf(Gr.x, dx[p], gr));
-                    const float t = fmaf(Mr.z, dz[p], fmaf(Mr.x, dx[p], tr));
-                    // |g| / f_z 2^-(a^2 + b^2) = |g| 2^-(a^2 + b^2 - log2(1/f_z))
-                    const float amp = fabsf(g) * ex2_approx(-fmaf(a, a, fmaf(b, b, -lfz[p])));
-                    // t (radians) minus 2 pi round(t / 2 pi), rounding on the FP32 pipe (+-1.5 * 2^23)
-                    const float kr = __fadd_rn(fmaf(t, 0.15915494309189535f, 12582912.0f), -12582912.0f);
-                    const float ang = fmaf(kr, -6.28318530717958647692f, t);
-                    acc_re[p] = fmaf(amp, cos_approx(ang), acc_re[p]);
-                    acc_im[p] = fmaf(amp, sin_approx(ang), acc_im[p]);
+                    for (int p = 0; p < PX; ++p) {
+                        const float a = fmaf(Ar.z, dz[p], fmaf(Ar.x, dx[p], ar));
+                        const float b = fmaf(Br.z, dz[p], fmaf(Br.x, dx[p], br));
+                        const float g = fmaf(Gr.z, dz[p], fmaf(Gr.x, dx[p], gr));
+                        const float t = fmaf(Mr.z, dz[p], fmaf(Mr.x, dx[p], tr));
+                        // |g| / f_z 2^-(a^2 + b^2) = |g| 2^-(a^2 + b^2 - log2(1/f_z))
+                        const float amp = fabsf(g) * ex2_approx(-fmaf(a, a, fmaf(b, b, -lfz[p])));
+                        // t (radians) minus 2 pi round(t / 2 pi), rounding on the FP32 pipe (+-1.5 * 2^23)
+                        const float kr = __fadd_rn(fmaf(t, 0.15915494309189535f, 12582912.0f), -12582912.0f);
+                        const float ang = fmaf(kr, -6.28318530717958647692f, t);
+                        acc_re[p] = fmaf(amp, cos_approx(ang), acc_re[p]);
+                        acc_im[p] = fmaf(amp, sin_approx(ang), acc_im[p]);
+                    }
                 }
             }
 #pragma unroll
@@ -234,17 +258,18 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
         // ---- epilogue: compensated total, centred-DFT pre-modulation, store ----
         if (prow < A.H) {
             float2 *out = reinterpret_cast<float2 *>(A.out[scene]) + (size_t)l * A.H * A.W + (size_t)prow * A.W;
-            const double frow = mod_frac(prow, A.H / 2, A.H);
+            const long long hw = (long long)A.H * A.W;
+            const float inv_hw = 1.0f / (float)hw;
 #pragma unroll
             for (int p = 0; p < PX; ++p) {
                 const int col = pcol0 + p;
                 if (col < A.W) {
                     float re = sum_re[p] + cmp_re[p], im = sum_im[p] + cmp_im[p];
-                    if (A.field_mode) {
-                        double fr = frow + mod_frac(col, A.W / 2, A.W);
-                        fr -= rint(fr);
+                    if (A.field_mode) {  // e^{-j2pi(m r0/H + n c0/W)}, the angle an exact integer over H W
+                        long long num = mod_num2(prow, A.H / 2, 1, col, A.W / 2, 1, A.H, A.W);
+                        if (2 * num > hw) num -= hw;
                         float sn, cs;
-                        sincospif(-2.0f * (float)fr, &sn, &cs);
+                        sincospif(-2.0f * (float)num * inv_hw, &sn, &cs);
                         const float r2 = re * cs - im * sn;
                         im = re * sn + im * cs;
                         re = r2;
@@ -260,16 +285,37 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
 // ---- tile configurations (autotuned) ----------------------------------------------------
 
 template <int TW, int TH, int PX>
-static cudaError_t launch_cfg(const SplatArgs &a, int grid, cudaStream_t s) {
-    constexpr int CHUNK = 64, STAGES = 3;
-    constexpr int NT = (TW / PX) * TH;
-    const size_t smem = sizeof(Rec) * STAGES * CHUNK + sizeof(float4) * 4 * CHUNK;
-    auto kern = k_splat_mixed<TW, TH, PX, CHUNK, STAGES>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, NT, smem, s>>>(a);
-    count_launches(1);
-    return cudaGetLastError();
+struct SplatCfg {
+    static constexpr int NT = (TW / PX) * TH;
+    static constexpr int CHUNK = NT, STAGES = 3;
+    static constexpr size_t smem = sizeof(Rec) * STAGES * CHUNK + sizeof(float4) * 4 * CHUNK + (size_t)(NT / 32) * NT;
+    // the opt-in shared-memory size is a per-device function attribute: set it once per
+    // device (gws_prepare or the first call), not while a stream is being captured
+    static cudaError_t prepare() {
+        static bool done[64] = {false};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+        e = cudaFuncSetAttribute(k_splat_mixed<TW, TH, PX, CHUNK, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+        return e;
+    }
+    static cudaError_t launch(const SplatArgs &a, int grid, cudaStream_t s) {
+        cudaError_t e = prepare();
+        if (e != cudaSuccess) return e;
+        k_splat_mixed<TW, TH, PX, CHUNK, STAGES><<<grid, NT, smem, s>>>(a);
+        count_launches(1);
+        return cudaGetLastError();
+    }
+};
+
+cudaError_t prepare_splat_kernels() {
+    cudaError_t e = SplatCfg<64, 32, 8>::prepare();
+    if (e == cudaSuccess) e = SplatCfg<32, 32, 4>::prepare();
+    if (e == cudaSuccess) e = SplatCfg<128, 16, 8>::prepare();
+    return e;
 }
 
 static const TileCfg kCfgs[] = {{1, 64, 32}, {2, 32, 32}, {3, 128, 16}};
@@ -286,9 +332,9 @@ int splat_mixed_ctas_per_sm(int cfg) {
 
 cudaError_t launch_splat_mixed(int cfg, const SplatArgs &a, int grid, cudaStream_t s) {
     switch (cfg) {
-        case 2: return launch_cfg<32, 32, 4>(a, grid, s);
-        case 3: return launch_cfg<128, 16, 8>(a, grid, s);
-        default: return launch_cfg<64, 32, 8>(a, grid, s);
+        case 2: return SplatCfg<32, 32, 4>::launch(a, grid, s);
+        case 3: return SplatCfg<128, 16, 8>::launch(a, grid, s);
+        default: return SplatCfg<64, 32, 8>::launch(a, grid, s);
     }
 }
 
@@ -327,10 +373,11 @@ __global__ void __launch_bounds__(256) k_splat_fp64(const __grid_constant__ Spla
         }
     }
     if (A.field_mode) {
-        double fr = mod_frac(r, A.H / 2, A.H) + mod_frac(c, A.W / 2, A.W);
-        fr -= rint(fr);
+        const long long hw = (long long)A.H * A.W;
+        long long num = mod_num2(r, A.H / 2, 1, c, A.W / 2, 1, A.H, A.W);
+        if (2 * num > hw) num -= hw;
         double sn, cs;
-        sincospi(-2.0 * fr, &sn, &cs);
+        sincospi(-2.0 * (double)num / (double)hw, &sn, &cs);
         const double t = sre * cs - sim * sn;
         sim = sre * sn + sim * cs;
         sre = t;

@@ -352,6 +352,21 @@ def footprint_pairs(g: Gaussians, slm: Slm, workspace=None, **kw) -> int:
     return int(out.value)
 
 
+def autotune(g: Gaussians, slm: Slm, workspace=None, **kw) -> int:
+    """Times every splat tile configuration on this scene; the fastest becomes the default
+    for this (H, W, n_lambda).  Returns its id."""
+    lib = load()
+    slm = Slm.of(slm)
+    g.check(slm.n_lambda)
+    opts = make_opts(**kw)
+    scratch = torch.empty((slm.n_lambda, slm.H, slm.W), dtype=torch.complex64, device=g.mean.device)
+    _attach_ws(opts, [g.n], slm, g.mean.device, workspace)
+    best = C.c_int(0)
+    _check(lib.gws_autotune(C.byref(g._c()), C.c_int64(g.n), C.byref(slm._c()), C.byref(opts),
+                            C.c_void_p(scratch.data_ptr()), C.byref(best)), "gws_autotune")
+    return int(best.value)
+
+
 def last_launch_count() -> int:
     return int(load().gws_last_launch_count())
 

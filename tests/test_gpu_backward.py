@@ -72,7 +72,7 @@ def test_backward_is_deterministic():
         assert torch.equal(a[k], b[k]), k
 
 
-def test_backward_empty_and_unsupported():
+def test_backward_empty_and_unsupported():  # FP64 backward is not provided
     slm = SLM(16, 16, 8e-6, 8e-6, (520e-9,))
     sc = uniform_scene(10, 3, slm)
     G = torch.as_tensor(cotangent(1, slm), device="cuda")
@@ -170,3 +170,57 @@ def test_full_size_backward_sampled_gaussians(cfg):
     for k in GROUPS:
         e = rel_l2(got[k].cpu().numpy()[which].astype(np.float64), ref[k])
         assert e < TOL, (k, e)
+
+
+# ---------------------------------------------------------------------------------------
+# depth-sorted transmittance: cross terms through T_i
+# ---------------------------------------------------------------------------------------
+
+def test_backward_sorted_t_matches_oracle():
+    slm = SLM(64, 72, 8e-6, 8e-6, (638e-9, 520e-9))
+    sc = surface_scene(50, 60, slm, n_surfaces=2, scale_median_px=5.0)
+    T = O.transmittance(sc)
+    assert (T < 0.95).sum() > 10  # the cross terms matter
+    G = cotangent(51, slm)
+    got = gws.backward(dev(sc), slm, torch.as_tensor(G, device="cuda"), blend=gws.BLEND_SORTED_T)
+    ref = O.backward_field(sc, slm, G.astype(np.complex128), blend=O.BLEND_SORTED_T)
+    _cmp(got, ref)
+    # and the cross terms are not negligible: the order-invariant gradients differ
+    oit = O.backward_field(sc, slm, G.astype(np.complex128), blend=O.BLEND_OIT)
+    assert rel_l2(oit["mean"], ref["mean"]) > 1e-2
+
+
+def test_backward_sorted_t_matches_central_differences():
+    from tests.helpers import qaxis
+    slm = SLM(20, 24, 8e-6, 8e-6, (638e-9, 450e-9))
+    sc = make_scene([[0, 0, 2e-3], [12e-6, -6e-6, 3e-3], [-8e-6, 10e-6, 4e-3]],
+                    [qaxis([1, 0.4, 0], 0.5), qaxis([0.3, 1, 0], 0.4), qaxis([0, 0, 1], 1.0)],
+                    [[25e-6, 18e-6], [20e-6, 22e-6], [15e-6, 17e-6]], [0.8, 0.6, 0.7],
+                    [[0.9, 0.4], [0.5, 0.8], [0.7, 0.6]])
+    G = random_field(52, (2, 20, 24)).astype(np.complex64)
+    Gt = torch.as_tensor(G.astype(np.complex128), device="cuda")
+
+    def loss(s):
+        g = gws.Gaussians(torch.tensor(s.mean, dtype=torch.float64, device="cuda"),
+                          torch.tensor(s.quat, dtype=torch.float32, device="cuda"),
+                          torch.tensor(s.scale, dtype=torch.float32, device="cuda"),
+                          torch.tensor(s.opacity, dtype=torch.float32, device="cuda"),
+                          torch.tensor(s.amp, dtype=torch.float32, device="cuda"))
+        U = gws.forward(g, slm, prec=gws.PREC_FP64, domain=gws.DOMAIN_SPECTRUM, blend=gws.BLEND_SORTED_T)
+        return float((Gt.conj() * U).real.sum())
+
+    got = gws.backward(dev(sc), slm, torch.as_tensor(G, device="cuda"), domain=gws.DOMAIN_SPECTRUM,
+                       blend=gws.BLEND_SORTED_T)
+    for field in GROUPS:
+        arr = getattr(sc, field)
+        fd = np.zeros_like(arr)
+        for idx in np.ndindex(arr.shape):
+            base = arr[idx]
+            h = 1e-11 if field == "mean" else 2e-3 * (abs(base) + (1e-5 if field == "scale" else 0.1))
+            sp = sc.subset(np.arange(sc.n))
+            sm = sc.subset(np.arange(sc.n))
+            getattr(sp, field)[idx] = np.float32(base + h) if field != "mean" else base + h
+            getattr(sm, field)[idx] = np.float32(base - h) if field != "mean" else base - h
+            fd[idx] = (loss(sp) - loss(sm)) / ((getattr(sp, field)[idx] - base) + (base - getattr(sm, field)[idx]))
+        e = rel_l2(got[field].cpu().numpy().astype(np.float64), fd)
+        assert e < 5e-4, (field, e)

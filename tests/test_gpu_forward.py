@@ -276,3 +276,65 @@ def test_encode_matches_oracle(shape):
     d = _circ(gws.encode(torch.as_tensor(f32, device="cuda"), slm, amp_scale=s).cpu().numpy(),
               O.encode(f32.astype(np.complex128), amp_scale=s))
     assert d.max() < 2e-3
+
+
+# ---------------------------------------------------------------------------------------
+# autotuner, CUDA-graph capture, the batched multi-scene workload
+# ---------------------------------------------------------------------------------------
+
+def test_autotune_picks_a_config_and_stays_correct():
+    slm = SLM(120, 176, 8e-6, 8e-6, (638e-9, 520e-9, 450e-9))
+    sc = surface_scene(30, 300, slm, n_surfaces=3)
+    g = dev(sc)
+    best = gws.autotune(g, slm)
+    assert best in (1, 2, 3)
+    u = gws.forward(g, slm, domain=gws.DOMAIN_SPECTRUM).cpu().numpy()  # tile_cfg 0 -> the tuned one
+    assert max(per_lambda_rel(u, O.spectrum(sc, slm))) < TOLMX
+
+
+def test_batched_forward_replays_from_a_cuda_graph():
+    slm = SLM(96, 128, 8e-6, 8e-6, (638e-9, 520e-9, 450e-9))
+    scenes = [surface_scene(40 + k, n, slm, n_surfaces=2) for k, n in enumerate([200, 35, 1, 120, 0, 64])]
+    gs = [dev(s) for s in scenes]
+    S = gws.Slm.of(slm)
+    gws.prepare(S, n_scenes=len(gs))
+    ws = torch.empty(gws.workspace_size([g.n for g in gs], S, gws.make_opts()), dtype=torch.uint8, device="cuda")
+    ref = gws.forward_batched(gs, slm, workspace=ws)
+    outs = [torch.empty_like(r) for r in ref]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        gws.forward_batched(gs, slm, outs=outs, workspace=ws)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    for o in outs:
+        o.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        gws.forward_batched(gs, slm, outs=outs, workspace=ws)
+    graph.replay()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        assert torch.equal(o, r)
+    graph.replay()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        assert torch.equal(o, r)
+
+
+def test_batched_multi_scene_workload():
+    """64 scenes of log-uniform size in [1k, 200k] x 3 wavelengths at 1920x1080 in one call:
+    sampled spectra of three scenes vs the oracle, and bit-equality with single calls."""
+    from paper_2505_06582_gb300.scenes import batched_scenes
+    slm = SLM(1080, 1920, 8e-6, 8e-6, (638e-9, 520e-9, 450e-9))
+    scenes = batched_scenes(slm)
+    gs = [dev(s) for s in scenes]
+    outs = gws.forward_batched(gs, slm, domain=gws.DOMAIN_SPECTRUM)
+    for k in (0, 17, 63):
+        lam, r, c = _samples(slm, 60, k)
+        got = outs[k][torch.as_tensor(lam, dtype=torch.long), torch.as_tensor(r, dtype=torch.long),
+                      torch.as_tensor(c, dtype=torch.long)].cpu().numpy()
+        ref = O.spectrum_at(scenes[k], slm, lam, r, c)
+        assert rel_l2(got, ref) < TOLMX
+        single = gws.forward(gs[k], slm, domain=gws.DOMAIN_SPECTRUM)
+        assert torch.equal(single, outs[k])
