@@ -32,6 +32,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "holograms/s (1M Gaussians, 1920x1080, 3 λ) fwd & fwd+bwd; Gaussian·freq-px/s"
 WORKLOAD = "headline_1m_1080p_3l"
+# DRAM bytes (read + write) of one k_splat_mixed launch on the headline workload, from
+# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (profiles/k_splat_mixed__headline_1m_1080p_3l.md)
+SPLAT_TRAFFIC_MB = 1471.3  # 1.41 GB read + 61.3 MB written (wavelength-major items)
 
 
 def parse():
@@ -41,6 +44,15 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=None, help="override the Gaussian count (testing only)")
+    p.add_argument("--workload", default=WORKLOAD,
+                   help="named workload of paper_2505_06582_gb300.scenes.CONFIGS (default: the headline)")
+    p.add_argument("--prec", default="mixed", choices=["mixed", "fp64"],
+                   help="fp64: the plain FP64 comparison path (forward + encode only)")
+    p.add_argument("--blend", default="oit", choices=["oit", "sorted", "exact"],
+                   help="oit (Eq. 12, the headline), sorted (depth-sorted T at the centres) or exact (Algorithm S2,"
+                        " forward + encode only)")
+    p.add_argument("--traffic-mb", type=float, default=None,
+                   help="DRAM bytes per splat launch from an ncu capture of this workload (MB)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
@@ -152,7 +164,7 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2505_06582_gb300.scenes import config_scene
-    scene, slm = config_scene(WORKLOAD, n=args.n)
+    scene, slm = config_scene(args.workload, n=args.n)
     per = []
     for _ in range(args.warmup):
         cpu_baseline(scene, slm, seconds=2.0)
@@ -162,7 +174,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "holograms/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_gaussians": scene.n, "H": slm.H, "W": slm.W,
+            "config": {"workload": args.workload, "n_gaussians": scene.n, "H": slm.H, "W": slm.W,
                        "n_lambda": slm.n_lambda, "pitch_m": slm.pitch_x},
             "cpu_baseline": {"kind": "oracle", "cores": per[0]["cores"], "sample": per[0]["sample"], "value": v,
                              "unit": "holograms/s"},
@@ -182,24 +194,30 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    scene, slm = config_scene(WORKLOAD, n=args.n)
+    scene, slm = config_scene(args.workload, n=args.n)
     g = gws.Gaussians.from_scene(scene, dev)
     S = gws.Slm.of(slm)
-    have_bwd = True
+    fp64 = args.prec == "fp64"
+    prec = gws.PREC_FP64 if fp64 else gws.PREC_MIXED
+    blend = {"oit": gws.BLEND_OIT, "sorted": gws.BLEND_SORTED_T, "exact": gws.BLEND_EXACT}[args.blend]
+    have_bwd = not fp64 and args.blend != "exact"
     cot = torch.as_tensor(cotangent(11, slm), device=dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     gws.prepare(S)
-    ws = torch.empty(gws.workspace_size([g.n], S, gws.make_opts()), dtype=torch.uint8, device=dev)
+    ws = torch.empty(gws.workspace_size([g.n], S, gws.make_opts(prec=prec, blend=blend)), dtype=torch.uint8,
+                     device=dev)
     # autotune the splat tile on a strided 10% sample of the scene (outside the timed region)
     sub = gws.Gaussians(*(getattr(g, k)[::10].contiguous() for k in ("mean", "quat", "scale", "opacity", "amp")))
-    tile_cfg = gws.autotune(sub, S, workspace=ws)
-    field = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.complex64, device=dev)
+    tile_cfg = gws.autotune(sub, S, workspace=ws) if not fp64 else 0
+    field = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.complex128 if fp64 else torch.complex64, device=dev)
     phase = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.float32, device=dev)
     timers = dict(debug_flags=gws.DEBUG_TIME_KERNELS)
 
     def step(timed_kernels):
-        kw = timers if timed_kernels else {}
+        kw = dict(timers) if timed_kernels else {}
+        kw["prec"] = prec
+        kw["blend"] = blend
         launches = 0
         gws.forward(g, S, out=field, workspace=ws, **kw)
         launches += gws.last_launch_count()
@@ -215,12 +233,7 @@ def run_ours(args):
             t_bwd = gws.kernel_time_ms(gws.TIMER_SPLAT_BWD) if timed_kernels else None
         return launches, t_splat, t_fft, t_enc, t_bwd
 
-    try:
-        step(False)
-    except gws.GwsError as e:
-        if e.code != 6:
-            raise
-        have_bwd = False
+    step(False)
     torch.cuda.synchronize()
     for _ in range(args.warmup):
         step(False)
@@ -273,12 +286,12 @@ def run_ours(args):
         for k in host:
             dbuf[k].copy_(host[k], non_blocking=True)
         gd = gws.Gaussians(dbuf["mean"], dbuf["quat"], dbuf["scale"], dbuf["opacity"], dbuf["amp"])
-        gws.forward(gd, S, out=field, workspace=ws)
+        gws.forward(gd, S, out=field, workspace=ws, prec=prec, blend=blend)
         gws.encode(field, S, out=phase, workspace=ws)
         phase_host.copy_(phase, non_blocking=True)
         if have_bwd:
             cbuf.copy_(cot_host, non_blocking=True)
-            gr = gws.backward(gd, S, cbuf, workspace=ws)
+            gr = gws.backward(gd, S, cbuf, workspace=ws, blend=blend)
             for k in grads_host:
                 grads_host[k].copy_(gr[k], non_blocking=True)
         e1.record(stream)
@@ -287,8 +300,8 @@ def run_ours(args):
     e2e_ms = max_over_ranks(statistics.median(e2e_times), world, dist if world > 1 else None, dev)
 
     # roofline of the dominant kernel (the splat): algorithmic pairs / its event time
-    pairs = gws.footprint_pairs(g, S, workspace=ws)
     dense = g.n * S.H * S.W * S.n_lambda
+    pairs = dense if fp64 else gws.footprint_pairs(g, S, workspace=ws)
     splat = statistics.median(splat_ms)
     sm_mhz = clk.get("sm_mhz") or 1440.0
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -298,12 +311,33 @@ def run_ours(args):
     if bwd_ms:
         dom_ms["splat_bwd"] = statistics.median(bwd_ms)
     fwd_ms = ms - (dom_ms.get("splat_bwd", 0.0))
+    # HBM-bound stages: algorithmic bytes = one read + one write of every slice per pass
+    hbm_peak = 6785.9
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, KeyError, ValueError):
+        pass
+    cplx = 16 if fp64 else 8
+    px = S.H * S.W * S.n_lambda
+    fft_bytes = 2 * 2 * cplx * px  # in-place inverse FFT (read + write) + post-modulation (read + write)
+    enc_bytes = cplx * px + (cplx + 4) * px  # max-|u| pass (read) + encoding (read field, write phase)
+    hbm = {"fft_stage": {"bytes": fft_bytes, "ms": dom_ms["fft"],
+                         "achieved_gbs": fft_bytes / (dom_ms["fft"] * 1e-3) / 1e9},
+           "encode": {"bytes": enc_bytes, "ms": dom_ms["encode"],
+                      "achieved_gbs": enc_bytes / (dom_ms["encode"] * 1e-3) / 1e9}}
+    for v in hbm.values():
+        v["peak_gbs"] = hbm_peak
+        v["frac"] = v["achieved_gbs"] / hbm_peak
 
+    traffic_mb = args.traffic_mb
+    if traffic_mb is None and args.workload == WORKLOAD and not fp64 and args.n is None:
+        traffic_mb = SPLAT_TRAFFIC_MB
     line = {"metric": METRIC, "value": value, "unit": "holograms/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_gaussians": g.n, "H": S.H, "W": S.W, "n_lambda": S.n_lambda,
-                       "pitch_m": S.pitch_x, "blend": "oit", "precision": "mixed", "trunc_eps": 1e-5,
+            "config": {"workload": args.workload, "n_gaussians": g.n, "H": S.H, "W": S.W, "n_lambda": S.n_lambda,
+                       "pitch_m": S.pitch_x, "blend": args.blend, "precision": args.prec,
+                       "trunc_eps": None if fp64 else 1e-5,
                        "step": "forward+encode" + ("+backward" if have_bwd else ""), "tile_cfg": tile_cfg,
                        "l2": "flushed before each timed step (512 MB write)", "parallelism": f"replicas x{world}"},
             "fwd_holograms_per_s": world * 1000.0 / fwd_ms if have_bwd else value,
@@ -311,10 +345,13 @@ def run_ours(args):
                       "dense_pairs_per_s": world * dense / (fwd_ms * 1e-3),
                       "algorithmic_pairs_per_s": world * pairs / (fwd_ms * 1e-3)},
             "kernel_ms": dom_ms,
-            "roofline": {"kernel": "k_splat_mixed", "bound": "alu", "achieved": achieved / 1e9,
+            "roofline": {"kernel": "k_splat_fp64" if fp64 else "k_splat_mixed", "bound": "alu",
+                         "achieved": achieved / 1e9,
                          "peak": peak_pairs / 1e9, "unit": "Gpair/s", "frac": achieved / peak_pairs,
-                         "traffic": None,
-                         "peak_basis": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median sampled) x 6.4 pairs/clk/SM"},
+                         "traffic": None if traffic_mb is None else traffic_mb * 1e6,
+                         "peak_basis": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median sampled) x 6.4 pairs/clk/SM"
+                                       + (" (FP32/MUFU peak; the FP64 path runs on the FP64 pipe)" if fp64 else "")},
+            "hbm": hbm,
             "e2e": {"value": aggregate_rate(world, e2e_ms), "unit": "holograms/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

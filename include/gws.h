@@ -77,8 +77,11 @@ typedef enum {
 } gws_status;
 
 typedef enum {
-    GWS_BLEND_OIT = 0,     /* Eq. 12: order-invariant sum, T_i = 1 */
-    GWS_BLEND_SORTED_T = 1 /* Eq. 5-6 with T_i at the Gaussian's centre (depth-sorted) */
+    GWS_BLEND_OIT = 0,      /* Eq. 12: order-invariant sum, T_i = 1 */
+    GWS_BLEND_SORTED_T = 1, /* Eq. 5-6 with T_i at the Gaussian's centre (depth-sorted) */
+    GWS_BLEND_EXACT = 2     /* Eq. 5-6 with the spatial transmittance map (Algorithm S2): front to back,
+                               u_SLM += c o F(T u_k) H(f, -z_k), T *= 1 - alpha_k, alpha_k = o |u_k|
+                               above t_eps (or binarised at t_binarize); MIXED forward only */
 } gws_blend;
 
 typedef enum {
@@ -145,6 +148,8 @@ typedef struct {
     void *stream;            /* cudaStream_t (NULL = legacy default stream) */
     void *workspace;         /* device scratch, >= gws_workspace_size() bytes */
     size_t workspace_bytes;
+    float t_binarize;        /* EXACT: > 0 binarises alpha (disk occlusion, Algorithm S2); default 0 */
+    int exact_batch;         /* EXACT: Gaussians per batch of fields in flight (0 = 128) */
 } gws_opts;
 
 /* Fills *o with the defaults listed above (OIT, MIXED, FIELD). */
@@ -162,7 +167,8 @@ GWS_API gws_status gws_workspace_size(const int64_t *n, int n_scenes, const gws_
                               size_t *bytes);
 
 /* Per-device set-up for this grid on the current device: creates the cuFFT plans (batch
- * n_lambda; complex64 and, for FP64, complex128) and sets the kernels' shared-memory
+ * n_lambda; n_scenes * n_lambda for batched calls whose outputs are contiguous; the exact
+ * blending batch; complex64 and, for FP64, complex128) and sets the kernels' shared-memory
  * attributes.  May allocate (inside cuFFT).  Call it before capturing gws_* calls into a
  * CUDA graph. */
 GWS_API gws_status gws_prepare(const gws_slm *slm, const gws_opts *opts, int n_scenes);

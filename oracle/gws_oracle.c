@@ -691,6 +691,80 @@ void gwso_backward_spectrum_at(int64_t n, const double *mean, const double *quat
     }
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Exact alpha wave blending (Eq. 5-6 with the spatial transmittance map; Algorithm S2)  */
+/* ------------------------------------------------------------------------------------ */
+
+/* Front to back: for Gaussian k, u_k = the Gaussian's field on its own depth plane (Eq. 10
+ * with the depth component of the mean set to zero, then the centred inverse DFT); the
+ * SLM spectrum gains c_k o_k F(T u_k) H(f, -z_k) (F = the centred forward DFT scaled by
+ * px py, the continuous transform on the grid); alpha_k = o_k |u_k|, kept where
+ * alpha_k > t_eps (binarize > 0: alpha_k = 1 where alpha_k > binarize, else 0); then
+ * T <- T (1 - alpha_k).  T starts at 1.  Writes the SLM spectrum (complex128
+ * [n_lambda][H][W]) and, if T_out is not NULL, the final transmittance map [n_lambda][H][W]. */
+void gwso_exact_awb(int64_t n, const double *mean, const double *quat, const double *scale, const double *opacity,
+                    const double *amp, int n_lambda, const double *wavelengths, int H, int W, double px, double py,
+                    double t_eps, double binarize, double *spec_out, double *T_out) {
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    gwso_depth_order(n, mean, order);
+    const size_t hw = (size_t)H * W;
+    double *uhat = (double *)malloc(sizeof(double) * 2 * hw);
+    double *u = (double *)malloc(sizeof(double) * 2 * hw);
+    double *V = (double *)malloc(sizeof(double) * 2 * hw);
+    double *T = (double *)malloc(sizeof(double) * hw);
+    double dfx = 1.0 / (W * px), dfy = 1.0 / (H * py);
+    for (int l = 0; l < n_lambda; ++l) {
+        double *spec = spec_out + 2 * (size_t)l * hw;
+        memset(spec, 0, sizeof(double) * 2 * hw);
+        for (size_t k = 0; k < hw; ++k) T[k] = 1.0;
+        for (int64_t p = 0; p < n; ++p) {
+            int64_t i = order[p];
+            gauss_t G;
+            load_gaussian(i, mean, quat, scale, opacity, &G);
+            const double zk = G.mu[2];
+            G.mu[2] = 0.0; /* the field on the Gaussian's own plane */
+            for (int r = 0; r < H; ++r)
+                for (int c = 0; c < W; ++c) {
+                    freq_t f = grid_freq(r, c, H, W, px, py, wavelengths[l]);
+                    term_t t = gaussian_term(&G, &f, 0);
+                    uhat[2 * ((size_t)r * W + c)] = t.re;
+                    uhat[2 * ((size_t)r * W + c) + 1] = t.im;
+                }
+            centred_dft2(uhat, u, H, W, +1, dfx * dfy);
+            const double co = amp[i * n_lambda + l] * opacity[i];
+            for (size_t k = 0; k < hw; ++k) {
+                V[2 * k] = co * T[k] * u[2 * k];
+                V[2 * k + 1] = co * T[k] * u[2 * k + 1];
+            }
+            centred_dft2(V, uhat, H, W, -1, px * py); /* uhat <- F(c o T u_k) */
+            for (int r = 0; r < H; ++r)
+                for (int c = 0; c < W; ++c) {
+                    freq_t f = grid_freq(r, c, H, W, px, py, wavelengths[l]);
+                    if (!f.propagating) continue;
+                    double cyc = -f.fz * zk; /* H(f, -z_k) = exp(-j 2 pi f_z z_k) */
+                    cyc -= nearbyint(cyc);
+                    const double cr = cos(TWO_PI * cyc), ci = sin(TWO_PI * cyc);
+                    const size_t o = (size_t)r * W + c;
+                    const double vr = uhat[2 * o], vi = uhat[2 * o + 1];
+                    spec[2 * o] += vr * cr - vi * ci;
+                    spec[2 * o + 1] += vr * ci + vi * cr;
+                }
+            for (size_t k = 0; k < hw; ++k) {
+                double a = opacity[i] * hypot(u[2 * k], u[2 * k + 1]);
+                if (!(a > t_eps)) a = 0.0;
+                if (binarize > 0.0) a = (a > binarize) ? 1.0 : 0.0;
+                T[k] *= (1.0 - a);
+            }
+        }
+        if (T_out) memcpy(T_out + (size_t)l * hw, T, sizeof(double) * hw);
+    }
+    free(T);
+    free(V);
+    free(u);
+    free(uhat);
+    free(order);
+}
+
 int gwso_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -212,3 +212,17 @@ def backward_spectrum_at(scene, slm, gspec, which, phase_match=False):
                                     _p(g), C.c_int64(k), _p(which), _p(out["mean"]), _p(out["quat"]),
                                     _p(out["scale"]), _p(out["opacity"]), _p(out["amp"]))
     return out
+
+
+def exact_awb(scene, slm, t_eps=ALPHA_MIN, binarize=0.0, with_T=False):
+    """Exact alpha wave blending (Algorithm S2): SLM spectrum [n_lambda][H][W] (and T map)."""
+    mean, quat, scale, opa, amp = _scene_arrays(scene)
+    wl = _d(slm.wavelengths)
+    out = np.empty((slm.n_lambda, slm.H, slm.W, 2))
+    T = np.empty((slm.n_lambda, slm.H, slm.W)) if with_T else None
+    lib().gwso_exact_awb(C.c_int64(mean.shape[0]), _p(mean), _p(quat), _p(scale), _p(opa), _p(amp),
+                         C.c_int(slm.n_lambda), _p(wl), C.c_int(slm.H), C.c_int(slm.W), C.c_double(slm.pitch_x),
+                         C.c_double(slm.pitch_y), C.c_double(t_eps), C.c_double(binarize), _p(out),
+                         None if T is None else _p(T))
+    spec = out[..., 0] + 1j * out[..., 1]
+    return (spec, T) if with_T else spec

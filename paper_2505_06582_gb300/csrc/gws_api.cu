@@ -81,6 +81,17 @@ static gws_status get_plan(int H, int W, int batch, int dbl, Plan *out) {
     return GWS_OK;
 }
 
+// a plan that already exists (no creation in the call path)
+static bool cached_plan(int H, int W, int batch, int dbl, Plan *out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plans.find(PlanKey{dev, H, W, batch, dbl, 0});
+    if (it == g_plans.end()) return false;
+    *out = it->second;
+    return true;
+}
+
 static gws_status exec_fft(const Plan &p, void *data, void *work, int dbl, int direction, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     if (cufftSetStream(p.h, s) != CUFFT_SUCCESS) return GWS_ERR_CUDA;
@@ -99,6 +110,8 @@ struct Layout {
     size_t status, queue, amax, gpre, ampc, dkey0, dkey1, dval0, dval1, skey0, skey1, hist, tsorted, tg, tdata;
     size_t rec64, w64, fkey0, fkey1, fval0, fval1, rec, Rr, ikey0, ikey1, ival0, ival1, icount, invrec, gspec, bacc;
     size_t pixtab, dT, tq;
+    size_t ex_U, ex_T, ex_arr, ex_inner, ex_inner_bytes;
+    int ex_B;
     size_t cufft, total;
     int tiles_x, tiles_y, n_tiles, cfg;
 };
@@ -124,6 +137,11 @@ static int default_cfg(const gws_opts *o, const gws_slm *slm) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(std::make_tuple(slm->H, slm->W, slm->n_lambda));
     return it != g_tuned.end() ? it->second : 1;
+}
+
+static int exact_batch(const gws_opts *o) {
+    int B = o->exact_batch > 0 ? o->exact_batch : 128;
+    return B > GWS_MAX_SCENES ? GWS_MAX_SCENES : B;
 }
 
 static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *slm, const gws_opts *o, Layout *L,
@@ -177,8 +195,8 @@ static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *sl
         L->fval1 = P.take(4 * n_rec);
         L->rec = P.take(sizeof(Rec) * n_rec);
         L->Rr = P.take(4 * n_rec);
-        L->ikey0 = P.take(4 * n_items);
-        L->ikey1 = P.take(4 * n_items);
+        L->ikey0 = P.take(8 * n_items);
+        L->ikey1 = P.take(8 * n_items);
         L->ival0 = P.take(4 * n_items);
         L->ival1 = P.take(4 * n_items);
         L->icount = P.take(4 * n_items);
@@ -188,12 +206,42 @@ static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *sl
         L->pixtab = P.take(sizeof(float) * 2 * (size_t)nl * slm->H * slm->W);
         L->dT = P.take(sizeof(double) * n);
     }
+    L->ex_U = L->ex_T = L->ex_arr = L->ex_inner = L->ex_inner_bytes = 0;
+    L->ex_B = 0;
     size_t fft_work = 0;
+    if (o->blend == GWS_BLEND_EXACT && o->prec == GWS_PREC_MIXED) {
+        const int B = exact_batch(o);
+        L->ex_B = B;
+        const size_t hw = (size_t)slm->H * slm->W;
+        L->ex_U = P.take(sizeof(float) * 2 * (size_t)B * nl * hw);
+        L->ex_T = P.take(sizeof(float) * nl * hw);
+        L->ex_arr = P.take((size_t)B * (24 + 16 + 8 + 4 + 4 * nl + 8 + 4 * nl + 4) + 256 * 8);
+        gws_opts inner = *o;  // the batch's fields: the order-invariant forward of B one-Gaussian scenes
+        inner.blend = GWS_BLEND_OIT;
+        inner.domain = GWS_DOMAIN_FIELD;
+        Layout Li;
+        gws_status st = plan_layout(B, B, slm, &inner, &Li, true);
+        if (st != GWS_OK) return st;
+        L->ex_inner_bytes = Li.total;
+        L->ex_inner = P.take(Li.total);
+        Plan p;  // the exact path always transforms (forward DFT of each batch of masked fields, final inverse)
+        st = get_plan(slm->H, slm->W, nl, 0, &p);
+        if (st != GWS_OK) return st;
+        fft_work = std::max(fft_work, p.work);
+        st = get_plan(slm->H, slm->W, B * nl, 0, &p);
+        if (st != GWS_OK) return st;
+        fft_work = std::max(fft_work, p.work);
+    }
     if (need_fft_plans) {
         Plan p;
         gws_status st = get_plan(slm->H, slm->W, nl, o->prec == GWS_PREC_FP64, &p);
         if (st != GWS_OK) return st;
-        fft_work = p.work;
+        fft_work = std::max(fft_work, p.work);
+        if (n_scenes > 1) {  // one batched transform when the scenes' outputs are contiguous
+            st = get_plan(slm->H, slm->W, n_scenes * nl, o->prec == GWS_PREC_FP64, &p);
+            if (st != GWS_OK) return st;
+            fft_work = std::max(fft_work, p.work);
+        }
     }
     L->cufft = P.take(fft_work);
     L->total = P.cur;
@@ -218,7 +266,9 @@ static gws_status check_slm(const gws_slm *slm) {
 
 static gws_status check_opts(const gws_opts *o) {
     if (!o) return GWS_ERR_INVALID_ARG;
-    if (o->blend != GWS_BLEND_OIT && o->blend != GWS_BLEND_SORTED_T) return GWS_ERR_INVALID_ARG;
+    if (o->blend != GWS_BLEND_OIT && o->blend != GWS_BLEND_SORTED_T && o->blend != GWS_BLEND_EXACT)
+        return GWS_ERR_INVALID_ARG;
+    if (!(o->t_binarize >= 0.f && o->t_binarize < 1.f) || o->exact_batch < 0) return GWS_ERR_INVALID_ARG;
     if (o->prec != GWS_PREC_FP64 && o->prec != GWS_PREC_MIXED) return GWS_ERR_INVALID_ARG;
     if (o->domain != GWS_DOMAIN_FIELD && o->domain != GWS_DOMAIN_SPECTRUM) return GWS_ERR_INVALID_ARG;
     if (!(o->trunc_eps > 0.f && o->trunc_eps < 1.f)) return GWS_ERR_INVALID_ARG;
@@ -361,8 +411,88 @@ static int num_sms() {
 }
 
 static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, int n_scenes, const gws_slm *slm,
+                               const gws_opts *o, void *const *out);
+
+// Exact alpha wave blending (Algorithm S2), front to back in batches of B Gaussians; see
+// gws_exact.cu.  The batch's fields at their own planes come from the batched forward (one
+// single-Gaussian scene each, depth component of the mean zeroed, c = o = 1).
+static gws_status exact_forward(const gws_gaussians *scene, long long n, const gws_slm *slm, const gws_opts *o,
+                                const Layout &L, const Front &F, void *out, cudaStream_t s) {
+    const int nl = slm->n_lambda, H = slm->H, W = slm->W;
+    const long long hw = (long long)H * W;
+    const double dfx = 1.0 / (W * slm->pitch_x), dfy = 1.0 / (H * slm->pitch_y);
+    const int B = L.ex_B;
+    float2 *acc = static_cast<float2 *>(out);
+    float2 *U = at<float2>(o, L.ex_U);
+    float *Tm = at<float>(o, L.ex_T);
+    char *arr = at<char>(o, L.ex_arr);
+    ExactBatch E;
+    E.mean = reinterpret_cast<double *>(arr);
+    E.zk = E.mean + 3 * B;
+    E.quat = reinterpret_cast<float *>(E.zk + B);
+    E.scale = E.quat + 4 * B;
+    E.opacity = E.scale + 2 * B;
+    E.amp = E.opacity + B;
+    E.co = E.amp + (size_t)B * nl;
+    E.ok = E.co + (size_t)B * nl;
+    InvLam il;
+    std::memset(&il, 0, sizeof il);
+    for (int l = 0; l < nl; ++l) il.v[l] = 1.0 / slm->wavelengths[l];
+    float2 *pixtab = at<float2>(o, L.pixtab);
+    CU(launch_pixtab(nl, H, W, dfx, dfy, il, pixtab, s));
+    CU(cudaMemsetAsync(acc, 0, sizeof(float2) * (size_t)nl * hw, s));
+    CU(launch_fill(Tm, (long long)nl * hw, 1.f, s));
+    gws_opts inner = *o;
+    inner.blend = GWS_BLEND_OIT;
+    inner.domain = GWS_DOMAIN_FIELD;
+    inner.debug_flags &= ~(unsigned)GWS_DEBUG_TIME_KERNELS;
+    inner.workspace = at<char>(o, L.ex_inner);
+    inner.workspace_bytes = L.ex_inner_bytes;
+    Plan p;
+    GS(get_plan(H, W, nl, 0, &p));
+    std::vector<gws_gaussians> gb(B);
+    std::vector<int64_t> ones(B, 1);
+    std::vector<void *> outs(B);
+    for (int k = 0; k < B; ++k) {
+        gb[k].mean = E.mean + 3 * k;
+        gb[k].quat = E.quat + 4 * k;
+        gb[k].scale = E.scale + 2 * k;
+        gb[k].opacity = E.opacity + k;
+        gb[k].amp = E.amp + (size_t)k * nl;
+        outs[k] = U + (size_t)k * nl * hw;
+    }
+    timer_mark(o, GWS_TIMER_SPLAT_FWD, 0, s);  // the whole front-to-back loop
+    for (long long b0 = 0; b0 < n; b0 += B) {
+        const int nb = (int)std::min<long long>(B, n - b0);
+        CU(launch_exact_gather(F.sorted, b0, nb, scene, nl, E, s));
+        GS(forward_impl(gb.data(), ones.data(), nb, slm, &inner, outs.data()));
+        CU(launch_exact_mask(U, Tm, E, nb, nl, hw, o->alpha_min, o->t_binarize, s));
+        // centred forward DFT scaled by px py: the spectrum of each masked field
+        CU(launch_modulate(U, 0, nb * nl, H, W, 1.0, 1, s));
+        Plan pb;
+        if (nb == B && cached_plan(H, W, B * nl, 0, &pb)) {
+            GS(exec_fft(pb, U, at<char>(o, L.cufft), 0, CUFFT_FORWARD, s));
+        } else {
+            for (int k = 0; k < nb; ++k)
+                GS(exec_fft(p, U + (size_t)k * nl * hw, at<char>(o, L.cufft), 0, CUFFT_FORWARD, s));
+        }
+        CU(launch_modulate(U, 0, nb * nl, H, W, slm->pitch_x * slm->pitch_y, 2, s));
+        CU(launch_exact_accum(U, acc, pixtab, E, nb, nl, H, W, dfx, dfy, il, s));
+    }
+    timer_mark(o, GWS_TIMER_SPLAT_FWD, 1, s);
+    timer_mark(o, GWS_TIMER_FFT, 0, s);
+    if (o->domain == GWS_DOMAIN_FIELD) {
+        CU(launch_modulate(acc, 0, nl, H, W, 1.0, 3, s));
+        GS(exec_fft(p, acc, at<char>(o, L.cufft), 0, CUFFT_INVERSE, s));
+        CU(launch_modulate(acc, 0, nl, H, W, dfx * dfy, 0, s));
+    }
+    timer_mark(o, GWS_TIMER_FFT, 1, s);
+    timer_mark(o, GWS_TIMER_TOTAL, 1, s);
+    return GWS_OK;
+}
+
+static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, int n_scenes, const gws_slm *slm,
                                const gws_opts *o, void *const *out) {
-    t_launches = 0;
     GS(check_slm(slm));
     GS(check_opts(o));
     if (n_scenes < 1 || n_scenes > GWS_MAX_SCENES || !n || !out) return GWS_ERR_INVALID_ARG;
@@ -389,6 +519,11 @@ static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, in
         return GWS_OK;
     }
     Front F;
+    if (o->blend == GWS_BLEND_EXACT) {
+        if (dbl || n_scenes != 1) return GWS_ERR_UNSUPPORTED;
+        GS(run_front(scenes, n, n_scenes, slm, o, L, false, &F, s));
+        return exact_forward(scenes, n_total, slm, o, L, F, out[0], s);
+    }
     GS(run_front(scenes, n, n_scenes, slm, o, L, o->blend == GWS_BLEND_SORTED_T, &F, s));
     const double dfx = 1.0 / (W * slm->pitch_x), dfy = 1.0 / (H * slm->pitch_y);
     if (dbl) {
@@ -416,13 +551,14 @@ static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, in
         GS(run_records(F, slm, o, L, 0, s, &rec));
         const int n_seg = n_scenes * nl;
         const TileCfg tc = tile_cfg(L.cfg);
-        unsigned *ik0 = at<unsigned>(o, L.ikey0), *ik1 = at<unsigned>(o, L.ikey1);
+        unsigned long long *ik0 = at<unsigned long long>(o, L.ikey0), *ik1 = at<unsigned long long>(o, L.ikey1);
         unsigned *iv0 = at<unsigned>(o, L.ival0), *iv1 = at<unsigned>(o, L.ival1);
         int *icount = at<int>(o, L.icount);
         CU(launch_items(at<float>(o, L.Rr), F.S, n_seg, H, W, tc.tw, tc.th, L.tiles_x, L.n_tiles, dfx, dfy, ik0, iv0,
                         icount, s));
         const long long n_items = (long long)n_seg * L.n_tiles;
-        CU(radix_sort<unsigned>(ik0, ik1, iv0, iv1, n_items, 0, 32, at<unsigned>(o, L.hist), s));
+        CU(radix_sort<unsigned long long>(ik0, ik1, iv0, iv1, n_items, 0, 32 + seg_bits(n_seg), at<unsigned>(o, L.hist),
+                                          s));
         CU(cudaMemsetAsync(at<int>(o, L.queue), 0, 16, s));
         SplatArgs a;
         std::memset(&a, 0, sizeof a);
@@ -451,12 +587,20 @@ static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, in
         timer_mark(o, GWS_TIMER_SPLAT_FWD, 1, s);
     }
     if (fft) {
-        Plan p;
+        Plan p, pb;
         GS(get_plan(H, W, nl, dbl, &p));
         timer_mark(o, GWS_TIMER_FFT, 0, s);
-        for (int k = 0; k < n_scenes; ++k) {
-            GS(exec_fft(p, out[k], at<char>(o, L.cufft), dbl, CUFFT_INVERSE, s));
-            CU(launch_modulate(out[k], dbl, nl, H, W, dfx * dfy, 0, s));
+        bool contiguous = n_scenes > 1;
+        for (int k = 1; k < n_scenes && contiguous; ++k)
+            contiguous = static_cast<char *>(out[k]) == static_cast<char *>(out[0]) + (size_t)k * nl * slice;
+        if (contiguous && cached_plan(H, W, n_scenes * nl, dbl, &pb)) {
+            GS(exec_fft(pb, out[0], at<char>(o, L.cufft), dbl, CUFFT_INVERSE, s));
+            CU(launch_modulate(out[0], dbl, n_scenes * nl, H, W, dfx * dfy, 0, s));
+        } else {
+            for (int k = 0; k < n_scenes; ++k) {
+                GS(exec_fft(p, out[k], at<char>(o, L.cufft), dbl, CUFFT_INVERSE, s));
+                CU(launch_modulate(out[k], dbl, nl, H, W, dfx * dfy, 0, s));
+            }
         }
         timer_mark(o, GWS_TIMER_FFT, 1, s);
     }
@@ -528,6 +672,10 @@ gws_status gws_prepare(const gws_slm *slm, const gws_opts *opts, int n_scenes) {
     CU(prepare_bwd_kernels());
     Plan p;
     GS(get_plan(slm->H, slm->W, slm->n_lambda, 0, &p));
+    if (n_scenes > 1) GS(get_plan(slm->H, slm->W, n_scenes * slm->n_lambda, opts->prec == GWS_PREC_FP64, &p));
+    if (opts->blend == GWS_BLEND_EXACT) {
+        GS(get_plan(slm->H, slm->W, exact_batch(opts) * slm->n_lambda, 0, &p));
+    }
     return get_plan(slm->H, slm->W, slm->n_lambda, opts->prec == GWS_PREC_FP64, &p);
 }
 
@@ -536,12 +684,15 @@ gws_status gws_forward(const gws_gaussians *g, int64_t n, const gws_slm *slm, co
     std::memset(&empty, 0, sizeof empty);
     void *outs[1] = {field_out};
     int64_t ns[1] = {n};
+    t_launches = 0;
     return forward_impl(g ? g : &empty, ns, 1, slm, opts, outs);
 }
 
 gws_status gws_forward_batched(const gws_gaussians *scenes, const int64_t *n, int n_scenes, const gws_slm *slm,
                                const gws_opts *opts, void *const *field_out) {
     if (!scenes) return GWS_ERR_INVALID_ARG;
+    if (opts && opts->blend == GWS_BLEND_EXACT) return GWS_ERR_UNSUPPORTED;
+    t_launches = 0;
     return forward_impl(scenes, n, n_scenes, slm, opts, field_out);
 }
 

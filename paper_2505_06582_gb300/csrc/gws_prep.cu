@@ -527,8 +527,10 @@ __global__ void k_count_pairs(const GPre *__restrict__ gp, long long n, int n_la
 
 // work items: (segment, tile) -> number of leading records whose footprint radius reaches
 // the tile (records are in decreasing-radius order); key orders items by decreasing work
+// Items are ordered segment-major (one wavelength's records -- at most a few hundred MB --
+// stay resident in L2 while all CTAs stream them), longest first inside a segment.
 __global__ void k_items(const float *__restrict__ Rr, Segs S, int n_seg, int H, int W, int tw, int th, int tiles_x,
-                        int n_tiles, double dfx, double dfy, unsigned *__restrict__ ikey,
+                        int n_tiles, double dfx, double dfy, unsigned long long *__restrict__ ikey,
                         unsigned *__restrict__ ival, int *__restrict__ icount) {
     const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= (long long)n_seg * n_tiles) return;
@@ -548,7 +550,7 @@ __global__ void k_items(const float *__restrict__ Rr, Segs S, int n_seg, int H, 
         else hi = mid;
     }
     icount[it] = (int)lo;
-    ikey[it] = 0xFFFFFFFFu - (unsigned)lo;
+    ikey[it] = ((unsigned long long)seg << 32) | (0xFFFFFFFFu - (unsigned)lo);
     ival[it] = (unsigned)it;
 }
 
@@ -590,9 +592,11 @@ __global__ void k_modulate(typename Cx<R>::T *__restrict__ data, int n_slices, i
         sc = scale;
     } else if (mode == 1) {  // e^{+j2pi(m0 r/H + n0 c/W)}
         num = mod_num2(h2, r, 1, w2, c, 1, H, W);
-    } else {  // e^{-j2pi(m0 r0/H + n0 c0/W)} e^{+j2pi(m r0/H + n c0/W)}
+    } else if (mode == 2) {  // e^{-j2pi(m0 r0/H + n0 c0/W)} e^{+j2pi(m r0/H + n c0/W)}
         num = mod_num2(r, h2, 1, c, w2, 1, H, W) - mod_num2(h2, h2, 1, w2, w2, 1, H, W);
         sc = scale;
+    } else {  // forward pre-modulation e^{-j2pi(m r0/H + n c0/W)} (natural-layout spectrum -> cuFFT input)
+        num = -mod_num2(r, h2, 1, c, w2, 1, H, W);
     }
     if (num < 0) num += hw;
     if (2 * num > hw) num -= hw;  // |angle| <= 1/2 cycle
@@ -750,7 +754,7 @@ cudaError_t launch_foot_inspect(const GPre *gp, long long n, float rho, float dz
 }
 
 cudaError_t launch_items(const float *Rr, const Segs &S, int n_seg, int H, int W, int tw, int th, int tiles_x,
-                         int n_tiles, double dfx, double dfy, unsigned *ikey, unsigned *ival, int *icount,
+                         int n_tiles, double dfx, double dfy, unsigned long long *ikey, unsigned *ival, int *icount,
                          cudaStream_t s) {
     const long long n = (long long)n_seg * n_tiles;
     k_items<<<nblk(n, 256), 256, 0, s>>>(Rr, S, n_seg, H, W, tw, th, tiles_x, n_tiles, dfx, dfy, ikey, ival, icount);

@@ -29,12 +29,30 @@ cudaError_t launch_gather(const unsigned long long *key, const unsigned *val, co
                           cudaStream_t s);
 cudaError_t launch_foot_inspect(const GPre *gp, long long n, float rho, float dzmax, float *out, cudaStream_t s);
 cudaError_t launch_items(const float *Rr, const Segs &S, int n_seg, int H, int W, int tw, int th, int tiles_x,
-                         int n_tiles, double dfx, double dfy, unsigned *ikey, unsigned *ival, int *icount,
+                         int n_tiles, double dfx, double dfy, unsigned long long *ikey, unsigned *ival, int *icount,
                          cudaStream_t s);
 cudaError_t launch_count_pairs(const GPre *gp, long long n, int n_lambda, const FootParams &F, int H, int W,
                                double dfx, double dfy, unsigned long long *acc, cudaStream_t s);
 cudaError_t launch_modulate(void *data, int prec64, int n_slices, int H, int W, double scale, int mode,
                             cudaStream_t s);
+struct ExactBatch {  // one batch of exact blending (Gaussians in depth order)
+    double *mean;    // [B][3], depth component zeroed
+    float *quat;     // [B][4]
+    float *scale;    // [B][2]
+    float *opacity;  // [B] (1: the field itself)
+    float *amp;      // [B][L] (1)
+    double *zk;      // [B] depths
+    float *co;       // [B][L] c o
+    float *ok;       // [B] o
+};
+cudaError_t launch_exact_gather(const unsigned *sorted, long long b0, int nb, const gws_gaussians *g, int L,
+                                const ExactBatch &E, cudaStream_t s);
+cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s);
+cudaError_t launch_exact_mask(float2 *U, float *T, const ExactBatch &E, int nb, int L, long long hw, float t_eps,
+                              float t_bin, cudaStream_t s);
+cudaError_t launch_exact_accum(const float2 *V, float2 *acc, const float2 *pixtab, const ExactBatch &E, int nb, int L,
+                               int H, int W, double dfx, double dfy, const InvLam &il, cudaStream_t s);
+
 cudaError_t launch_encode(const void *field, int prec64, int n_lambda, int H, int W, unsigned long long *amax2,
                           double amp_scale, float *out, cudaStream_t s);
 

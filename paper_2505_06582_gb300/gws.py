@@ -18,7 +18,7 @@ import torch
 
 from . import _build
 
-BLEND_OIT, BLEND_SORTED_T = 0, 1
+BLEND_OIT, BLEND_SORTED_T, BLEND_EXACT = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 DOMAIN_FIELD, DOMAIN_SPECTRUM = 0, 1
 DEBUG_FORCE_TIMEOUT = 1
@@ -50,7 +50,8 @@ class _Opts(C.Structure):
     _fields_ = [("blend", C.c_int), ("prec", C.c_int), ("domain", C.c_int), ("phase_match", C.c_int),
                 ("trunc_eps", C.c_float), ("alpha_min", C.c_float), ("tile_cfg", C.c_int),
                 ("debug_flags", C.c_uint32), ("timeout_cycles", C.c_uint64), ("stream", C.c_void_p),
-                ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+                ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t), ("t_binarize", C.c_float),
+                ("exact_batch", C.c_int)]
 
 
 _lib = None
@@ -173,13 +174,15 @@ _WS = _Workspace()
 
 
 def make_opts(blend=BLEND_OIT, prec=PREC_MIXED, domain=DOMAIN_FIELD, phase_match=False, trunc_eps=1e-5,
-              alpha_min=1.0 / 255.0, tile_cfg=0, debug_flags=0, timeout_cycles=2_000_000_000, stream=None):
+              alpha_min=1.0 / 255.0, tile_cfg=0, debug_flags=0, timeout_cycles=2_000_000_000, stream=None,
+              t_binarize=0.0, exact_batch=0):
     lib = load()
     o = _Opts()
     lib.gws_opts_default(C.byref(o))
     o.blend, o.prec, o.domain, o.phase_match = int(blend), int(prec), int(domain), int(bool(phase_match))
     o.trunc_eps, o.alpha_min, o.tile_cfg = float(trunc_eps), float(alpha_min), int(tile_cfg)
     o.debug_flags, o.timeout_cycles = int(debug_flags), int(timeout_cycles)
+    o.t_binarize, o.exact_batch = float(t_binarize), int(exact_batch)
     if stream is None:
         stream = torch.cuda.current_stream()
     o.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))

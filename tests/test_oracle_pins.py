@@ -487,3 +487,49 @@ def test_subset_backward_equals_full_backward():
     sub = O.backward_spectrum_at(sc, slm, G, [4, 1])
     for k in full:
         assert np.allclose(sub[k], full[k][[4, 1]], rtol=1e-13, atol=0), k
+
+
+# ---------------------------------------------------------------------------------------
+# exact alpha wave blending (Algorithm S2)
+# ---------------------------------------------------------------------------------------
+
+def test_exact_awb_without_occlusion_is_the_order_invariant_sum():
+    """alpha below t_eps everywhere -> T = 1 -> F(F^-1(u_k)) H(f, -z_k) sums to Eq. 12 exactly:
+    pins the DFT scales and the propagation sign against the independently pinned closed form."""
+    slm = SLM(24, 32, 8e-6, 6e-6, (638e-9, 450e-9))
+    sc = uniform_scene(61, 7, slm, scale_median_px=2.5)
+    sc.opacity[:] = 0.9 / 255
+    assert np.abs(O.exact_awb(sc, slm) - O.spectrum(sc, slm)).max() < 1e-10 * np.abs(O.spectrum(sc, slm)).max()
+    one = sc.subset([3])
+    one.opacity[:] = 0.8
+    assert rel_l2(O.exact_awb(one, slm), O.spectrum(one, slm)) < 1e-11
+
+
+def test_exact_awb_transmittance_map_by_hand():
+    """Untilted in-focus Gaussians (|u_k| = G_k on the grid): T = prod (1 - o_k G_k) where o_k G_k > t_eps."""
+    slm = SLM(48, 48, 8e-6, 8e-6, (520e-9,))
+    s1, s2 = 4 * 8e-6, 3 * 8e-6
+    sc = make_scene([[0, 0, 1e-3], [24e-6, -16e-6, 3e-3]], [[1, 0, 0, 0]] * 2, [[s1, s1], [s2, s2]], [0.7, 0.5],
+                    [[1.0], [1.0]])
+    _, T = O.exact_awb(sc, slm, with_T=True)
+    xs = (np.arange(48) - 24) * 8e-6
+    X, Y = np.meshgrid(xs, xs)
+    a1 = 0.7 * np.exp(-0.5 * (X ** 2 + Y ** 2) / s1 ** 2)
+    a2 = 0.5 * np.exp(-0.5 * ((X - 24e-6) ** 2 + (Y + 16e-6) ** 2) / s2 ** 2)
+    ref = (1 - np.where(a1 > 1 / 255, a1, 0)) * (1 - np.where(a2 > 1 / 255, a2, 0))
+    assert np.abs(T[0] - ref).max() < 1e-9
+
+
+def test_exact_awb_binarized_disk_hides_what_is_behind():
+    """t_binarize (disk occlusion): an opaque disk in front of a small Gaussian hides it."""
+    # the rear Gaussian (2.5 px) is band-limited on this grid only by e^-31, so its field has
+    # no ringing outside the disk (|u_front| > 0.05 within ~29 px of the front's centre)
+    slm = SLM(80, 80, 8e-6, 8e-6, (520e-9,))
+    front = make_scene([[0, 0, 2e-3]], [[1, 0, 0, 0]], [[12 * 8e-6, 12 * 8e-6]], [1.0], [[0.6]])
+    rear = make_scene([[8e-6, 0, 5e-3]], [[1, 0, 0, 0]], [[2.5 * 8e-6, 2.5 * 8e-6]], [0.9], [[0.8]])
+    both = rear.concat(front)
+    got = O.exact_awb(both, slm, binarize=0.05)
+    only_front = O.exact_awb(front, slm, binarize=0.05)
+    assert rel_l2(got, only_front) < 1e-9
+    # without the disk the rear Gaussian shows through (soft alpha)
+    assert rel_l2(O.exact_awb(both, slm), only_front) > 1e-3
