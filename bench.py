@@ -32,9 +32,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "holograms/s (1M Gaussians, 1920x1080, 3 λ) fwd & fwd+bwd; Gaussian·freq-px/s"
 WORKLOAD = "headline_1m_1080p_3l"
-# DRAM bytes (read + write) of one k_splat_mixed launch on the headline workload, from
-# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (profiles/k_splat_mixed__headline_1m_1080p_3l.md)
-SPLAT_TRAFFIC_MB = 1471.3  # 1.41 GB read + 61.3 MB written (wavelength-major items)
+# DRAM bytes (read + write) of one launch of each splat on the headline workload, from
+# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (profiles/k_splat_*__headline_1m_1080p_3l.md)
+SPLAT_TRAFFIC_MB = 1559.1  # 1.49 GB read + 69.1 MB written
+BWD_TRAFFIC_MB = 722.7     # 421.5 MB read + 301.2 MB written (wavelength-major work items)
+# Per (Gaussian, frequency) pair: the forward needs ex2, sin and cos on the MUFU (32, 16, 16 per
+# SM per clock): 1 / (1/32 + 2/16) = 6.4 pairs/clk/SM; its 17 FP32 lane-ops (8 affine, 2 exponent,
+# 1 |g| e, 3 phase reduction, 1 sin/cos prescale, 2 accumulations) allow 128 / 17 = 7.5.  The
+# backward adds the gradient products and the 12 moment sums: 36 FP32 lane-ops per pair
+# (8 affine, 2 exponent, 3 phase reduction, 1 prescale, 2 sign(g) e products, 4 complex product,
+# 2 |g| products, 2 a'/b' products, 12 moments) -> 128 / 36 = 3.56 pairs/clk/SM, below its MUFU 6.4.
+# (The sin/cos argument scaling is counted once; counting it twice would lower both peaks.)
+FWD_PAIRS_PER_CLK = 6.4
+BWD_PAIRS_PER_CLK = 128.0 / 36.0
 
 
 def parse():
@@ -299,17 +309,33 @@ def run_ours(args):
         e2e_times.append(e0.elapsed_time(e1))
     e2e_ms = max_over_ranks(statistics.median(e2e_times), world, dist if world > 1 else None, dev)
 
-    # roofline of the dominant kernel (the splat): algorithmic pairs / its event time
+    # rooflines of the two splats: algorithmic pairs (the footprint pairs both visit) / event time
     dense = g.n * S.H * S.W * S.n_lambda
     pairs = dense if fp64 else gws.footprint_pairs(g, S, workspace=ws)
     splat = statistics.median(splat_ms)
     sm_mhz = clk.get("sm_mhz") or 1440.0
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_pairs = n_sm * sm_mhz * 1e6 * 6.4  # issue-bound: 128 lanes / 20 issues per pair (= MUFU bound, 6.4/clk/SM)
-    achieved = pairs / (splat * 1e-3)
     dom_ms = {"splat_fwd": splat, "fft": statistics.median(fft_ms), "encode": statistics.median(enc_ms)}
     if bwd_ms:
         dom_ms["splat_bwd"] = statistics.median(bwd_ms)
+    full_size = args.workload == WORKLOAD and not fp64 and args.n is None and args.blend == "oit"
+
+    def roof(kernel, kms, per_clk, basis, traffic_mb):
+        achieved = pairs / (kms * 1e-3)
+        peak = n_sm * sm_mhz * 1e6 * per_clk
+        return {"kernel": kernel, "bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
+                "frac": achieved / peak, "traffic": None if traffic_mb is None else traffic_mb * 1e6,
+                "peak_basis": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median sampled) x {per_clk:.2f} pairs/clk/SM, " + basis}
+
+    rooflines = {"splat_fwd": roof(
+        "k_splat_fp64" if fp64 else "k_splat_mixed", splat, FWD_PAIRS_PER_CLK,
+        "MUFU bound (ex2 + sin + cos per pair)" + (" (FP32/MUFU peak; the FP64 path runs on the FP64 pipe)" if fp64 else ""),
+        args.traffic_mb if args.traffic_mb is not None else (SPLAT_TRAFFIC_MB if full_size else None))}
+    if bwd_ms:
+        rooflines["splat_bwd"] = roof("k_splat_bwd", dom_ms["splat_bwd"], BWD_PAIRS_PER_CLK,
+                                      "FP32 bound (36 lane-ops per pair at 128 lanes/clk/SM; MUFU bound 6.4)",
+                                      BWD_TRAFFIC_MB if full_size else None)
+    dominant = max(rooflines, key=lambda k: dom_ms[k])
     fwd_ms = ms - (dom_ms.get("splat_bwd", 0.0))
     # HBM-bound stages: algorithmic bytes = one read + one write of every slice per pass
     hbm_peak = 6785.9
@@ -329,9 +355,6 @@ def run_ours(args):
         v["peak_gbs"] = hbm_peak
         v["frac"] = v["achieved_gbs"] / hbm_peak
 
-    traffic_mb = args.traffic_mb
-    if traffic_mb is None and args.workload == WORKLOAD and not fp64 and args.n is None:
-        traffic_mb = SPLAT_TRAFFIC_MB
     line = {"metric": METRIC, "value": value, "unit": "holograms/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -345,12 +368,8 @@ def run_ours(args):
                       "dense_pairs_per_s": world * dense / (fwd_ms * 1e-3),
                       "algorithmic_pairs_per_s": world * pairs / (fwd_ms * 1e-3)},
             "kernel_ms": dom_ms,
-            "roofline": {"kernel": "k_splat_fp64" if fp64 else "k_splat_mixed", "bound": "alu",
-                         "achieved": achieved / 1e9,
-                         "peak": peak_pairs / 1e9, "unit": "Gpair/s", "frac": achieved / peak_pairs,
-                         "traffic": None if traffic_mb is None else traffic_mb * 1e6,
-                         "peak_basis": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median sampled) x 6.4 pairs/clk/SM"
-                                       + (" (FP32/MUFU peak; the FP64 path runs on the FP64 pipe)" if fp64 else "")},
+            "roofline": rooflines[dominant],
+            "rooflines": rooflines,
             "hbm": hbm,
             "e2e": {"value": aggregate_rate(world, e2e_ms), "unit": "holograms/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

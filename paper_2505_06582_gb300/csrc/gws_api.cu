@@ -109,7 +109,7 @@ static gws_status exec_fft(const Plan &p, void *data, void *work, int dbl, int d
 struct Layout {
     size_t status, queue, amax, gpre, ampc, dkey0, dkey1, dval0, dval1, skey0, skey1, hist, tsorted, tg, tdata;
     size_t rec64, w64, fkey0, fkey1, fval0, fval1, rec, Rr, ikey0, ikey1, ival0, ival1, icount, invrec, gspec, bacc;
-    size_t pixtab, dT, tq;
+    size_t pixtab, gtiles, dT, tq;
     size_t ex_U, ex_T, ex_arr, ex_inner, ex_inner_bytes;
     int ex_B;
     size_t cufft, total;
@@ -186,7 +186,7 @@ static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *sl
         L->w64 = P.take(8 * n * nl);
         L->fkey0 = L->fkey1 = L->fval0 = L->fval1 = L->rec = L->Rr = 0;
         L->ikey0 = L->ikey1 = L->ival0 = L->ival1 = L->icount = L->invrec = L->gspec = L->bacc = 0;
-        L->pixtab = L->dT = 0;
+        L->pixtab = L->gtiles = L->dT = 0;
     } else {
         L->rec64 = L->w64 = 0;
         L->fkey0 = P.take(8 * n_rec);
@@ -203,7 +203,9 @@ static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *sl
         L->invrec = P.take(4 * n_rec);
         L->gspec = P.take(sizeof(float) * 2 * (size_t)nl * slm->H * slm->W);
         L->bacc = P.take(sizeof(double) * 13 * n_rec);
-        L->pixtab = P.take(sizeof(float) * 2 * (size_t)nl * slm->H * slm->W);
+        // the backward's tile-major tables (also the natural-layout table of the exact blend)
+        L->pixtab = P.take(std::max(bwd_table_bytes(nl, slm->H, slm->W), sizeof(float) * 2 * (size_t)nl * slm->H * slm->W));
+        L->gtiles = P.take(bwd_table_bytes(nl, slm->H, slm->W));
         L->dT = P.take(sizeof(double) * n);
     }
     L->ex_U = L->ex_T = L->ex_arr = L->ex_inner = L->ex_inner_bytes = 0;
@@ -439,7 +441,7 @@ static gws_status exact_forward(const gws_gaussians *scene, long long n, const g
     std::memset(&il, 0, sizeof il);
     for (int l = 0; l < nl; ++l) il.v[l] = 1.0 / slm->wavelengths[l];
     float2 *pixtab = at<float2>(o, L.pixtab);
-    CU(launch_pixtab(nl, H, W, dfx, dfy, il, pixtab, s));
+    CU(launch_pixtab(nl, H, W, dfx, dfy, il, 64, 32, pixtab, s));  // the tiles of k_exact_accum
     CU(cudaMemsetAsync(acc, 0, sizeof(float2) * (size_t)nl * hw, s));
     CU(launch_fill(Tm, (long long)nl * hw, 1.f, s));
     gws_opts inner = *o;
@@ -891,13 +893,13 @@ gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, c
     InvLam il;
     std::memset(&il, 0, sizeof il);
     for (int l = 0; l < nl; ++l) il.v[l] = 1.0 / slm->wavelengths[l];
-    float2 *pixtab = at<float2>(opts, L.pixtab);
-    CU(launch_pixtab(nl, H, W, dfx, dfy, il, pixtab, s));
+    float4 *pixtab = at<float4>(opts, L.pixtab), *gtiles = at<float4>(opts, L.gtiles);
+    CU(launch_bwd_tables(nl, H, W, dfx, dfy, il, gsrc, gtiles, pixtab, s));
     CU(cudaMemsetAsync(at<int>(opts, L.queue), 0, 16, s));
     BwdArgs a;
     std::memset(&a, 0, sizeof a);
     a.rec = rec;
-    a.gspec = gsrc;
+    a.gtiles = gtiles;
     a.pixtab = pixtab;
     a.acc = at<double>(opts, L.bacc);
     a.queue = at<int>(opts, L.queue);

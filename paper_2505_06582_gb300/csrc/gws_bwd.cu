@@ -6,11 +6,14 @@
 //
 // The spectra are recomputed, never stored.  A work item is a block of BB consecutive
 // records of one wavelength (footprint order, so a block's footprints are alike).  The CTA
-// walks the frequency tiles of the block's footprint union; per tile it stages G and a
-// per-pixel table (f_z - f0_z, log2(1/f_z)) in shared memory with cp.async (zero fill past
-// the grid), culls each record exactly, and one warp takes one record over the tile's
-// 2048 pixels (lanes over pixels), accumulating 16 FP32 partial sums; these are reduced
-// across the warp and merged per tile into 13 FP64 totals per record in shared memory:
+// walks the 64 x 32 frequency tiles of the block's footprint union; per tile it stages G and
+// a per-pixel table (f_z - f0_z, log2 f_z) in shared memory with cp.async from copies laid
+// out tile by tile (k_gtiles, k_pixtab_tiles: zero / +inf padded past the grid, so a tile is
+// one contiguous 16 KB block per array, and a lane's two columns c and c + 32 of a row sit
+// side by side for the packed f32x2 arithmetic), culls each record exactly, and one warp
+// takes one record over the tile (lane = column pair, rows in a loop), accumulating 16 FP32
+// partial sums per column; these are reduced across the warp and merged per tile into 13
+// FP64 totals per record in shared memory:
 //   TA = sum R a' d,  TB = sum R b' d,  TG = sum sign(g) Re(P0) f,  TI = sum I f,  SI = sum I,
 // with P0 = conj(G) f_z^-1 2^-(a'^2+b'^2) e^{j phi},  R = |g| Re(P0),  I = |g| Im(P0),
 // g = r3.f, d = f - f_r.  A record's totals are only touched by the warp holding it in the
@@ -22,6 +25,7 @@
 namespace gws {
 
 constexpr int BTW = 64, BTH = 32, BPX = BTW * BTH;
+constexpr int BQ = BPX / 2;  // float4 column pairs per tile and array
 constexpr int BB = 128;   // records per work item
 constexpr int BNT = 256;  // threads per CTA
 constexpr int NTOT = 13;
@@ -35,8 +39,8 @@ struct TileConst {  // geometry of the current tile, computed once by thread 0
 };
 
 struct BwdShared {
-    float2 g[2][BPX];
-    float2 px[2][BPX];
+    float4 g[2][BQ];   // [row][lane]: (Re G(c), Re G(c + 32), Im G(c), Im G(c + 32)), c = c_lo + lane
+    float4 px[2][BQ];  // [row][lane]: (dz(c), dz(c + 32), log2 f_z(c), log2 f_z(c + 32))
     Rec rec[BB];
     float4 sv[BB][4];
     int2 rows[BB];  // per surviving record: the tile rows [x, y] its footprint's bounding box reaches
@@ -48,10 +52,8 @@ struct BwdShared {
     int item;
 };
 
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(smem)), "l"(gmem),
-                 "r"(valid ? 8 : 0)
-                 : "memory");
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
@@ -108,17 +110,19 @@ __device__ __forceinline__ float warp_transpose_reduce16(float v[16], int lane) 
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-// per-pixel table of the backward tiles: (f_z - f0_z, log2(1 / f_z)); (0, -inf) where evanescent
-__global__ void k_pixtab(int n_lambda, int H, int W, double dfx, double dfy, InvLam inv_lam, float2 *__restrict__ tab) {
+// per-pixel table in the natural layout for tw x th tiles (the exact blend's accumulation):
+// (f_z - f0_z of the pixel's tile, log2(1 / f_z)); (0, -inf) where evanescent
+__global__ void k_pixtab(int n_lambda, int H, int W, double dfx, double dfy, InvLam inv_lam, int tw, int th,
+                         float2 *__restrict__ tab) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long hw = (long long)H * W;
     if (idx >= hw * n_lambda) return;
     const int l = (int)(idx / hw);
     const long long pix = idx % hw;
     const int r = (int)(pix / W), c = (int)(pix % W);
-    const int tx = c / BTW, ty = r / BTH;
-    const int c_lo = tx * BTW, r_lo = ty * BTH;
-    const int c_hi = min(c_lo + BTW, W) - 1, r_hi = min(r_lo + BTH, H) - 1;
+    const int tx = c / tw, ty = r / th;
+    const int c_lo = tx * tw, r_lo = ty * th;
+    const int c_hi = min(c_lo + tw, W) - 1, r_hi = min(r_lo + th, H) - 1;
     const double k2 = inv_lam.v[l] * inv_lam.v[l];
     int c_ref, r_ref;
     tile_ref(c_lo, c_hi, r_lo, r_hi, H, W, dfx, dfy, k2, c_ref, r_ref);
@@ -138,11 +142,64 @@ __global__ void k_pixtab(int n_lambda, int H, int W, double dfx, double dfy, Inv
     tab[idx] = v;
 }
 
+// The backward's tile-major copies, one float4 per (wavelength, tile, row, lane) holding the
+// columns c = c_lo + lane and c + 32 of the row.  Past the grid: G = 0 and log2 f_z = +inf, so
+// padded pixels add nothing.  Evanescent pixels: dz = 0, log2 f_z = +inf (2^-inf = 0).
+__global__ void k_pixtab_tiles(int n_lambda, int H, int W, double dfx, double dfy, InvLam inv_lam, int tiles_x,
+                               int tiles_y, float4 *__restrict__ tab) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long per_l = (long long)tiles_x * tiles_y * BQ;
+    if (idx >= per_l * n_lambda) return;
+    const int l = (int)(idx / per_l);
+    const long long rem = idx % per_l;
+    const int t = (int)(rem / BQ), q = (int)(rem % BQ);
+    const int tx = t % tiles_x, ty = t / tiles_x;
+    const int c_lo = tx * BTW, r_lo = ty * BTH;
+    const int r = r_lo + q / 32, c0 = c_lo + q % 32;
+    const int c_hi = min(c_lo + BTW, W) - 1, r_hi = min(r_lo + BTH, H) - 1;
+    const double k2 = inv_lam.v[l] * inv_lam.v[l];
+    int c_ref, r_ref;
+    tile_ref(c_lo, c_hi, r_lo, r_hi, H, W, dfx, dfy, k2, c_ref, r_ref);
+    const double f0x = (double)(c_ref - W / 2) * dfx, f0y = (double)(r_ref - H / 2) * dfy;
+    const double f0z = sqrt(fmax(k2 - (f0x * f0x + f0y * f0y), 0.0));
+    float dz[2] = {0.f, 0.f}, lf[2] = {INFINITY, INFINITY};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int c = c0 + 32 * h;
+        if (r >= H || c >= W) continue;
+        const double fx = (double)(c - W / 2) * dfx, fy = (double)(r - H / 2) * dfy;
+        const double rho2 = fx * fx + fy * fy;
+        if (rho2 < k2) {
+            const double fz = sqrt(k2 - rho2);
+            dz[h] = (float)(fz - f0z);
+            lf[h] = (float)log2(fz);
+        }
+    }
+    tab[idx] = make_float4(dz[0], dz[1], lf[0], lf[1]);
+}
+
+__global__ void k_gtiles(const float2 *__restrict__ G, int n_lambda, int H, int W, int tiles_x, int tiles_y,
+                         float4 *__restrict__ out) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long per_l = (long long)tiles_x * tiles_y * BQ;
+    if (idx >= per_l * n_lambda) return;
+    const int l = (int)(idx / per_l);
+    const long long rem = idx % per_l;
+    const int t = (int)(rem / BQ), q = (int)(rem % BQ);
+    const int r = (t / tiles_x) * BTH + q / 32, c0 = (t % tiles_x) * BTW + q % 32;
+    float2 v[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int c = c0 + 32 * h;
+        if (r < H && c < W) v[h] = G[((size_t)l * H + r) * W + c];
+    }
+    out[idx] = make_float4(v[0].x, v[1].x, v[0].y, v[1].y);
+}
+
 __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ BwdArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BwdShared &S = *reinterpret_cast<BwdShared *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int L = A.segs.n_lambda;
     const long long n = A.segs.off[1];  // single scene
 
     for (;;) {
@@ -150,7 +207,9 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
         __syncthreads();
         const int it = S.item;
         if (it >= A.n_items) break;
-        const int l = it % L, blk = it / L;
+        // wavelength-major: the CTAs in flight share one wavelength's tables in L2
+        const int nblk = (int)((n + BB - 1) / BB);
+        const int l = it / nblk, blk = it % nblk;
         const long long seg_base = (long long)l * n;
         const long long k0 = (long long)blk * BB;
         const int nrec = (int)min((long long)BB, n - k0);
@@ -189,20 +248,17 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
         __syncthreads();
         const int ntx = S.tx1 - S.tx0 + 1, nty = S.ty1 - S.ty0 + 1;
         const int n_t = (ntx > 0 && nty > 0) ? ntx * nty : 0;
-        const float2 *gsl = A.gspec + (size_t)l * A.H * A.W;
-        const float2 *tsl = A.pixtab + (size_t)l * A.H * A.W;
+        const size_t ntiles = (size_t)A.tiles_x * A.tiles_y;
+        const float4 *gsl = A.gtiles + (size_t)l * ntiles * BQ;
+        const float4 *tsl = A.pixtab + (size_t)l * ntiles * BQ;
 
         auto issue = [&](int t, int buf) {
-            const int tx = S.tx0 + t % ntx, ty = S.ty0 + t / ntx;
-            const int c_lo = tx * BTW, r_lo = ty * BTH;
+            const size_t tile = (size_t)(S.ty0 + t / ntx) * A.tiles_x + (S.tx0 + t % ntx);
 #pragma unroll
-            for (int i = 0; i < BPX / BNT; ++i) {
+            for (int i = 0; i < BQ / BNT; ++i) {
                 const int e = tid + BNT * i;
-                const int r = r_lo + (e >> 6), c = c_lo + (e & 63);
-                const bool ok = r < A.H && c < A.W;
-                const size_t off = ok ? (size_t)r * A.W + c : 0;
-                cp_async8(&S.g[buf][e], gsl + off, ok);
-                cp_async8(&S.px[buf][e], tsl + off, ok);
+                cp_async16(&S.g[buf][e], gsl + tile * BQ + e);
+                cp_async16(&S.px[buf][e], tsl + tile * BQ + e);
             }
         };
         if (n_t > 0) issue(0, 0);
@@ -264,7 +320,7 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
             }
             __syncthreads();
             const float dfxf = (float)A.dfx, dfyf = (float)A.dfy;
-            const float dx0 = (float)(c_lo + lane - c_ref) * dfxf;
+            const float dx0 = (float)(c_lo + lane - c_ref) * dfxf;  // the lane's columns c and c + 32
             const float dx1 = (float)(c_lo + lane + 32 - c_ref) * dfxf;
             const float dyb = (float)(r_lo - r_ref) * dfyf;
             int q = 0;
@@ -275,60 +331,57 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                 m &= m - 1u;
                 if ((q++ & (BNT / 32 - 1)) != warp) continue;
                 const int2 rr = S.rows[k];
-                const int row_lo = rr.x & 0xffff, row_hi = rr.y;
+                const int row_lo = rr.x, row_hi = rr.y;
                 const float4 Ar = S.sv[k][0], Br = S.sv[k][1], Gr = S.sv[k][2], Mr = S.sv[k][3];
-                const float ac[2] = {fmaf(Ar.x, dx0, Ar.w), fmaf(Ar.x, dx1, Ar.w)};
-                const float bc[2] = {fmaf(Br.x, dx0, Br.w), fmaf(Br.x, dx1, Br.w)};
-                const float gc[2] = {fmaf(Gr.x, dx0, Gr.w), fmaf(Gr.x, dx1, Gr.w)};
-                const float tc[2] = {fmaf(Mr.x, dx0, Mr.w), fmaf(Mr.x, dx1, Mr.w)};
-                float sp[4][2], sz[4], sy[4];
+                const float2 ac = make_float2(fmaf(Ar.x, dx0, Ar.w), fmaf(Ar.x, dx1, Ar.w));
+                const float2 bc = make_float2(fmaf(Br.x, dx0, Br.w), fmaf(Br.x, dx1, Br.w));
+                const float2 gc = make_float2(fmaf(Gr.x, dx0, Gr.w), fmaf(Gr.x, dx1, Gr.w));
+                const float2 tc = make_float2(fmaf(Mr.x, dx0, Mr.w), fmaf(Mr.x, dx1, Mr.w));
+                const float2 ay = pair(Ar.y), az = pair(Ar.z), by = pair(Br.y), bz = pair(Br.z);
+                const float2 gy = pair(Gr.y), gz = pair(Gr.z), ty = pair(Mr.y), tz = pair(Mr.z);
+                float2 sp[4], sz[4], sy[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) sp[u][0] = sp[u][1] = sz[u] = sy[u] = 0.f;
-                // one row = two pixels per lane (columns lane and lane + 32): a static two-pixel
-                // body, unrolled over rows for four independent pixels in flight
+                for (int u = 0; u < 4; ++u) sp[u] = sz[u] = sy[u] = pair(0.f);
+                // one row = the lane's two columns as one f32x2 pair; two rows in flight
 #pragma unroll 2
                 for (int row = row_lo; row <= row_hi; ++row) {
-                    const float dy = fmaf((float)row, dfyf, dyb);
+                    const float2 dy = pair(fmaf((float)row, dfyf, dyb));
+                    const float4 G4 = S.g[buf][32 * row + lane];
+                    const float4 P4 = S.px[buf][32 * row + lane];
+                    const float2 gr = make_float2(G4.x, G4.y), gi = make_float2(G4.z, G4.w);
+                    const float2 dz = make_float2(P4.x, P4.y), lf = make_float2(P4.z, P4.w);
+                    const float2 a = __ffma2_rn(az, dz, __ffma2_rn(ay, dy, ac));
+                    const float2 b = __ffma2_rn(bz, dz, __ffma2_rn(by, dy, bc));
+                    const float2 g = __ffma2_rn(gz, dz, __ffma2_rn(gy, dy, gc));
+                    const float2 tt = __ffma2_rn(tz, dz, __ffma2_rn(ty, dy, tc));
+                    const float2 uq = __ffma2_rn(a, a, __ffma2_rn(b, b, lf));  // a'^2 + b'^2 + log2 f_z
+                    // round-to-nearest turn count: t / 2pi + 1.5 2^23, minus 1.5 2^23
+                    const float2 kr = __fadd2_rn(__ffma2_rn(tt, pair(0.15915494309189535f), pair(12582912.0f)),
+                                                 pair(-12582912.0f));
+                    const float2 ang = __ffma2_rn(kr, pair(-6.28318530717958647692f), tt);
+                    const float2 es = make_float2(with_sign_of(ex2_approx(-uq.x), g.x), with_sign_of(ex2_approx(-uq.y), g.y));
+                    const float2 kc = __fmul2_rn(es, make_float2(cos_approx(ang.x), cos_approx(ang.y)));
+                    const float2 ks = __fmul2_rn(es, make_float2(sin_approx(ang.x), sin_approx(ang.y)));
+                    // sign(g) P0 = sign(g) conj(G) f_z^-1 2^-(a'^2+b'^2) e^{j phi}
+                    const float2 Rg = __ffma2_rn(gr, kc, __fmul2_rn(gi, ks));
+                    const float2 gk = __fmul2_rn(gi, kc);
+                    const float2 Pi = __ffma2_rn(gr, ks, make_float2(-gk.x, -gk.y));
+                    const float2 R = __fmul2_rn(g, Rg), I = __fmul2_rn(g, Pi);  // |g| Re P0, |g| Im P0
+                    const float2 X[4] = {__fmul2_rn(R, a), __fmul2_rn(R, b), Rg, I};
 #pragma unroll
-                    for (int par = 0; par < 2; ++par) {
-                        const int j = 2 * row + par;
-                        const float2 gg = S.g[buf][32 * j + lane];
-                        const float2 pt = S.px[buf][32 * j + lane];
-                        const float a = fmaf(Ar.z, pt.x, fmaf(Ar.y, dy, ac[par]));
-                        const float b = fmaf(Br.z, pt.x, fmaf(Br.y, dy, bc[par]));
-                        const float g = fmaf(Gr.z, pt.x, fmaf(Gr.y, dy, gc[par]));
-                        const float tt = fmaf(Mr.z, pt.x, fmaf(Mr.y, dy, tc[par]));
-                        const float e = ex2_approx(-fmaf(a, a, fmaf(b, b, -pt.y)));
-                        const float kr = __fadd_rn(fmaf(tt, 0.15915494309189535f, 12582912.0f), -12582912.0f);
-                        const float ang = fmaf(kr, -6.28318530717958647692f, tt);
-                        const float kc = e * cos_approx(ang), ks = e * sin_approx(ang);
-                        const float p0r = fmaf(gg.x, kc, gg.y * ks);
-                        const float p0i = fmaf(gg.x, ks, -gg.y * kc);
-                        const float ag = fabsf(g);
-                        const float R = ag * p0r, I = ag * p0i;
-                        const float Rg = __int_as_float(__float_as_int(p0r) ^ (__float_as_int(g) & 0x80000000));  // sign(g) p0r
-                        const float Ra = R * a, Rb = R * b;
-                        sp[0][par] += Ra;
-                        sp[1][par] += Rb;
-                        sp[2][par] += Rg;
-                        sp[3][par] += I;
-                        sz[0] = fmaf(Ra, pt.x, sz[0]);
-                        sz[1] = fmaf(Rb, pt.x, sz[1]);
-                        sz[2] = fmaf(Rg, pt.x, sz[2]);
-                        sz[3] = fmaf(I, pt.x, sz[3]);
-                        sy[0] = fmaf(Ra, dy, sy[0]);
-                        sy[1] = fmaf(Rb, dy, sy[1]);
-                        sy[2] = fmaf(Rg, dy, sy[2]);
-                        sy[3] = fmaf(I, dy, sy[3]);
+                    for (int u = 0; u < 4; ++u) {
+                        sp[u] = __fadd2_rn(sp[u], X[u]);
+                        sy[u] = __ffma2_rn(X[u], dy, sy[u]);
+                        sz[u] = __ffma2_rn(X[u], dz, sz[u]);
                     }
                 }
                 float v[16];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    v[4 * u + 0] = sp[u][0] + sp[u][1];
-                    v[4 * u + 1] = fmaf(dx0, sp[u][0], dx1 * sp[u][1]);
-                    v[4 * u + 2] = sy[u];
-                    v[4 * u + 3] = sz[u];
+                    v[4 * u + 0] = sp[u].x + sp[u].y;
+                    v[4 * u + 1] = fmaf(dx0, sp[u].x, dx1 * sp[u].y);
+                    v[4 * u + 2] = sy[u].x + sy[u].y;
+                    v[4 * u + 3] = sz[u].x + sz[u].y;
                 }
                 const float tot = warp_transpose_reduce16(v, lane);
                 if ((lane & 1) == 0) S.red[warp][lane >> 1] = tot;
@@ -421,16 +474,29 @@ __global__ void k_grad_assemble(const GPre *__restrict__ gp, const float *__rest
     if (G.dT) G.dT[g] = dT;
 }
 
-cudaError_t launch_pixtab(int n_lambda, int H, int W, double dfx, double dfy, const InvLam &il, float2 *tab,
-                          cudaStream_t s) {
+cudaError_t launch_pixtab(int n_lambda, int H, int W, double dfx, double dfy, const InvLam &il, int tw, int th,
+                          float2 *tab, cudaStream_t s) {
     const long long n = (long long)n_lambda * H * W;
-    k_pixtab<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n_lambda, H, W, dfx, dfy, il, tab);
+    k_pixtab<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n_lambda, H, W, dfx, dfy, il, tw, th, tab);
     count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_tables(int n_lambda, int H, int W, double dfx, double dfy, const InvLam &il, const float2 *G,
+                              float4 *gtiles, float4 *pixtab, cudaStream_t s) {
+    const int tx = bwd_tiles_x(W), ty = bwd_tiles_y(H);
+    const long long n = (long long)n_lambda * tx * ty * BQ;
+    k_pixtab_tiles<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n_lambda, H, W, dfx, dfy, il, tx, ty, pixtab);
+    k_gtiles<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(G, n_lambda, H, W, tx, ty, gtiles);
+    count_launches(2);
     return cudaGetLastError();
 }
 
 int bwd_tiles_x(int W) { return (W + BTW - 1) / BTW; }
 int bwd_tiles_y(int H) { return (H + BTH - 1) / BTH; }
+size_t bwd_table_bytes(int n_lambda, int H, int W) {
+    return sizeof(float4) * (size_t)n_lambda * bwd_tiles_x(W) * bwd_tiles_y(H) * BQ;
+}
 
 cudaError_t prepare_bwd_kernels() {
     static bool done[64] = {false};

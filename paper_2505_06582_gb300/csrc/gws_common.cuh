@@ -125,6 +125,12 @@ __device__ __forceinline__ void quat_cols(const T q[4], T r1[3], T r2[3], T r3[3
     r3[2] = T(1) - T(2) * (x * x + y * y);
 }
 
+// packed f32x2 helpers: both lanes of a pair equal; sign(g) e for e >= 0 (g's sign bit on e)
+__device__ __forceinline__ float2 pair(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float with_sign_of(float e, float g) {
+    return __int_as_float(__float_as_int(e) ^ (__float_as_int(g) & 0x80000000));
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

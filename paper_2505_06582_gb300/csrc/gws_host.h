@@ -83,8 +83,8 @@ cudaError_t launch_splat_fp64(const Splat64Args &a, cudaStream_t s);
 
 struct BwdArgs {
     const Rec *rec;         // backward records (r3 unit, W separate), segment-major (single scene)
-    const float2 *gspec;    // dL/du_SLM [lambda][H][W], natural layout
-    const float2 *pixtab;   // [lambda][H][W]: (f_z - f0_z of the pixel's tile, log2(1/f_z))
+    const float4 *gtiles;   // dL/du_SLM, tile-major column pairs (k_gtiles)
+    const float4 *pixtab;   // (f_z - f0_z of the pixel's tile, log2 f_z), tile-major column pairs
     double *acc;            // [n_records][13] totals
     int *queue;
     int *status;
@@ -108,8 +108,8 @@ struct InvLam {
     double v[GWS_MAX_LAMBDA];
 };
 
-cudaError_t launch_pixtab(int n_lambda, int H, int W, double dfx, double dfy, const InvLam &il, float2 *tab,
-                          cudaStream_t s);
+cudaError_t launch_pixtab(int n_lambda, int H, int W, double dfx, double dfy, const InvLam &il, int tw, int th,
+                          float2 *tab, cudaStream_t s);
 cudaError_t launch_splat_bwd(const BwdArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_grad_assemble(const GPre *gp, const float *ampc, const double *T_g, const int *invrec,
                                  const double *acc, const float *quat_in, long long n, int L, const GradArgs &G,
@@ -117,5 +117,8 @@ cudaError_t launch_grad_assemble(const GPre *gp, const float *ampc, const double
 int bwd_block_size();
 int bwd_tiles_x(int W);
 int bwd_tiles_y(int H);
+size_t bwd_table_bytes(int n_lambda, int H, int W);  // one tile-major table (G or the per-pixel table)
+cudaError_t launch_bwd_tables(int n_lambda, int H, int W, double dfx, double dfy, const InvLam &il, const float2 *G,
+                              float4 *gtiles, float4 *pixtab, cudaStream_t s);
 
 }  // namespace gws

@@ -106,17 +106,28 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
         const float dfxf = (float)A.dfx, dfyf = (float)A.dfy;
         const float dy = (float)((double)(prow - r_ref) * A.dfy);
         const double fyd = (double)(prow - A.H / 2) * A.dfy;
-        float dx[PX], dz[PX], lfz[PX];
+        // pixels p = 2 h + {0, 1} form the f32x2 pair h of the packed arithmetic
+        constexpr int PH = PX / 2;
+        float2 dx[PH], dz[PH], lfz[PH];
 #pragma unroll
         for (int p = 0; p < PX; ++p) {
             const int col = pcol0 + p;
-            dx[p] = (float)(col - c_ref) * dfxf;
             const double fxd = (double)(col - A.W / 2) * A.dfx;
             const double rho2 = fxd * fxd + fyd * fyd;
             const bool ok = prow < A.H && col < A.W && rho2 < k2;
             const double fz = ok ? sqrt(k2 - rho2) : 1.0;
-            lfz[p] = ok ? (float)(-log2(fz)) : -INFINITY;  // log2(1 / f_z), folded into the exponent
-            dz[p] = ok ? (float)(fz - f0z) : 0.f;
+            const float vx = (float)(col - c_ref) * dfxf;
+            const float vl = ok ? (float)log2(fz) : INFINITY;  // log2 f_z: 2^-(a^2 + b^2 + log2 f_z) = f_z^-1 2^-(a^2 + b^2)
+            const float vz = ok ? (float)(fz - f0z) : 0.f;
+            if (p & 1) {
+                dx[p / 2].y = vx;
+                lfz[p / 2].y = vl;
+                dz[p / 2].y = vz;
+            } else {
+                dx[p / 2].x = vx;
+                lfz[p / 2].x = vl;
+                dz[p / 2].x = vz;
+            }
         }
         // tile rectangle (pixel-centre frequencies of the valid pixels) for the cull
         const float x0 = (float)((double)(c_lo - A.W / 2) * A.dfx), x1 = (float)((double)(c_hi - A.W / 2) * A.dfx);
@@ -135,9 +146,12 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
             }
         }
 
-        float acc_re[PX], acc_im[PX], sum_re[PX], sum_im[PX], cmp_re[PX], cmp_im[PX];
+        float2 acc_re[PH], acc_im[PH];
+        float sum_re[PX], sum_im[PX], cmp_re[PX], cmp_im[PX];
 #pragma unroll
-        for (int p = 0; p < PX; ++p) acc_re[p] = acc_im[p] = sum_re[p] = sum_im[p] = cmp_re[p] = cmp_im[p] = 0.f;
+        for (int h = 0; h < PH; ++h) acc_re[h] = acc_im[h] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int p = 0; p < PX; ++p) sum_re[p] = sum_im[p] = cmp_re[p] = cmp_im[p] = 0.f;
 
         bool timed_out = false;
         if (A.debug & GWS_DEBUG_FORCE_TIMEOUT) {
@@ -217,29 +231,36 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
                 for (int i = 0; i < cnt; ++i) {
                     const int k = lst[i];
                     const float4 Ar = s_sv[k * 4 + 0], Br = s_sv[k * 4 + 1], Gr = s_sv[k * 4 + 2], Mr = s_sv[k * 4 + 3];
-                    const float ar = fmaf(Ar.y, dy, Ar.w), br = fmaf(Br.y, dy, Br.w);
-                    const float gr = fmaf(Gr.y, dy, Gr.w), tr = fmaf(Mr.y, dy, Mr.w);
+                    const float2 ar = pair(fmaf(Ar.y, dy, Ar.w)), br = pair(fmaf(Br.y, dy, Br.w));
+                    const float2 gr = pair(fmaf(Gr.y, dy, Gr.w)), tr = pair(fmaf(Mr.y, dy, Mr.w));
+                    const float2 ax = pair(Ar.x), az = pair(Ar.z), bx = pair(Br.x), bz = pair(Br.z);
+                    const float2 gx = pair(Gr.x), gz = pair(Gr.z), tx2 = pair(Mr.x), tz = pair(Mr.z);
 #pragma unroll
-                    for (int p = 0; p < PX; ++p) {
-                        const float a = fmaf(Ar.z, dz[p], fmaf(Ar.x, dx[p], ar));
-                        const float b = fmaf(Br.z, dz[p], fmaf(Br.x, dx[p], br));
-                        const float g = fmaf(Gr.z, dz[p], fmaf(Gr.x, dx[p], gr));
-                        const float t = fmaf(Mr.z, dz[p], fmaf(Mr.x, dx[p], tr));
-                        // |g| / f_z 2^-(a^2 + b^2) = |g| 2^-(a^2 + b^2 - log2(1/f_z))
-                        const float amp = fabsf(g) * ex2_approx(-fmaf(a, a, fmaf(b, b, -lfz[p])));
+                    for (int h = 0; h < PH; ++h) {
+                        const float2 a = __ffma2_rn(az, dz[h], __ffma2_rn(ax, dx[h], ar));
+                        const float2 b = __ffma2_rn(bz, dz[h], __ffma2_rn(bx, dx[h], br));
+                        const float2 g = __ffma2_rn(gz, dz[h], __ffma2_rn(gx, dx[h], gr));
+                        const float2 t = __ffma2_rn(tz, dz[h], __ffma2_rn(tx2, dx[h], tr));
+                        // |g| / f_z 2^-(a^2 + b^2) = g (sign(g) 2^-(a^2 + b^2 + log2 f_z))
+                        const float2 u = __ffma2_rn(a, a, __ffma2_rn(b, b, lfz[h]));
+                        const float2 amp = __fmul2_rn(g, make_float2(with_sign_of(ex2_approx(-u.x), g.x),
+                                                                     with_sign_of(ex2_approx(-u.y), g.y)));
                         // t (radians) minus 2 pi round(t / 2 pi), rounding on the FP32 pipe (+-1.5 * 2^23)
-                        const float kr = __fadd_rn(fmaf(t, 0.15915494309189535f, 12582912.0f), -12582912.0f);
-                        const float ang = fmaf(kr, -6.28318530717958647692f, t);
-                        acc_re[p] = fmaf(amp, cos_approx(ang), acc_re[p]);
-                        acc_im[p] = fmaf(amp, sin_approx(ang), acc_im[p]);
+                        const float2 kr = __fadd2_rn(__ffma2_rn(t, pair(0.15915494309189535f), pair(12582912.0f)),
+                                                     pair(-12582912.0f));
+                        const float2 ang = __ffma2_rn(kr, pair(-6.28318530717958647692f), t);
+                        acc_re[h] = __ffma2_rn(amp, make_float2(cos_approx(ang.x), cos_approx(ang.y)), acc_re[h]);
+                        acc_im[h] = __ffma2_rn(amp, make_float2(sin_approx(ang.x), sin_approx(ang.y)), acc_im[h]);
                     }
                 }
             }
 #pragma unroll
-            for (int p = 0; p < PX; ++p) {
-                two_sum_acc(sum_re[p], cmp_re[p], acc_re[p]);
-                two_sum_acc(sum_im[p], cmp_im[p], acc_im[p]);
-                acc_re[p] = acc_im[p] = 0.f;
+            for (int h = 0; h < PH; ++h) {
+                two_sum_acc(sum_re[2 * h], cmp_re[2 * h], acc_re[h].x);
+                two_sum_acc(sum_re[2 * h + 1], cmp_re[2 * h + 1], acc_re[h].y);
+                two_sum_acc(sum_im[2 * h], cmp_im[2 * h], acc_im[h].x);
+                two_sum_acc(sum_im[2 * h + 1], cmp_im[2 * h + 1], acc_im[h].y);
+                acc_re[h] = acc_im[h] = make_float2(0.f, 0.f);
             }
             __syncthreads();
         }

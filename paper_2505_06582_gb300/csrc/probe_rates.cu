@@ -1,4 +1,5 @@
-// probe_rates.cu -- unit-rate microbenchmarks for the roofline denominators: FP32 FMA, MUFU ex2 / sin, FP64 DFMA
+// probe_rates.cu -- unit-rate microbenchmarks for the roofline denominators: FP32 FMA (scalar and packed
+// f32x2, with and without a negated addend), MUFU ex2 / sin, FP64 DFMA
 // (CUDA events; every access in bounds, no waits).  Build: nvcc -O3 -gencode arch=compute_103a,code=sm_103a probe_rates.cu
 #include <cstdio>
 #include <cuda_runtime.h>
@@ -9,6 +10,26 @@ __global__ void k_fma(float* out, float a, float b){
   for(int i=0;i<ITERS;i++){ x0=fmaf(x0,a,b); x1=fmaf(x1,a,b); x2=fmaf(x2,a,b); x3=fmaf(x3,a,b);
     x4=fmaf(x4,a,b); x5=fmaf(x5,a,b); x6=fmaf(x6,a,b); x7=fmaf(x7,a,b);}
   out[blockIdx.x*blockDim.x+threadIdx.x]=x0+x1+x2+x3+x4+x5+x6+x7;
+}
+// x = -x * a + b: the negated addend shows whether the sign folds into the instruction
+__global__ void k_fma_neg(float* out, float a, float b){
+  float x0=threadIdx.x, x1=x0+1, x2=x0+2, x3=x0+3, x4=x0+4, x5=x0+5, x6=x0+6, x7=x0+7;
+  for(int i=0;i<ITERS;i++){ x0=fmaf(a,b,-x0); x1=fmaf(a,b,-x1); x2=fmaf(a,b,-x2); x3=fmaf(a,b,-x3);
+    x4=fmaf(a,b,-x4); x5=fmaf(a,b,-x5); x6=fmaf(a,b,-x6); x7=fmaf(a,b,-x7);}
+  out[blockIdx.x*blockDim.x+threadIdx.x]=x0+x1+x2+x3+x4+x5+x6+x7;
+}
+template <bool NEG>
+__global__ void k_ffma2(float* out, float a, float b){
+  const float2 a2=make_float2(a,a), b2=make_float2(b,b);
+  float2 x[8];
+  for(int j=0;j<8;j++) x[j]=make_float2(threadIdx.x+j, threadIdx.x+j+0.5f);
+  for(int i=0;i<ITERS;i++){
+#pragma unroll
+    for(int j=0;j<8;j++) x[j] = NEG ? __ffma2_rn(a2, b2, make_float2(-x[j].x, -x[j].y)) : __ffma2_rn(x[j], a2, b2);
+  }
+  float s=0.f;
+  for(int j=0;j<8;j++) s+=x[j].x+x[j].y;
+  out[blockIdx.x*blockDim.x+threadIdx.x]=s;
 }
 __device__ __forceinline__ float ex2(float x){float y; asm volatile("ex2.approx.ftz.f32 %0, %1;":"=f"(y):"f"(x)); return y;}
 __device__ __forceinline__ float sn(float x){float y; asm volatile("sin.approx.ftz.f32 %0, %1;":"=f"(y):"f"(x)); return y;}
@@ -42,6 +63,12 @@ int main(){
   for(int rep=0;rep<3;rep++){
     k_fma<<<blocks,threads>>>(o,0.999f,0.001f); CK(cudaEventRecord(e0)); k_fma<<<blocks,threads>>>(o,0.999f,0.001f); CK(cudaEventRecord(e1)); CK(cudaEventSynchronize(e1)); cudaEventElapsedTime(&ms,e0,e1);
     double fma_rate = (double)n*ITERS*8/(ms*1e-3); printf("fp32 fma/s %.4g  per SM per clk(at %d kHz) %.2f\n", fma_rate, clk, fma_rate/p.multiProcessorCount/(clk*1e3));
+    k_fma_neg<<<blocks,threads>>>(o,0.999f,0.001f); CK(cudaEventRecord(e0)); k_fma_neg<<<blocks,threads>>>(o,0.999f,0.001f); CK(cudaEventRecord(e1)); CK(cudaEventSynchronize(e1)); cudaEventElapsedTime(&ms,e0,e1);
+    fma_rate = (double)n*ITERS*8/(ms*1e-3); printf("fp32 fma (negated addend) /s %.4g per SM per clk %.2f\n", fma_rate, fma_rate/p.multiProcessorCount/(clk*1e3));
+    k_ffma2<false><<<blocks,threads>>>(o,0.999f,0.001f); CK(cudaEventRecord(e0)); k_ffma2<false><<<blocks,threads>>>(o,0.999f,0.001f); CK(cudaEventRecord(e1)); CK(cudaEventSynchronize(e1)); cudaEventElapsedTime(&ms,e0,e1);
+    fma_rate = (double)n*ITERS*8/(ms*1e-3); printf("fp32x2 ffma2 instr/s %.4g per SM per clk %.2f (lane-FMAs x2)\n", fma_rate, fma_rate/p.multiProcessorCount/(clk*1e3));
+    k_ffma2<true><<<blocks,threads>>>(o,0.999f,0.001f); CK(cudaEventRecord(e0)); k_ffma2<true><<<blocks,threads>>>(o,0.999f,0.001f); CK(cudaEventRecord(e1)); CK(cudaEventSynchronize(e1)); cudaEventElapsedTime(&ms,e0,e1);
+    fma_rate = (double)n*ITERS*8/(ms*1e-3); printf("fp32x2 ffma2 (negated addend) instr/s %.4g per SM per clk %.2f\n", fma_rate, fma_rate/p.multiProcessorCount/(clk*1e3));
     k_ex2<<<blocks,threads>>>(o,0.5f); CK(cudaEventRecord(e0)); k_ex2<<<blocks,threads>>>(o,0.5f); CK(cudaEventRecord(e1)); CK(cudaEventSynchronize(e1)); cudaEventElapsedTime(&ms,e0,e1);
     double ex2_rate=(double)n*ITERS*8/(ms*1e-3); printf("ex2+fmul pairs/s %.4g per SM per clk %.2f\n", ex2_rate, ex2_rate/p.multiProcessorCount/(clk*1e3));
     k_ex2only<<<blocks,threads>>>(o); CK(cudaEventRecord(e0)); k_ex2only<<<blocks,threads>>>(o); CK(cudaEventRecord(e1)); CK(cudaEventSynchronize(e1)); cudaEventElapsedTime(&ms,e0,e1);
