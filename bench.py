@@ -63,6 +63,9 @@ def parse():
                         " forward + encode only)")
     p.add_argument("--traffic-mb", type=float, default=None,
                    help="DRAM bytes per splat launch from an ncu capture of this workload (MB)")
+    p.add_argument("--front-end", action="store_true",
+                   help="start each step from world-space Gaussians (a 2DGS-OIT style scene with degree-3 SH "
+                        "opacity) and run the holographics front end first")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
@@ -205,8 +208,29 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     scene, slm = config_scene(args.workload, n=args.n)
-    g = gws.Gaussians.from_scene(scene, dev)
     S = gws.Slm.of(slm)
+    front = None
+    if args.front_end:
+        # world-space input: the same count, grid and wavelengths; the front end makes the splat's input
+        from paper_2505_06582_gb300.scenes import CONFIGS, world_scene
+        ws_scene = world_scene(CONFIGS[args.workload]["seed"], scene.n, slm,
+                               n_surfaces=CONFIGS[args.workload].get("n_surfaces", 8), volume_frac=0.2)
+
+        def tdev(a, dt):
+            return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+        front = dict(world=gws.WorldGaussians(tdev(ws_scene.mean, torch.float64), tdev(ws_scene.quat, torch.float32),
+                                              tdev(ws_scene.scale, torch.float32), tdev(ws_scene.amp, torch.float32),
+                                              sh_opacity=tdev(ws_scene.sh, torch.float32), sh_degree=3),
+                     cam=gws.Camera(ws_scene.view, ws_scene.fx, ws_scene.fy, ws_scene.cx, ws_scene.cy,
+                                    gws.PROJ_PERSPECTIVE, 0.1),
+                     holo=ws_scene.holo, scene=ws_scene)
+        g, valid = gws.holographics(front["world"], front["cam"], front["holo"], compact=False)
+        if not bool(valid.bool().all()):
+            raise RuntimeError("front-end workload: every Gaussian must stay in view")
+        from paper_2505_06582_gb300.scenes import Scene
+        scene = Scene(*(getattr(g, k).cpu().numpy() for k in ("mean", "quat", "scale", "opacity", "amp")))
+    else:
+        g = gws.Gaussians.from_scene(scene, dev)
     fp64 = args.prec == "fp64"
     prec = gws.PREC_FP64 if fp64 else gws.PREC_MIXED
     blend = {"oit": gws.BLEND_OIT, "sorted": gws.BLEND_SORTED_T, "exact": gws.BLEND_EXACT}[args.blend]
@@ -224,11 +248,21 @@ def run_ours(args):
     phase = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.float32, device=dev)
     timers = dict(debug_flags=gws.DEBUG_TIME_KERNELS)
 
+    fe0, fe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cur = {"g": g}
+
     def step(timed_kernels):
         kw = dict(timers) if timed_kernels else {}
         kw["prec"] = prec
         kw["blend"] = blend
         launches = 0
+        t_front = None
+        if front is not None:
+            fe0.record(stream)
+            cur["g"], _ = gws.holographics(front["world"], front["cam"], front["holo"], compact=False)
+            fe1.record(stream)
+            launches += 1
+        g = cur["g"]
         gws.forward(g, S, out=field, workspace=ws, **kw)
         launches += gws.last_launch_count()
         t_splat = gws.kernel_time_ms(gws.TIMER_SPLAT_FWD) if timed_kernels else None
@@ -241,7 +275,10 @@ def run_ours(args):
             gws.backward(g, S, cot, workspace=ws, **kw)
             launches += gws.last_launch_count()
             t_bwd = gws.kernel_time_ms(gws.TIMER_SPLAT_BWD) if timed_kernels else None
-        return launches, t_splat, t_fft, t_enc, t_bwd
+        if front is not None and timed_kernels:
+            fe1.synchronize()
+            t_front = fe0.elapsed_time(fe1)
+        return launches, t_splat, t_fft, t_enc, t_bwd, t_front
 
     step(False)
     torch.cuda.synchronize()
@@ -255,12 +292,14 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    times, splat_ms, fft_ms, enc_ms, bwd_ms, launches = [], [], [], [], [], 0
+    times, splat_ms, fft_ms, enc_ms, bwd_ms, front_ms, launches = [], [], [], [], [], [], 0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
         flush.zero_()
         e0.record(stream)
-        n_l, ts, tf, te, tb = step(True)
+        n_l, ts, tf, te, tb, tfe = step(True)
+        if tfe is not None:
+            front_ms.append(tfe)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -278,12 +317,16 @@ def run_ours(args):
     value = aggregate_rate(world, ms)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
-    host = {k: getattr(g, k).cpu().pin_memory() for k in ("mean", "quat", "scale", "opacity", "amp")}
+    src = front["world"] if front is not None else g
+    in_keys = ("mean", "quat", "scale", "sh_opacity", "amp") if front is not None else \
+        ("mean", "quat", "scale", "opacity", "amp")
+    host = {k: getattr(src, k).cpu().pin_memory() for k in in_keys}
     cot_host = cot.cpu().pin_memory()
     phase_host = torch.empty(phase.shape, dtype=phase.dtype).pin_memory()
-    dbuf = {k: torch.empty_like(getattr(g, k)) for k in host}
+    dbuf = {k: torch.empty_like(getattr(src, k)) for k in host}
     cbuf = torch.empty_like(cot)
-    grads_host = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in host.items()}
+    grads_host = {k: torch.empty(getattr(g, k).shape, dtype=getattr(g, k).dtype).pin_memory()
+                  for k in ("mean", "quat", "scale", "opacity", "amp")}
     h2d = sum(v.numel() * v.element_size() for v in host.values()) + (cot_host.numel() * cot_host.element_size()
                                                                        if have_bwd else 0)
     d2h = phase_host.numel() * phase_host.element_size() + (
@@ -295,7 +338,12 @@ def run_ours(args):
         e0.record(stream)
         for k in host:
             dbuf[k].copy_(host[k], non_blocking=True)
-        gd = gws.Gaussians(dbuf["mean"], dbuf["quat"], dbuf["scale"], dbuf["opacity"], dbuf["amp"])
+        if front is not None:
+            wd = gws.WorldGaussians(dbuf["mean"], dbuf["quat"], dbuf["scale"], dbuf["amp"],
+                                    sh_opacity=dbuf["sh_opacity"], sh_degree=3)
+            gd, _ = gws.holographics(wd, front["cam"], front["holo"], compact=False)
+        else:
+            gd = gws.Gaussians(dbuf["mean"], dbuf["quat"], dbuf["scale"], dbuf["opacity"], dbuf["amp"])
         gws.forward(gd, S, out=field, workspace=ws, prec=prec, blend=blend)
         gws.encode(field, S, out=phase, workspace=ws)
         phase_host.copy_(phase, non_blocking=True)
@@ -335,7 +383,22 @@ def run_ours(args):
         rooflines["splat_bwd"] = roof("k_splat_bwd", dom_ms["splat_bwd"], BWD_PAIRS_PER_CLK,
                                       "FP32 bound (36 lane-ops per pair at 128 lanes/clk/SM; MUFU bound 6.4)",
                                       BWD_TRAFFIC_MB if full_size else None)
-    dominant = max(rooflines, key=lambda k: dom_ms[k])
+    if front_ms:
+        dom_ms["front_end"] = statistics.median(front_ms)
+        # algorithmic bytes per Gaussian: mean 24 + quat 16 + scale 12 + 16 SH floats 64 read,
+        # mean 24 + quat 16 + scale 8 + opacity 4 + flag 1 written
+        fb = 169 * g.n
+        hbm_peak_fe = 6785.9
+        try:
+            hbm_peak_fe = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        except (OSError, KeyError, ValueError):
+            pass
+        ach = fb / (dom_ms["front_end"] * 1e-3) / 1e9
+        rooflines["front_end"] = {"kernel": "k_holographics", "bound": "hbm", "achieved": ach, "peak": hbm_peak_fe,
+                                  "unit": "GB/s", "frac": ach / hbm_peak_fe, "traffic": None,
+                                  "note": "169 algorithmic bytes per Gaussian; the FP64 per-Gaussian algebra, not "
+                                          "HBM, sets its time"}
+    dominant = max((k for k in rooflines if k != "front_end"), key=lambda k: dom_ms[k])
     fwd_ms = ms - (dom_ms.get("splat_bwd", 0.0))
     # HBM-bound stages: algorithmic bytes = one read + one write of every slice per pass
     hbm_peak = 6785.9
@@ -358,10 +421,12 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "holograms/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n_gaussians": g.n, "H": S.H, "W": S.W, "n_lambda": S.n_lambda,
+            "config": {"workload": args.workload + ("+front_end(world_scene)" if front is not None else ""),
+                       "n_gaussians": g.n, "H": S.H, "W": S.W, "n_lambda": S.n_lambda,
                        "pitch_m": S.pitch_x, "blend": args.blend, "precision": args.prec,
                        "trunc_eps": None if fp64 else 1e-5,
-                       "step": "forward+encode" + ("+backward" if have_bwd else ""), "tile_cfg": tile_cfg,
+                       "step": ("front_end+" if front is not None else "") + "forward+encode"
+                               + ("+backward" if have_bwd else ""), "tile_cfg": tile_cfg,
                        "l2": "flushed before each timed step (512 MB write)", "parallelism": f"replicas x{world}"},
             "fwd_holograms_per_s": world * 1000.0 / fwd_ms if have_bwd else value,
             "pairs": {"dense_per_hologram": dense, "algorithmic_per_hologram": pairs,

@@ -261,6 +261,62 @@ GWS_API int gws_last_launch_count(void);
 GWS_API gws_status gws_autotune(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
                         void *field_scratch, int *best_cfg);
 
+/* ---- holographics front end (Supplement Sec. 1.1) and view-dependent opacity (Sec. 4.2) ----
+ *
+ * Turns Gaussians optimised in world space (e.g. by a 2DGS / 2DGS-OIT model) into the
+ * hologram-space inputs of the splat for one view:
+ *   model transform   Sigma_w = R_w S_w S_w^T R_w^T                      (3 scales; surfel: s_z = 0)
+ *   view transform    x_v = W x_w + t, the camera looking down -z
+ *   projective map    perspective phi(x, y, z) = (fx x / (-z) + cx, fy y / (-z) + cy),
+ *                     orthographic (fx x + cx, fy y + cy); J = d phi / dx at the mean (EWA)
+ *   lifting           J W Sigma_w W^T J^T = R' S'^2 R'^T -> R_v = diag(R', 1), S_v = [S'; 0],
+ *                     mu_v = (phi(W mu_w + t), (W mu_w + t)_z)
+ *   hologram map      mu = A mu_v + b, Sigma = A R_v S_v S_v^T R_v^T A^T = R diag(s_u^2, s_v^2, 0) R^T
+ * and the opacity factor SH(o, d) of alpha = G * SH(o, d): real spherical harmonics of degree
+ * <= 3 (Condon-Shortley phase, m = -l..l), d the unit direction from the camera centre
+ * -W^T t to mu_w, clamped to [0, 1].  The output scales are descending (s_u >= s_v), r3 =
+ * r1 x r2 and the quaternion has w >= 0. */
+typedef enum { GWS_PROJ_PERSPECTIVE = 0, GWS_PROJ_ORTHOGRAPHIC = 1 } gws_projection;
+
+typedef struct { /* device memory */
+    const double *mean;       /* [n][3] world-space means */
+    const float *quat;        /* [n][4] world rotation (w, x, y, z), any non-zero norm */
+    const float *scale;       /* [n][3] world scales (>= 0; a 2D surfel has scale[2] = 0) */
+    const float *sh_opacity;  /* [n][sh_stride] SH coefficients of the opacity, or NULL */
+    const float *opacity;     /* [n] view-independent opacity, used when sh_opacity is NULL */
+    int sh_degree;            /* 0 .. 3: (sh_degree + 1)^2 coefficients are read */
+    int sh_stride;            /* floats per Gaussian in sh_opacity; 0 means (sh_degree + 1)^2 */
+} gws_world_gaussians;
+
+typedef struct { /* writable Gaussians, same layout as gws_gaussians, device memory */
+    double *mean;
+    float *quat;
+    float *scale;
+    float *opacity;
+    float *amp;
+} gws_gaussians_out;
+
+typedef struct { /* host values */
+    double view[12];          /* row-major 3x4 [W | t]: x_view = W x_world + t */
+    double fx, fy, cx, cy;    /* projective mapping into ray space */
+    int projection;           /* gws_projection */
+    double z_near;            /* a Gaussian is culled when its view depth -z is below z_near */
+} gws_camera;
+
+/* Front end for one view.  in: n world-space Gaussians (device).  cam: the view (host).
+ * holo: HOST row-major 3x4 [A | b], ray space -> hologram space; A's first two columns must be
+ * linearly independent.  Writes out->mean, out->quat, out->scale and out->opacity (device,
+ * n entries each; out->amp is not touched and may be NULL) and, when valid is not NULL,
+ * valid[i] = 1 for a kept Gaussian, 0 for a culled one (view depth below z_near, or a
+ * non-finite / zero-norm input): culled entries get a zero mean, scales and opacity and the
+ * identity rotation, and are meant to be dropped before the splat.  Runs on opts.stream
+ * (other opts fields are ignored; no workspace).  Errors: GWS_ERR_INVALID_ARG for NULL
+ * pointers (n > 0), n < 0, sh_degree outside 0..3, sh_stride below the coefficient count, an
+ * unknown projection, non-finite camera / transform values or a rank-deficient A. */
+GWS_API gws_status gws_holographics(const gws_world_gaussians *in, int64_t n, const gws_camera *cam,
+                                    const double holo[12], const gws_opts *opts, gws_gaussians_out *out,
+                                    unsigned char *valid);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,6 +21,7 @@ from . import _build
 BLEND_OIT, BLEND_SORTED_T, BLEND_EXACT = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 DOMAIN_FIELD, DOMAIN_SPECTRUM = 0, 1
+PROJ_PERSPECTIVE, PROJ_ORTHOGRAPHIC = 0, 1
 DEBUG_FORCE_TIMEOUT = 1
 DEBUG_TIME_KERNELS = 2
 TIMER_SPLAT_FWD, TIMER_SPLAT_BWD, TIMER_FFT, TIMER_ENCODE, TIMER_TOTAL = 0, 1, 2, 3, 4
@@ -54,13 +55,28 @@ class _Opts(C.Structure):
                 ("exact_batch", C.c_int)]
 
 
+class _GaussiansOut(C.Structure):
+    _fields_ = [("mean", C.c_void_p), ("quat", C.c_void_p), ("scale", C.c_void_p), ("opacity", C.c_void_p),
+                ("amp", C.c_void_p)]
+
+
+class _WorldGaussians(C.Structure):
+    _fields_ = [("mean", C.c_void_p), ("quat", C.c_void_p), ("scale", C.c_void_p), ("sh_opacity", C.c_void_p),
+                ("opacity", C.c_void_p), ("sh_degree", C.c_int), ("sh_stride", C.c_int)]
+
+
+class _Camera(C.Structure):
+    _fields_ = [("view", C.c_double * 12), ("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double),
+                ("cy", C.c_double), ("projection", C.c_int), ("z_near", C.c_double)]
+
+
 _lib = None
 _lib_lock = threading.Lock()
 
 EXPORTS = ["gws_opts_default", "gws_status_string", "gws_version", "gws_workspace_size", "gws_prepare",
            "gws_forward", "gws_forward_batched", "gws_backward", "gws_encode", "gws_get_device_status",
            "gws_depth_order", "gws_transmittance", "gws_footprints", "gws_last_launch_count", "gws_autotune",
-           "gws_kernel_time_ms", "gws_footprint_pairs", "gws_encode_noalloc"]
+           "gws_kernel_time_ms", "gws_footprint_pairs", "gws_encode_noalloc", "gws_holographics"]
 
 
 def lib_path() -> str:
@@ -368,6 +384,87 @@ def autotune(g: Gaussians, slm: Slm, workspace=None, **kw) -> int:
     _check(lib.gws_autotune(C.byref(g._c()), C.c_int64(g.n), C.byref(slm._c()), C.byref(opts),
                             C.c_void_p(scratch.data_ptr()), C.byref(best)), "gws_autotune")
     return int(best.value)
+
+
+@dataclass
+class WorldGaussians:
+    """World-space Gaussians of a 2DGS / 2DGS-OIT style model (device tensors)."""
+    mean: torch.Tensor                      # float64 [n,3]
+    quat: torch.Tensor                      # float32 [n,4] (w, x, y, z)
+    scale: torch.Tensor                     # float32 [n,3] (surfels: scale[:, 2] = 0)
+    amp: torch.Tensor                       # float32 [n,L], passed through to the hologram-space set
+    sh_opacity: torch.Tensor | None = None  # float32 [n,K], K >= (sh_degree + 1)^2
+    opacity: torch.Tensor | None = None     # float32 [n], used when sh_opacity is None
+    sh_degree: int = 3
+
+    @property
+    def n(self):
+        return int(self.mean.shape[0])
+
+    def check(self):
+        n = self.n
+        need = [("mean", self.mean, torch.float64, (n, 3)), ("quat", self.quat, torch.float32, (n, 4)),
+                ("scale", self.scale, torch.float32, (n, 3))]
+        if self.sh_opacity is not None:
+            if self.sh_opacity.dim() != 2 or self.sh_opacity.shape[0] != n:
+                raise ValueError("sh_opacity: expected [n, K]")
+            need.append(("sh_opacity", self.sh_opacity, torch.float32, tuple(self.sh_opacity.shape)))
+        elif self.opacity is not None:
+            need.append(("opacity", self.opacity, torch.float32, (n,)))
+        else:
+            raise ValueError("either sh_opacity or opacity is required")
+        for name, t, dt, shape in need:
+            if t.dtype != dt or tuple(t.shape) != shape or not t.is_contiguous() or not t.is_cuda:
+                raise ValueError(f"{name}: expected contiguous CUDA {dt} {shape}, got {t.dtype} {tuple(t.shape)}")
+
+
+@dataclass
+class Camera:
+    """View [W | t] (3x4, x_view = W x_world + t, looking down -z) and projective mapping."""
+    view: np.ndarray
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    projection: int = PROJ_PERSPECTIVE
+    z_near: float = 0.0
+
+    def _c(self):
+        v = np.ascontiguousarray(np.asarray(self.view, dtype=np.float64).reshape(12))
+        return _Camera((C.c_double * 12)(*v.tolist()), float(self.fx), float(self.fy), float(self.cx), float(self.cy),
+                       int(self.projection), float(self.z_near))
+
+
+def holographics(world: WorldGaussians, camera: Camera, holo, compact: bool = True, stream=None):
+    """Holographics front end (gws_holographics): world-space Gaussians -> the splat's
+    hologram-space Gaussians for one view.  holo: 3x4 [A | b] (ray space -> hologram space).
+    Returns (Gaussians, valid): with compact=True the culled Gaussians are dropped (valid then
+    says which inputs were kept); otherwise every input keeps its slot."""
+    world.check()
+    lib = load()
+    n, dev = world.n, world.mean.device
+    mean = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    quat = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    scale = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    opacity = torch.empty((n,), dtype=torch.float32, device=dev)
+    valid = torch.empty((n,), dtype=torch.uint8, device=dev)
+    sh = world.sh_opacity
+    win = _WorldGaussians(world.mean.data_ptr(), world.quat.data_ptr(), world.scale.data_ptr(),
+                          sh.data_ptr() if sh is not None else None,
+                          world.opacity.data_ptr() if (sh is None and world.opacity is not None) else None,
+                          int(world.sh_degree), int(sh.shape[1]) if sh is not None else 0)
+    out = _GaussiansOut(mean.data_ptr(), quat.data_ptr(), scale.data_ptr(), opacity.data_ptr(), None)
+    h = np.ascontiguousarray(np.asarray(holo, dtype=np.float64).reshape(12))
+    hc = (C.c_double * 12)(*h.tolist())
+    opts = make_opts(stream=stream)
+    _check(lib.gws_holographics(C.byref(win), C.c_int64(n), C.byref(camera._c()), hc, C.byref(opts), C.byref(out),
+                                C.c_void_p(valid.data_ptr())), "gws_holographics")
+    g = Gaussians(mean, quat, scale, opacity, world.amp)
+    if compact:
+        keep = valid.bool()
+        g = Gaussians(mean[keep].contiguous(), quat[keep].contiguous(), scale[keep].contiguous(),
+                      opacity[keep].contiguous(), world.amp[keep].contiguous())
+    return g, valid
 
 
 def last_launch_count() -> int:

@@ -15,6 +15,10 @@ replaced by random surfaces because the trained scenes are not available:
 * ``surface_scene``  -- means on random spheres (SLM-facing hemispheres) and tilted
   planes, each Gaussian lying in its surface's tangent plane with a random in-plane
   angle.
+* ``world_scene``    -- the same kind of surfaces in the world space of a camera (the
+  input of the holographics front end: a 2DGS-OIT style model with degree-3 SH opacity
+  coefficients), with the view, the projective mapping and the display transform that
+  maps the image to the SLM and the view depths to the hologram volume.
 
 Units: metres.  Means are float64; everything else is float32.
 """
@@ -27,7 +31,7 @@ import numpy as np
 
 __all__ = [
     "SLM", "Scene", "uniform_scene", "surface_scene", "config_scene", "batched_sizes",
-    "cotangent", "random_field", "CONFIGS",
+    "cotangent", "random_field", "CONFIGS", "WorldScene", "world_scene",
 ]
 
 
@@ -177,6 +181,110 @@ def surface_scene(seed: int, n: int, slm: SLM, n_surfaces=8, scale_median_px=2.0
     opacity = rng.uniform(opacity_range[0], opacity_range[1], mean.shape[0]).astype(np.float32)
     amp = rng.uniform(0.0, 1.0, (mean.shape[0], slm.n_lambda)).astype(np.float32)
     return Scene(mean, q, scale, opacity, amp, {"kind": "surface", "seed": seed, "surfaces": n_surfaces})
+
+
+@dataclass
+class WorldScene:
+    """World-space Gaussians of one view (front-end input) and the view / display geometry."""
+    mean: np.ndarray      # float64 [N,3], world (m)
+    quat: np.ndarray      # float32 [N,4] (w, x, y, z), world rotation
+    scale: np.ndarray     # float32 [N,3]; surfels have scale[:, 2] = 0
+    sh: np.ndarray        # float32 [N,16], degree-3 SH coefficients of the opacity
+    amp: np.ndarray       # float32 [N, n_lambda]
+    view: np.ndarray      # float64 [3,4]: x_view = W x_world + t, camera looking down -z
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    holo: np.ndarray      # float64 [3,4]: ray space (pixels, view z) -> hologram space (m)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.mean.shape[0])
+
+
+def _random_rotation(rng) -> np.ndarray:
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def world_scene(seed: int, n: int, slm: SLM, n_surfaces=8, depth=(1.5, 3.0), fov_deg=40.0,
+                hologram_depth=(2e-3, 10e-3), scale_px=2.0, sigma_log=0.5, volume_frac=0.0,
+                sh_spread=0.1) -> WorldScene:
+    """Surfaces (camera-facing sphere caps and tilted planes) inside the view frustum at view
+    depths ``depth`` (m), posed in the world by a random camera; surfels whose projected scales
+    are about ``scale_px`` pixels.  A fraction ``volume_frac`` gets a non-zero third scale (3D
+    Gaussians).  The SH opacity has a DC term for a base opacity U[0.3, 1] and higher orders
+    N(0, sh_spread).  The display maps pixel (u, v) to (u - W/2) px, (v - H/2) py and the view
+    depths linearly onto ``hologram_depth`` (near -> near)."""
+    rng = np.random.default_rng(seed)
+    W_px, H_px = slm.W, slm.H
+    fx = fy = (W_px / 2) / math.tan(math.radians(fov_deg) / 2)
+    cx, cy = W_px / 2, H_px / 2
+    half_x, half_y = (W_px / 2) / fx, (H_px / 2) / fy  # frustum half-widths per unit depth
+    counts = np.full(n_surfaces, n // n_surfaces)
+    counts[: n - counts.sum()] += 1
+    pts, nrm = [], []
+    for k in range(n_surfaces):
+        m = int(counts[k])
+        if m == 0:
+            continue
+        d = rng.uniform(depth[0] + 0.2 * (depth[1] - depth[0]), depth[1] - 0.2 * (depth[1] - depth[0]))
+        ctr = np.array([rng.uniform(-0.5, 0.5) * half_x * d, rng.uniform(-0.5, 0.5) * half_y * d, -d])
+        if rng.uniform() < 0.5:  # sphere cap facing the camera (+z in view space)
+            rad = rng.uniform(0.05, 0.15) * d * half_y
+            v = rng.normal(size=(m, 3))
+            v /= np.linalg.norm(v, axis=1, keepdims=True)
+            v[:, 2] = np.abs(v[:, 2])
+            pts.append(ctr + rad * v)
+            nrm.append(v)
+        else:  # plane patch, normal within 45 degrees of the view axis
+            cos_t = rng.uniform(math.cos(math.radians(45.0)), 1.0)
+            sin_t = math.sqrt(1.0 - cos_t * cos_t)
+            phi = rng.uniform(0, 2 * math.pi)
+            nv = np.array([sin_t * math.cos(phi), sin_t * math.sin(phi), cos_t])
+            hx, hy = rng.uniform(0.1, 0.3) * half_x * d, rng.uniform(0.1, 0.3) * half_y * d
+            x = rng.uniform(ctr[0] - hx, ctr[0] + hx, m)
+            y = rng.uniform(ctr[1] - hy, ctr[1] + hy, m)
+            z = ctr[2] - (nv[0] * (x - ctr[0]) + nv[1] * (y - ctr[1])) / nv[2]
+            pts.append(np.stack([x, y, z], 1))
+            nrm.append(np.tile(nv, (m, 1)))
+    if n > 0:
+        xv = np.concatenate(pts)
+        normal = np.concatenate(nrm)
+    else:
+        xv, normal = np.zeros((0, 3)), np.zeros((0, 3))
+    xv[:, 2] = np.clip(xv[:, 2], -depth[1], -depth[0])
+    psi = rng.uniform(0, 2 * math.pi, xv.shape[0])
+    r1, r2, r3 = _tangent_frame(normal, psi) if n > 0 else (normal, normal, normal)
+    # camera pose: x_view = Rc x_world + t  <=>  x_world = Rc^T (x_view - t)
+    Rc = _random_rotation(rng)
+    t = rng.normal(size=3)
+    view = np.concatenate([Rc, t[:, None]], axis=1)
+    mean = (xv - t) @ Rc
+    frame = np.stack([r1, r2, r3], axis=2)  # view-space columns
+    wframe = np.einsum("ji,njk->nik", Rc, frame)  # Rc^T [r1 r2 r3]
+    q = _quat_from_frame(wframe[:, :, 0], wframe[:, :, 1], wframe[:, :, 2]).astype(np.float32) if n > 0 \
+        else np.zeros((0, 4), np.float32)
+    px_world = (-xv[:, 2]) / fx  # metres per pixel at each depth
+    s2 = np.exp(rng.normal(math.log(scale_px), sigma_log, (xv.shape[0], 2))) * px_world[:, None]
+    s3 = np.where(rng.uniform(size=xv.shape[0]) < volume_frac, 0.5 * s2.min(axis=1), 0.0)
+    scale = np.concatenate([s2, s3[:, None]], axis=1).astype(np.float32)
+    sh = rng.normal(0.0, sh_spread, (xv.shape[0], 16))
+    sh[:, 0] = rng.uniform(0.3, 1.0, xv.shape[0]) * 2.0 * math.sqrt(math.pi)  # Y_00 = 1 / (2 sqrt(pi))
+    amp = rng.uniform(0.0, 1.0, (xv.shape[0], slm.n_lambda)).astype(np.float32)
+    a = (hologram_depth[1] - hologram_depth[0]) / (depth[0] - depth[1])  # view z = -depth
+    bz = hologram_depth[0] + a * depth[0]
+    holo = np.array([[slm.pitch_x, 0.0, 0.0, -cx * slm.pitch_x],
+                     [0.0, slm.pitch_y, 0.0, -cy * slm.pitch_y],
+                     [0.0, 0.0, a, bz]])
+    return WorldScene(mean, q, scale, sh.astype(np.float32), amp, view, fx, fy, cx, cy, holo,
+                      {"kind": "world", "seed": seed, "surfaces": n_surfaces})
 
 
 RGB = (638e-9, 520e-9, 450e-9)
