@@ -79,9 +79,19 @@ typedef enum {
 typedef enum {
     GWS_BLEND_OIT = 0,      /* Eq. 12: order-invariant sum, T_i = 1 */
     GWS_BLEND_SORTED_T = 1, /* Eq. 5-6 with T_i at the Gaussian's centre (depth-sorted) */
-    GWS_BLEND_EXACT = 2     /* Eq. 5-6 with the spatial transmittance map (Algorithm S2): front to back,
+    GWS_BLEND_EXACT = 2,    /* Eq. 5-6 with the spatial transmittance map (Algorithm S2): front to back,
                                u_SLM += c o F(T u_k) H(f, -z_k), T *= 1 - alpha_k, alpha_k = o |u_k|
                                above t_eps (or binarised at t_binarize); MIXED forward only */
+    GWS_BLEND_PARTIAL_COHERENT = 3 /* Eq. 14 summed as Eq. 12: one time-multiplexed frame of partially
+                               coherent GWS.  Each Gaussian's spectrum (Eq. 10 at the origin) is
+                               convolved with the angular kernel K(f) = Y_l^m(k_hat) e^{j phi(f)}
+                               (opts.pc_l, opts.pc_m; k_hat = lambda (f_x, f_y, f_z), K = 0 where
+                               evanescent) and then translated by e^{-j 2 pi f . mu}: through the
+                               spatial domain, its field on its own plane times
+                               kappa(x) = sum_f K(f) e^{j 2 pi f . x} / sqrt(sum_f Y^2) (E|kappa|^2 = 1).
+                               phi(f) = 2 pi u - pi, u = SplitMix64 output number
+                               ((pc_frame L + l) H + r) W + c + 1 of the stream seeded with pc_seed
+                               (top 53 bits / 2^53).  MIXED forward only, single scene */
 } gws_blend;
 
 typedef enum {
@@ -149,7 +159,10 @@ typedef struct {
     void *workspace;         /* device scratch, >= gws_workspace_size() bytes */
     size_t workspace_bytes;
     float t_binarize;        /* EXACT: > 0 binarises alpha (disk occlusion, Algorithm S2); default 0 */
-    int exact_batch;         /* EXACT: Gaussians per batch of fields in flight (0 = 128) */
+    int exact_batch;         /* EXACT, PARTIAL_COHERENT: Gaussians per batch of fields in flight (0 = 128) */
+    int pc_l, pc_m;          /* PARTIAL_COHERENT: degree 0..3 and order -l..l of the kernel's SH; default 0, 0 */
+    uint64_t pc_seed;        /* PARTIAL_COHERENT: seed of the random phases; default 0 */
+    uint64_t pc_frame;       /* PARTIAL_COHERENT: frame index t (independent phases per frame); default 0 */
 } gws_opts;
 
 /* Fills *o with the defaults listed above (OIT, MIXED, FIELD). */

@@ -111,6 +111,7 @@ struct Layout {
     size_t rec64, w64, fkey0, fkey1, fval0, fval1, rec, Rr, ikey0, ikey1, ival0, ival1, icount, invrec, gspec, bacc;
     size_t pixtab, gtiles, dT, tq;
     size_t ex_U, ex_T, ex_arr, ex_inner, ex_inner_bytes;
+    size_t pc_kappa, pc_ysum;  // partial coherence: the kernel pattern [L][H][W] and sum_f Y^2 [L]
     int ex_B;
     size_t cufft, total;
     int tiles_x, tiles_y, n_tiles, cfg;
@@ -209,15 +210,22 @@ static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *sl
         L->dT = P.take(sizeof(double) * n);
     }
     L->ex_U = L->ex_T = L->ex_arr = L->ex_inner = L->ex_inner_bytes = 0;
+    L->pc_kappa = L->pc_ysum = 0;
     L->ex_B = 0;
     size_t fft_work = 0;
-    if (o->blend == GWS_BLEND_EXACT && o->prec == GWS_PREC_MIXED) {
+    const bool pc = o->blend == GWS_BLEND_PARTIAL_COHERENT;
+    if ((o->blend == GWS_BLEND_EXACT || pc) && o->prec == GWS_PREC_MIXED) {
         const int B = exact_batch(o);
         L->ex_B = B;
         const size_t hw = (size_t)slm->H * slm->W;
         L->ex_U = P.take(sizeof(float) * 2 * (size_t)B * nl * hw);
-        L->ex_T = P.take(sizeof(float) * nl * hw);
-        L->ex_arr = P.take((size_t)B * (24 + 16 + 8 + 4 + 4 * nl + 8 + 4 * nl + 4) + 256 * 8);
+        if (pc) {
+            L->pc_kappa = P.take(sizeof(float) * 2 * nl * hw);
+            L->pc_ysum = P.take(sizeof(double) * nl);
+        } else {
+            L->ex_T = P.take(sizeof(float) * nl * hw);
+        }
+        L->ex_arr = P.take((size_t)B * (24 + 16 + 8 + 4 + 4 * nl + 8 + 4 * nl + 4 + 24) + 256 * 9);
         gws_opts inner = *o;  // the batch's fields: the order-invariant forward of B one-Gaussian scenes
         inner.blend = GWS_BLEND_OIT;
         inner.domain = GWS_DOMAIN_FIELD;
@@ -268,8 +276,10 @@ static gws_status check_slm(const gws_slm *slm) {
 
 static gws_status check_opts(const gws_opts *o) {
     if (!o) return GWS_ERR_INVALID_ARG;
-    if (o->blend != GWS_BLEND_OIT && o->blend != GWS_BLEND_SORTED_T && o->blend != GWS_BLEND_EXACT)
+    if (o->blend != GWS_BLEND_OIT && o->blend != GWS_BLEND_SORTED_T && o->blend != GWS_BLEND_EXACT &&
+        o->blend != GWS_BLEND_PARTIAL_COHERENT)
         return GWS_ERR_INVALID_ARG;
+    if (o->pc_l < 0 || o->pc_l > 3 || o->pc_m < -o->pc_l || o->pc_m > o->pc_l) return GWS_ERR_INVALID_ARG;
     if (!(o->t_binarize >= 0.f && o->t_binarize < 1.f) || o->exact_batch < 0) return GWS_ERR_INVALID_ARG;
     if (o->prec != GWS_PREC_FP64 && o->prec != GWS_PREC_MIXED) return GWS_ERR_INVALID_ARG;
     if (o->domain != GWS_DOMAIN_FIELD && o->domain != GWS_DOMAIN_SPECTRUM) return GWS_ERR_INVALID_ARG;
@@ -437,6 +447,7 @@ static gws_status exact_forward(const gws_gaussians *scene, long long n, const g
     E.amp = E.opacity + B;
     E.co = E.amp + (size_t)B * nl;
     E.ok = E.co + (size_t)B * nl;
+    E.mu = nullptr;
     InvLam il;
     std::memset(&il, 0, sizeof il);
     for (int l = 0; l < nl; ++l) il.v[l] = 1.0 / slm->wavelengths[l];
@@ -466,7 +477,7 @@ static gws_status exact_forward(const gws_gaussians *scene, long long n, const g
     timer_mark(o, GWS_TIMER_SPLAT_FWD, 0, s);  // the whole front-to-back loop
     for (long long b0 = 0; b0 < n; b0 += B) {
         const int nb = (int)std::min<long long>(B, n - b0);
-        CU(launch_exact_gather(F.sorted, b0, nb, scene, nl, E, s));
+        CU(launch_exact_gather(F.sorted, b0, nb, scene, nl, E, 0, s));
         GS(forward_impl(gb.data(), ones.data(), nb, slm, &inner, outs.data()));
         CU(launch_exact_mask(U, Tm, E, nb, nl, hw, o->alpha_min, o->t_binarize, s));
         // centred forward DFT scaled by px py: the spectrum of each masked field
@@ -480,6 +491,93 @@ static gws_status exact_forward(const gws_gaussians *scene, long long n, const g
         }
         CU(launch_modulate(U, 0, nb * nl, H, W, slm->pitch_x * slm->pitch_y, 2, s));
         CU(launch_exact_accum(U, acc, pixtab, E, nb, nl, H, W, dfx, dfy, il, s));
+    }
+    timer_mark(o, GWS_TIMER_SPLAT_FWD, 1, s);
+    timer_mark(o, GWS_TIMER_FFT, 0, s);
+    if (o->domain == GWS_DOMAIN_FIELD) {
+        CU(launch_modulate(acc, 0, nl, H, W, 1.0, 3, s));
+        GS(exec_fft(p, acc, at<char>(o, L.cufft), 0, CUFFT_INVERSE, s));
+        CU(launch_modulate(acc, 0, nl, H, W, dfx * dfy, 0, s));
+    }
+    timer_mark(o, GWS_TIMER_FFT, 1, s);
+    timer_mark(o, GWS_TIMER_TOTAL, 1, s);
+    return GWS_OK;
+}
+
+// One frame of partially coherent GWS (Eq. 14 summed as Eq. 12): batches of B Gaussians; each
+// batch's fields at the origin on their own planes (the order-invariant forward of B one-Gaussian
+// scenes), times c o kappa, back to the spectrum by a centred forward DFT (scale px py), and
+// accumulated with the ramps e^{-j 2 pi f . mu}; a final centred inverse DFT gives the field.
+static gws_status pc_forward(const gws_gaussians *scene, long long n, const gws_slm *slm, const gws_opts *o,
+                             const Layout &L, const Front &F, void *out, cudaStream_t s) {
+    const int nl = slm->n_lambda, H = slm->H, W = slm->W;
+    const long long hw = (long long)H * W;
+    const double dfx = 1.0 / (W * slm->pitch_x), dfy = 1.0 / (H * slm->pitch_y);
+    const int B = L.ex_B;
+    float2 *acc = static_cast<float2 *>(out);
+    float2 *U = at<float2>(o, L.ex_U);
+    float2 *kappa = at<float2>(o, L.pc_kappa);
+    double *ysum = at<double>(o, L.pc_ysum);
+    char *arr = at<char>(o, L.ex_arr);
+    ExactBatch E;
+    E.mean = reinterpret_cast<double *>(arr);
+    E.zk = E.mean + 3 * B;
+    E.mu = E.zk + B;
+    E.quat = reinterpret_cast<float *>(E.mu + 3 * B);
+    E.scale = E.quat + 4 * B;
+    E.opacity = E.scale + 2 * B;
+    E.amp = E.opacity + B;
+    E.co = E.amp + (size_t)B * nl;
+    E.ok = E.co + (size_t)B * nl;
+    InvLam il;
+    std::memset(&il, 0, sizeof il);
+    for (int l = 0; l < nl; ++l) il.v[l] = 1.0 / slm->wavelengths[l];
+    Plan p;
+    GS(get_plan(H, W, nl, 0, &p));
+    timer_mark(o, GWS_TIMER_SPLAT_FWD, 0, s);  // the kernel pattern and the batch loop
+    // the frame's kernel pattern: kappa(x) = sum_f K(f) e^{j 2 pi f . x}, normalised in launch_pc_apply
+    CU(cudaMemsetAsync(ysum, 0, sizeof(double) * nl, s));
+    CU(launch_pc_kernel(kappa, ysum, o->pc_l, o->pc_m, (unsigned long long)o->pc_seed,
+                        (unsigned long long)o->pc_frame, nl, H, W, dfx, dfy, il, s));
+    CU(launch_modulate(kappa, 0, nl, H, W, 1.0, 3, s));
+    GS(exec_fft(p, kappa, at<char>(o, L.cufft), 0, CUFFT_INVERSE, s));
+    CU(launch_modulate(kappa, 0, nl, H, W, 1.0, 0, s));
+    float2 *pixtab = at<float2>(o, L.pixtab);
+    CU(launch_pixtab(nl, H, W, dfx, dfy, il, 64, 32, pixtab, s));  // the tiles of the accumulation
+    CU(cudaMemsetAsync(acc, 0, sizeof(float2) * (size_t)nl * hw, s));
+    gws_opts inner = *o;
+    inner.blend = GWS_BLEND_OIT;
+    inner.domain = GWS_DOMAIN_FIELD;
+    inner.phase_match = 0;  // applied with the ramps
+    inner.debug_flags &= ~(unsigned)GWS_DEBUG_TIME_KERNELS;
+    inner.workspace = at<char>(o, L.ex_inner);
+    inner.workspace_bytes = L.ex_inner_bytes;
+    std::vector<gws_gaussians> gb(B);
+    std::vector<int64_t> ones(B, 1);
+    std::vector<void *> outs(B);
+    for (int k = 0; k < B; ++k) {
+        gb[k].mean = E.mean + 3 * k;
+        gb[k].quat = E.quat + 4 * k;
+        gb[k].scale = E.scale + 2 * k;
+        gb[k].opacity = E.opacity + k;
+        gb[k].amp = E.amp + (size_t)k * nl;
+        outs[k] = U + (size_t)k * nl * hw;
+    }
+    for (long long b0 = 0; b0 < n; b0 += B) {
+        const int nb = (int)std::min<long long>(B, n - b0);
+        CU(launch_exact_gather(F.sorted, b0, nb, scene, nl, E, 1, s));
+        GS(forward_impl(gb.data(), ones.data(), nb, slm, &inner, outs.data()));
+        CU(launch_pc_apply(U, kappa, ysum, E, nb, nl, hw, s));
+        CU(launch_modulate(U, 0, nb * nl, H, W, 1.0, 1, s));
+        Plan pb;
+        if (nb == B && cached_plan(H, W, B * nl, 0, &pb)) {
+            GS(exec_fft(pb, U, at<char>(o, L.cufft), 0, CUFFT_FORWARD, s));
+        } else {
+            for (int k = 0; k < nb; ++k)
+                GS(exec_fft(p, U + (size_t)k * nl * hw, at<char>(o, L.cufft), 0, CUFFT_FORWARD, s));
+        }
+        CU(launch_modulate(U, 0, nb * nl, H, W, slm->pitch_x * slm->pitch_y, 2, s));
+        CU(launch_pc_accum(U, acc, pixtab, E, nb, nl, H, W, dfx, dfy, il, o->phase_match ? 1 : 0, s));
     }
     timer_mark(o, GWS_TIMER_SPLAT_FWD, 1, s);
     timer_mark(o, GWS_TIMER_FFT, 0, s);
@@ -521,9 +619,10 @@ static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, in
         return GWS_OK;
     }
     Front F;
-    if (o->blend == GWS_BLEND_EXACT) {
+    if (o->blend == GWS_BLEND_EXACT || o->blend == GWS_BLEND_PARTIAL_COHERENT) {
         if (dbl || n_scenes != 1) return GWS_ERR_UNSUPPORTED;
         GS(run_front(scenes, n, n_scenes, slm, o, L, false, &F, s));
+        if (o->blend == GWS_BLEND_PARTIAL_COHERENT) return pc_forward(scenes, n_total, slm, o, L, F, out[0], s);
         return exact_forward(scenes, n_total, slm, o, L, F, out[0], s);
     }
     GS(run_front(scenes, n, n_scenes, slm, o, L, o->blend == GWS_BLEND_SORTED_T, &F, s));
@@ -675,7 +774,7 @@ gws_status gws_prepare(const gws_slm *slm, const gws_opts *opts, int n_scenes) {
     Plan p;
     GS(get_plan(slm->H, slm->W, slm->n_lambda, 0, &p));
     if (n_scenes > 1) GS(get_plan(slm->H, slm->W, n_scenes * slm->n_lambda, opts->prec == GWS_PREC_FP64, &p));
-    if (opts->blend == GWS_BLEND_EXACT) {
+    if (opts->blend == GWS_BLEND_EXACT || opts->blend == GWS_BLEND_PARTIAL_COHERENT) {
         GS(get_plan(slm->H, slm->W, exact_batch(opts) * slm->n_lambda, 0, &p));
     }
     return get_plan(slm->H, slm->W, slm->n_lambda, opts->prec == GWS_PREC_FP64, &p);
@@ -693,7 +792,8 @@ gws_status gws_forward(const gws_gaussians *g, int64_t n, const gws_slm *slm, co
 gws_status gws_forward_batched(const gws_gaussians *scenes, const int64_t *n, int n_scenes, const gws_slm *slm,
                                const gws_opts *opts, void *const *field_out) {
     if (!scenes) return GWS_ERR_INVALID_ARG;
-    if (opts && opts->blend == GWS_BLEND_EXACT) return GWS_ERR_UNSUPPORTED;
+    if (opts && (opts->blend == GWS_BLEND_EXACT || opts->blend == GWS_BLEND_PARTIAL_COHERENT))
+        return GWS_ERR_UNSUPPORTED;
     t_launches = 0;
     return forward_impl(scenes, n, n_scenes, slm, opts, field_out);
 }
@@ -859,6 +959,8 @@ gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, c
     if (!grad_field || !out) return GWS_ERR_INVALID_ARG;
     if (n > 0 && (!out->mean || !out->quat || !out->scale || !out->opacity || !out->amp)) return GWS_ERR_INVALID_ARG;
     if (opts->prec != GWS_PREC_MIXED) return GWS_ERR_UNSUPPORTED;
+    // the exact blend and partial coherence are forward-only
+    if (opts->blend == GWS_BLEND_EXACT || opts->blend == GWS_BLEND_PARTIAL_COHERENT) return GWS_ERR_UNSUPPORTED;
     const bool sorted_t = opts->blend == GWS_BLEND_SORTED_T;
     const bool fft = opts->domain == GWS_DOMAIN_FIELD;
     Layout L;

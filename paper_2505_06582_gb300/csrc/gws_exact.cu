@@ -1,5 +1,6 @@
 // gws_exact.cu -- exact alpha wave blending (Eq. 5-6 with the spatial transmittance map,
-// Algorithm S2), front to back over depth-ordered batches of Gaussians:
+// Algorithm S2), front to back over depth-ordered batches of Gaussians, and the batches of
+// partially coherent GWS (Eq. 14; see the kernels after k_exact_accum):
 //   u_k = the Gaussian's field on its own depth plane (Eq. 10 with the depth of the mean
 //         set to zero, then the inverse DFT; produced by the batched forward),
 //   u_SLM(f) += c_k o_k F(T u_k)(f) H(f, -z_k),   H(f, z) = exp(j 2 pi z f_z),
@@ -13,13 +14,17 @@ namespace gws {
 
 __global__ void k_exact_gather(const unsigned *__restrict__ sorted, long long b0, int nb, const double *__restrict__ mean,
                                const float *__restrict__ quat, const float *__restrict__ scale,
-                               const float *__restrict__ opacity, const float *__restrict__ amp, int L, ExactBatch E) {
+                               const float *__restrict__ opacity, const float *__restrict__ amp, int L, ExactBatch E,
+                               int pc) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nb) return;
     const long long i = sorted[b0 + k];
-    E.mean[3 * k] = mean[3 * i];
-    E.mean[3 * k + 1] = mean[3 * i + 1];
-    E.mean[3 * k + 2] = 0.0;  // the field on the Gaussian's own plane
+    // the field on the Gaussian's own plane; partial coherence: at the origin (translated after the kernel)
+    E.mean[3 * k] = pc ? 0.0 : mean[3 * i];
+    E.mean[3 * k + 1] = pc ? 0.0 : mean[3 * i + 1];
+    E.mean[3 * k + 2] = 0.0;
+    if (pc)
+        for (int c = 0; c < 3; ++c) E.mu[3 * k + c] = mean[3 * i + c];
     for (int m = 0; m < 4; ++m) E.quat[4 * k + m] = quat[4 * i + m];
     E.scale[2 * k] = scale[2 * i];
     E.scale[2 * k + 1] = scale[2 * i + 1];
@@ -60,13 +65,17 @@ __global__ void k_exact_mask(float2 *__restrict__ U, float *__restrict__ Tm, Exa
 
 constexpr int ETW = 64, ETH = 32, EPX = 8;  // the tiles of the per-pixel table (f_z - f0_z, log2 1/f_z)
 
-// acc(f) += sum_k V_k(f) exp(-j 2 pi f_z z_k), f_z z_k = f0_z z_k (FP64, per tile) + (f_z - f0_z) z_k (FP32)
+// acc(f) += sum_k V_k(f) exp(-j 2 pi f_z z_k), f_z z_k = f0_z z_k (FP64, per tile) + (f_z - f0_z) z_k (FP32).
+// FULL (partial coherence): the whole ramp exp(-j 2 pi f . mu_k) (x exp(+j 2 pi mu_z / lambda) with
+// phase matching), anchored the same way: f . mu = f0 . mu (FP64) + (f - f0) . mu (FP32).
+template <bool FULL>
 __global__ void __launch_bounds__((ETW / EPX) * ETH) k_exact_accum(const float2 *__restrict__ V, float2 *__restrict__ acc,
                                                                    const float2 *__restrict__ pixtab, ExactBatch E,
                                                                    int nb, int L, int H, int W, double dfx, double dfy,
-                                                                   InvLam il) {
-    __shared__ float s_th[GWS_MAX_SCENES], s_mz[GWS_MAX_SCENES];
-    __shared__ double s_f0z;
+                                                                   InvLam il, int phase_match) {
+    __shared__ float s_th[GWS_MAX_SCENES], s_mz[GWS_MAX_SCENES], s_mx[GWS_MAX_SCENES], s_my[GWS_MAX_SCENES];
+    __shared__ double s_f0z, s_f0x, s_f0y;
+    __shared__ int s_cref, s_rref;
     const int tiles_x = (W + ETW - 1) / ETW;
     const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
     const int l = blockIdx.y;
@@ -78,19 +87,35 @@ __global__ void __launch_bounds__((ETW / EPX) * ETH) k_exact_accum(const float2 
         tile_ref(c_lo, c_hi, r_lo, r_hi, H, W, dfx, dfy, inv_lam * inv_lam, c_ref, r_ref);
         const double f0x = (double)(c_ref - W / 2) * dfx, f0y = (double)(r_ref - H / 2) * dfy;
         s_f0z = sqrt(fmax(inv_lam * inv_lam - (f0x * f0x + f0y * f0y), 0.0));
+        s_f0x = f0x;
+        s_f0y = f0y;
+        s_cref = c_ref;
+        s_rref = r_ref;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-        double cyc = -s_f0z * E.zk[k];
-        cyc -= rint(cyc);
-        s_th[k] = (float)(kTwoPi * cyc);
-        s_mz[k] = (float)(-kTwoPi * E.zk[k]);
+        if (FULL) {
+            const double mx = E.mu[3 * k], my = E.mu[3 * k + 1], mz = E.mu[3 * k + 2];
+            double cyc = -(s_f0x * mx + s_f0y * my + s_f0z * mz);
+            if (phase_match) cyc += mz * inv_lam;
+            cyc -= rint(cyc);
+            s_th[k] = (float)(kTwoPi * cyc);
+            s_mx[k] = (float)(-kTwoPi * mx);
+            s_my[k] = (float)(-kTwoPi * my);
+            s_mz[k] = (float)(-kTwoPi * mz);
+        } else {
+            double cyc = -s_f0z * E.zk[k];
+            cyc -= rint(cyc);
+            s_th[k] = (float)(kTwoPi * cyc);
+            s_mz[k] = (float)(-kTwoPi * E.zk[k]);
+        }
     }
     __syncthreads();
     const int row = r_lo + threadIdx.x / (ETW / EPX);
     const int col0 = c_lo + (threadIdx.x % (ETW / EPX)) * EPX;
     if (row >= H) return;
     const long long hw = (long long)H * W;
+    const float dyf = (float)((double)(row - s_rref) * dfy);
 #pragma unroll
     for (int p = 0; p < EPX; ++p) {
         const int col = col0 + p;
@@ -98,10 +123,12 @@ __global__ void __launch_bounds__((ETW / EPX) * ETH) k_exact_accum(const float2 
         const long long pix = (long long)row * W + col;
         const float2 pt = pixtab[(size_t)l * hw + pix];
         if (!(pt.y > -INFINITY)) continue;  // evanescent: H = 0
+        const float dxf = (float)((double)(col - s_cref) * dfx);
         float2 a = acc[(size_t)l * hw + pix];
         for (int k = 0; k < nb; ++k) {
             const float2 v = V[((size_t)k * L + l) * hw + pix];
-            const float t = fmaf(s_mz[k], pt.x, s_th[k]);
+            const float t = FULL ? fmaf(s_mz[k], pt.x, fmaf(s_my[k], dyf, fmaf(s_mx[k], dxf, s_th[k])))
+                                 : fmaf(s_mz[k], pt.x, s_th[k]);
             const float kr = __fadd_rn(fmaf(t, 0.15915494309189535f, 12582912.0f), -12582912.0f);
             const float ang = fmaf(kr, -6.28318530717958647692f, t);
             float sn, cs;
@@ -113,11 +140,96 @@ __global__ void __launch_bounds__((ETW / EPX) * ETH) k_exact_accum(const float2 
     }
 }
 
+// ---- partial coherence (Eq. 14) ---------------------------------------------------------
+
+// SplitMix64 (Steele, Lea and Flood, 2014): output number `ctr` of the stream seeded with `seed`
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long ctr) {
+    unsigned long long z = seed + ctr * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// real spherical harmonic Y_l^m (degree <= 3, Condon-Shortley phase, normalised) at unit (x, y, z)
+__device__ double sh_lm(int l, int m, double x, double y, double z) {
+    const double pi = 3.14159265358979323846;
+    switch (l * l + l + m) {
+        case 0: return 0.5 / sqrt(pi);
+        case 1: return -sqrt(3.0 / (4.0 * pi)) * y;
+        case 2: return sqrt(3.0 / (4.0 * pi)) * z;
+        case 3: return -sqrt(3.0 / (4.0 * pi)) * x;
+        case 4: return sqrt(15.0 / (4.0 * pi)) * x * y;
+        case 5: return -sqrt(15.0 / (4.0 * pi)) * y * z;
+        case 6: return sqrt(5.0 / (16.0 * pi)) * (3.0 * z * z - 1.0);
+        case 7: return -sqrt(15.0 / (4.0 * pi)) * x * z;
+        case 8: return sqrt(15.0 / (16.0 * pi)) * (x * x - y * y);
+        case 9: return -sqrt(35.0 / (32.0 * pi)) * y * (3.0 * x * x - y * y);
+        case 10: return sqrt(105.0 / (4.0 * pi)) * x * y * z;
+        case 11: return -sqrt(21.0 / (32.0 * pi)) * y * (5.0 * z * z - 1.0);
+        case 12: return sqrt(7.0 / (16.0 * pi)) * z * (5.0 * z * z - 3.0);
+        case 13: return -sqrt(21.0 / (32.0 * pi)) * x * (5.0 * z * z - 1.0);
+        case 14: return sqrt(105.0 / (16.0 * pi)) * z * (x * x - y * y);
+        default: return -sqrt(35.0 / (32.0 * pi)) * x * (x * x - 3.0 * y * y);
+    }
+}
+
+// K(f) = Y_l^m(lambda f) e^{j phi(f)} on the centred grid (0 where evanescent); ysum[l] += sum Y^2
+__global__ void __launch_bounds__(256) k_pc_kernel(float2 *__restrict__ K, double *__restrict__ ysum, int sh_l, int sh_m,
+                                                   unsigned long long seed, unsigned long long frame, int L, int H,
+                                                   int W, double dfx, double dfy, InvLam il) {
+    __shared__ double red[8];
+    const long long hw = (long long)H * W;
+    const int l = blockIdx.y;
+    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double y2 = 0.0;
+    if (pix < hw) {
+        const int r = (int)(pix / W), c = (int)(pix % W);
+        const double lam = 1.0 / il.v[l];
+        const double fx = (double)(c - W / 2) * dfx, fy = (double)(r - H / 2) * dfy;
+        const double k2 = il.v[l] * il.v[l], rho2 = fx * fx + fy * fy;
+        float2 v = make_float2(0.f, 0.f);
+        if (rho2 < k2) {
+            const double fz = sqrt(k2 - rho2);
+            const double Y = sh_lm(sh_l, sh_m, fx * lam, fy * lam, fz * lam);
+            const unsigned long long ctr = (frame * (unsigned long long)L + (unsigned long long)l) * (unsigned long long)hw +
+                                           (unsigned long long)pix + 1ull;
+            const double u = (double)(splitmix64(seed, ctr) >> 11) * 0x1.0p-53;
+            double sn, cs;
+            sincos(6.283185307179586476925 * u - 3.14159265358979323846, &sn, &cs);
+            v = make_float2((float)(Y * cs), (float)(Y * sn));
+            y2 = Y * Y;
+        }
+        K[(size_t)l * hw + pix] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) y2 += __shfl_xor_sync(0xffffffffu, y2, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = y2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        atomicAdd(ysum + l, t);
+    }
+}
+
+__global__ void k_pc_apply(float2 *__restrict__ U, const float2 *__restrict__ kappa, const double *__restrict__ ysum,
+                           ExactBatch E, int nb, int L, long long hw) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= hw * L * nb) return;
+    const int kl = (int)(idx / hw);  // k * L + l
+    const int l = kl % L;
+    const long long pix = idx % hw;
+    const float s = E.co[kl] * (float)(1.0 / sqrt(ysum[l]));
+    const float2 a = kappa[(size_t)l * hw + pix];
+    const float2 u = U[idx];
+    U[idx] = make_float2(s * (u.x * a.x - u.y * a.y), s * (u.x * a.y + u.y * a.x));
+}
+
 static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 cudaError_t launch_exact_gather(const unsigned *sorted, long long b0, int nb, const gws_gaussians *g, int L,
-                                const ExactBatch &E, cudaStream_t s) {
-    k_exact_gather<<<nblk(nb, 128), 128, 0, s>>>(sorted, b0, nb, g->mean, g->quat, g->scale, g->opacity, g->amp, L, E);
+                                const ExactBatch &E, int pc, cudaStream_t s) {
+    k_exact_gather<<<nblk(nb, 128), 128, 0, s>>>(sorted, b0, nb, g->mean, g->quat, g->scale, g->opacity, g->amp, L, E,
+                                                 pc);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -139,7 +251,32 @@ cudaError_t launch_exact_mask(float2 *U, float *T, const ExactBatch &E, int nb, 
 cudaError_t launch_exact_accum(const float2 *V, float2 *acc, const float2 *pixtab, const ExactBatch &E, int nb, int L,
                                int H, int W, double dfx, double dfy, const InvLam &il, cudaStream_t s) {
     const int tiles = ((W + ETW - 1) / ETW) * ((H + ETH - 1) / ETH);
-    k_exact_accum<<<dim3(tiles, L), (ETW / EPX) * ETH, 0, s>>>(V, acc, pixtab, E, nb, L, H, W, dfx, dfy, il);
+    k_exact_accum<false><<<dim3(tiles, L), (ETW / EPX) * ETH, 0, s>>>(V, acc, pixtab, E, nb, L, H, W, dfx, dfy, il, 0);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pc_kernel(float2 *K, double *ysum, int sh_l, int sh_m, unsigned long long seed,
+                             unsigned long long frame, int L, int H, int W, double dfx, double dfy, const InvLam &il,
+                             cudaStream_t s) {
+    const long long hw = (long long)H * W;
+    k_pc_kernel<<<dim3(nblk(hw, 256), L), 256, 0, s>>>(K, ysum, sh_l, sh_m, seed, frame, L, H, W, dfx, dfy, il);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pc_apply(float2 *U, const float2 *kappa, const double *ysum, const ExactBatch &E, int nb, int L,
+                            long long hw, cudaStream_t s) {
+    k_pc_apply<<<nblk(hw * L * nb, 256), 256, 0, s>>>(U, kappa, ysum, E, nb, L, hw);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pc_accum(const float2 *V, float2 *acc, const float2 *pixtab, const ExactBatch &E, int nb, int L,
+                            int H, int W, double dfx, double dfy, const InvLam &il, int phase_match, cudaStream_t s) {
+    const int tiles = ((W + ETW - 1) / ETW) * ((H + ETH - 1) / ETH);
+    k_exact_accum<true><<<dim3(tiles, L), (ETW / EPX) * ETH, 0, s>>>(V, acc, pixtab, E, nb, L, H, W, dfx, dfy, il,
+                                                                     phase_match);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -44,9 +44,23 @@ struct ExactBatch {  // one batch of exact blending (Gaussians in depth order)
     double *zk;      // [B] depths
     float *co;       // [B][L] c o
     float *ok;       // [B] o
+    double *mu;      // [B][3] the means (partial coherence: the inner fields sit at the origin)
 };
+// pc = 0: exact blending (the means keep x, y; depth zeroed); pc = 1: partial coherence (means zeroed)
 cudaError_t launch_exact_gather(const unsigned *sorted, long long b0, int nb, const gws_gaussians *g, int L,
-                                const ExactBatch &E, cudaStream_t s);
+                                const ExactBatch &E, int pc, cudaStream_t s);
+// partial coherence: the angular kernel K [L][H][W] (FP32 complex) and sum_f Y^2 per wavelength
+// (accumulated into ysum, which must be zeroed first)
+cudaError_t launch_pc_kernel(float2 *K, double *ysum, int sh_l, int sh_m, unsigned long long seed,
+                             unsigned long long frame, int L, int H, int W, double dfx, double dfy,
+                             const InvLam &il, cudaStream_t s);
+// w_k = c_k o_k u_k kappa / sqrt(ysum) in place, for the batch's fields U [nb][L][H][W]
+cudaError_t launch_pc_apply(float2 *U, const float2 *kappa, const double *ysum, const ExactBatch &E, int nb, int L,
+                            long long hw, cudaStream_t s);
+// acc += sum_k V_k(f) e^{-j 2 pi f . mu_k} (x e^{+j 2 pi mu_z / lambda} with phase matching)
+cudaError_t launch_pc_accum(const float2 *V, float2 *acc, const float2 *pixtab, const ExactBatch &E, int nb, int L,
+                            int H, int W, double dfx, double dfy, const InvLam &il, int phase_match,
+                            cudaStream_t s);
 cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s);
 cudaError_t launch_exact_mask(float2 *U, float *T, const ExactBatch &E, int nb, int L, long long hw, float t_eps,
                               float t_bin, cudaStream_t s);

@@ -18,7 +18,7 @@ import torch
 
 from . import _build
 
-BLEND_OIT, BLEND_SORTED_T, BLEND_EXACT = 0, 1, 2
+BLEND_OIT, BLEND_SORTED_T, BLEND_EXACT, BLEND_PARTIAL_COHERENT = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
 DOMAIN_FIELD, DOMAIN_SPECTRUM = 0, 1
 PROJ_PERSPECTIVE, PROJ_ORTHOGRAPHIC = 0, 1
@@ -52,7 +52,8 @@ class _Opts(C.Structure):
                 ("trunc_eps", C.c_float), ("alpha_min", C.c_float), ("tile_cfg", C.c_int),
                 ("debug_flags", C.c_uint32), ("timeout_cycles", C.c_uint64), ("stream", C.c_void_p),
                 ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t), ("t_binarize", C.c_float),
-                ("exact_batch", C.c_int)]
+                ("exact_batch", C.c_int), ("pc_l", C.c_int), ("pc_m", C.c_int), ("pc_seed", C.c_uint64),
+                ("pc_frame", C.c_uint64)]
 
 
 class _GaussiansOut(C.Structure):
@@ -191,7 +192,7 @@ _WS = _Workspace()
 
 def make_opts(blend=BLEND_OIT, prec=PREC_MIXED, domain=DOMAIN_FIELD, phase_match=False, trunc_eps=1e-5,
               alpha_min=1.0 / 255.0, tile_cfg=0, debug_flags=0, timeout_cycles=2_000_000_000, stream=None,
-              t_binarize=0.0, exact_batch=0):
+              t_binarize=0.0, exact_batch=0, pc_l=0, pc_m=0, pc_seed=0, pc_frame=0):
     lib = load()
     o = _Opts()
     lib.gws_opts_default(C.byref(o))
@@ -199,6 +200,7 @@ def make_opts(blend=BLEND_OIT, prec=PREC_MIXED, domain=DOMAIN_FIELD, phase_match
     o.trunc_eps, o.alpha_min, o.tile_cfg = float(trunc_eps), float(alpha_min), int(tile_cfg)
     o.debug_flags, o.timeout_cycles = int(debug_flags), int(timeout_cycles)
     o.t_binarize, o.exact_batch = float(t_binarize), int(exact_batch)
+    o.pc_l, o.pc_m, o.pc_seed, o.pc_frame = int(pc_l), int(pc_m), int(pc_seed), int(pc_frame)
     if stream is None:
         stream = torch.cuda.current_stream()
     o.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
