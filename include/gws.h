@@ -274,6 +274,35 @@ GWS_API int gws_last_launch_count(void);
 GWS_API gws_status gws_autotune(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
                         void *field_scratch, int *best_cfg);
 
+/* ---- triangle primitive (supplement, polygon-based methods) ----------------------------------
+ *
+ * Eq. 10 with the canonical Gaussian replaced by the canonical triangle {(0,0), (1,0), (1,1)}:
+ * for vertices v1, v2, v3 (hologram space), r1 = unit(v2 - v1), r3 = unit((v2 - v1) x (v3 - v1)),
+ * r2 = r3 x r1, V_o = [[r1.(v2-v1), r1.(v3-v1)], [0, r2.(v3-v1)]], A = [[1,1],[0,1]] V_o^-1 and
+ *   u_hat(f) = c o |r3 . f| / f_z |det V_o| T(A^-T (r1 . d, r2 . d)) e^{-j 2 pi f . v1}
+ * (the affine theorem of Eq. 8; d = f - f_r, the on-axis reference wave of Sec. 4.1; T the
+ * canonical triangle's spectrum; phase matching multiplies by e^{+j 2 pi v1_z / lambda}),
+ * summed over triangles as in Eq. 12.  Every (triangle, frequency) pair is evaluated (the
+ * spectrum of a triangle has no compact footprint). */
+typedef struct { /* device memory */
+    const double *vertices; /* [n][3][3]: v1, v2, v3, metres */
+    const float *opacity;   /* [n] */
+    const float *amp;       /* [n][n_lambda] */
+} gws_triangles;
+
+/* Workspace bytes for gws_forward_triangles with n triangles (opts.prec must be MIXED). */
+GWS_API gws_status gws_triangles_workspace_size(int64_t n, const gws_slm *slm, const gws_opts *opts, size_t *bytes);
+
+/* The field (or, with GWS_DOMAIN_SPECTRUM, the spectrum) of n triangles, complex64
+ * [n_lambda][H][W] in field_out (device).  opts: prec MIXED (FP32 with FP64 per-(triangle, tile)
+ * phase anchors), domain, phase_match, stream, workspace, GWS_DEBUG_TIME_KERNELS (the splat under
+ * GWS_TIMER_SPLAT_FWD); blend is ignored.  A degenerate (zero-area) or non-finite triangle
+ * contributes nothing and is recorded in the device status word (gws_get_device_status then
+ * returns GWS_ERR_INVALID_ARG or GWS_ERR_NONFINITE).  Errors: GWS_ERR_INVALID_ARG,
+ * GWS_ERR_UNSUPPORTED (FP64), GWS_ERR_WORKSPACE, GWS_ERR_CUDA. */
+GWS_API gws_status gws_forward_triangles(const gws_triangles *t, int64_t n, const gws_slm *slm, const gws_opts *opts,
+                                         void *field_out);
+
 /* ---- holographics front end (Supplement Sec. 1.1) and view-dependent opacity (Sec. 4.2) ----
  *
  * Turns Gaussians optimised in world space (e.g. by a 2DGS / 2DGS-OIT model) into the

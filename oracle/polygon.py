@@ -104,36 +104,51 @@ def frame(v):
     return R, Vo, A
 
 
-def spectrum(vertices, opacity, amp, slm, phase_match=False):
-    """u_hat_SLM(f), complex128 [n_lambda][H][W], of triangles (vertices [n,3,3], rows v1, v2, v3)."""
-    vertices = np.asarray(vertices, dtype=np.float64)
-    n = vertices.shape[0]
+def _at(vertices, opacity, amp, l, lam, FX, FY, phase_match):
+    """Sum over triangles of their spectra at the frequencies (FX, FY) (any shape), wavelength l."""
     R, Vo, A = frame(vertices)
     AinvT = np.transpose(np.linalg.inv(A), (0, 2, 1))
     detVo = np.abs(np.linalg.det(Vo))
+    k2 = 1.0 / lam ** 2
+    rho2 = FX ** 2 + FY ** 2
+    prop = rho2 < k2
+    FZ = np.sqrt(np.where(prop, k2 - rho2, 0.0))
+    DZ = FZ - 1.0 / lam
+    out = np.zeros(FX.shape, dtype=np.complex128)
+    for i in range(vertices.shape[0]):
+        r1, r2, r3 = R[i, :, 0], R[i, :, 1], R[i, :, 2]
+        do = np.stack([r1[0] * FX + r1[1] * FY + r1[2] * DZ, r2[0] * FX + r2[1] * FY + r2[2] * DZ])
+        nu = np.tensordot(AinvT[i], do, axes=(1, 0))
+        jac = np.abs(r3[0] * FX + r3[1] * FY + r3[2] * FZ) / np.where(prop, FZ, 1.0)
+        v1 = vertices[i, 0]
+        ph = -2.0 * np.pi * (FX * v1[0] + FY * v1[1] + FZ * v1[2])
+        if phase_match:
+            ph = ph + 2.0 * np.pi * v1[2] / lam
+        t = float(opacity[i]) * float(amp[i, l]) * jac * detVo[i] * canonical(nu[0], nu[1]) * np.exp(1j * ph)
+        out += np.where(prop, t, 0.0)
+    return out
+
+
+def spectrum(vertices, opacity, amp, slm, phase_match=False):
+    """u_hat_SLM(f), complex128 [n_lambda][H][W], of triangles (vertices [n,3,3], rows v1, v2, v3)."""
+    vertices = np.asarray(vertices, dtype=np.float64)
     H, W = slm.H, slm.W
     fx = (np.arange(W) - W // 2) / (W * slm.pitch_x)
     fy = (np.arange(H) - H // 2) / (H * slm.pitch_y)
     FX, FY = np.meshgrid(fx, fy)
     out = np.zeros((slm.n_lambda, H, W), dtype=np.complex128)
     for l, lam in enumerate(slm.wavelengths):
-        k2 = 1.0 / lam ** 2
-        rho2 = FX ** 2 + FY ** 2
-        prop = rho2 < k2
-        FZ = np.sqrt(np.where(prop, k2 - rho2, 0.0))
-        DZ = FZ - 1.0 / lam
-        for i in range(n):
-            r1, r2, r3 = R[i, :, 0], R[i, :, 1], R[i, :, 2]
-            do = np.stack([r1[0] * FX + r1[1] * FY + r1[2] * DZ, r2[0] * FX + r2[1] * FY + r2[2] * DZ])
-            nu = np.einsum("ij,jhw->ihw", AinvT[i], do)
-            jac = np.abs(r3[0] * FX + r3[1] * FY + r3[2] * FZ) / np.where(prop, FZ, 1.0)
-            v1 = vertices[i, 0]
-            ph = -2.0 * np.pi * (FX * v1[0] + FY * v1[1] + FZ * v1[2])
-            if phase_match:
-                ph = ph + 2.0 * np.pi * v1[2] / lam
-            t = float(opacity[i]) * float(amp[i, l]) * jac * detVo[i] * canonical(nu[0], nu[1]) * np.exp(1j * ph)
-            out[l] += np.where(prop, t, 0.0)
+        out[l] = _at(vertices, opacity, amp, l, lam, FX, FY, phase_match)
     return out
+
+
+def spectrum_at(vertices, opacity, amp, slm, l, rows, cols, phase_match=False):
+    """u_hat_SLM at grid samples (rows, cols) of wavelength index l."""
+    vertices = np.asarray(vertices, dtype=np.float64)
+    FX = (np.asarray(cols) - slm.W // 2) / (slm.W * slm.pitch_x)
+    FY = (np.asarray(rows) - slm.H // 2) / (slm.H * slm.pitch_y)
+    return _at(vertices, opacity, amp, l, slm.wavelengths[l], FX.astype(np.float64), FY.astype(np.float64),
+               phase_match)
 
 
 def field(vertices, opacity, amp, slm, phase_match=False):

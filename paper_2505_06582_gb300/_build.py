@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgws.so")
 SOURCES = ["gws_api.cu", "gws_prep.cu", "gws_sort.cu", "gws_splat.cu", "gws_bwd.cu", "gws_noalloc.cu", "gws_exact.cu",
-           "gws_front.cu"]
+           "gws_front.cu", "gws_tri.cu"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

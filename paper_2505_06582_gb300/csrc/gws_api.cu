@@ -1080,4 +1080,79 @@ gws_status gws_autotune(const gws_gaussians *g, int64_t n, const gws_slm *slm, c
     return GWS_OK;
 }
 
+// ---- triangle primitive ----------------------------------------------------------------------
+
+struct TriLayout {
+    size_t status, rec, w, cufft, total;
+};
+
+static gws_status tri_layout(int64_t n, const gws_slm *slm, bool fft, TriLayout *L) {
+    Planner P;
+    L->status = P.take(16);  // first: gws_get_device_status reads the word at the workspace start
+    L->rec = P.take(sizeof(TriRec) * (size_t)n);
+    L->w = P.take(sizeof(float) * (size_t)n * slm->n_lambda);
+    size_t work = 0;
+    if (fft) {
+        Plan p;
+        GS(get_plan(slm->H, slm->W, slm->n_lambda, 0, &p));
+        work = p.work;
+    }
+    L->cufft = P.take(std::max<size_t>(work, 16));
+    L->total = P.cur;
+    return GWS_OK;
+}
+
+gws_status gws_triangles_workspace_size(int64_t n, const gws_slm *slm, const gws_opts *opts, size_t *bytes) {
+    GS(check_slm(slm));
+    GS(check_opts(opts));
+    if (!bytes || n < 0 || n > (1ll << 30)) return GWS_ERR_INVALID_ARG;
+    if (opts->prec != GWS_PREC_MIXED) return GWS_ERR_UNSUPPORTED;
+    TriLayout L;
+    GS(tri_layout(n, slm, opts->domain == GWS_DOMAIN_FIELD, &L));
+    *bytes = L.total;
+    return GWS_OK;
+}
+
+gws_status gws_forward_triangles(const gws_triangles *t, int64_t n, const gws_slm *slm, const gws_opts *opts,
+                                 void *field_out) {
+    t_launches = 0;
+    GS(check_slm(slm));
+    GS(check_opts(opts));
+    if (!field_out || n < 0 || n > (1ll << 30)) return GWS_ERR_INVALID_ARG;
+    if (n > 0 && (!t || !t->vertices || !t->opacity || !t->amp)) return GWS_ERR_INVALID_ARG;
+    if (opts->prec != GWS_PREC_MIXED) return GWS_ERR_UNSUPPORTED;
+    const bool fft = opts->domain == GWS_DOMAIN_FIELD;
+    TriLayout L;
+    GS(tri_layout(n, slm, fft, &L));
+    if (!opts->workspace || opts->workspace_bytes < L.total) return GWS_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(opts->workspace) % 256 != 0) return GWS_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)opts->stream;
+    const int nl = slm->n_lambda, H = slm->H, W = slm->W;
+    const double dfx = 1.0 / (W * slm->pitch_x), dfy = 1.0 / (H * slm->pitch_y);
+    timers_reset(opts);
+    timer_mark(opts, GWS_TIMER_TOTAL, 0, s);
+    CU(cudaMemsetAsync(at<char>(opts, L.status), 0, 16, s));
+    InvLam il;
+    std::memset(&il, 0, sizeof il);
+    for (int l = 0; l < nl; ++l) il.v[l] = 1.0 / slm->wavelengths[l];
+    TriRec *rec = at<TriRec>(opts, L.rec);
+    float *w = at<float>(opts, L.w);
+    CU(launch_tri_prep(n > 0 ? t->vertices : nullptr, n > 0 ? t->opacity : nullptr, n > 0 ? t->amp : nullptr, n, nl,
+                       rec, w, at<int>(opts, L.status), s));
+    timer_mark(opts, GWS_TIMER_SPLAT_FWD, 0, s);
+    CU(launch_splat_tri(rec, w, n, nl, H, W, dfx, dfy, il, fft ? 1 : 0, opts->phase_match ? 1 : 0,
+                        static_cast<float2 *>(field_out), s));
+    timer_mark(opts, GWS_TIMER_SPLAT_FWD, 1, s);
+    if (fft) {
+        Plan p;
+        GS(get_plan(H, W, nl, 0, &p));
+        timer_mark(opts, GWS_TIMER_FFT, 0, s);
+        GS(exec_fft(p, field_out, at<char>(opts, L.cufft), 0, CUFFT_INVERSE, s));
+        CU(launch_modulate(field_out, 0, nl, H, W, dfx * dfy, 0, s));
+        timer_mark(opts, GWS_TIMER_FFT, 1, s);
+    }
+    timer_mark(opts, GWS_TIMER_TOTAL, 1, s);
+    return GWS_OK;
+}
+
 }  // extern "C"

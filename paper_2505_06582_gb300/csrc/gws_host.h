@@ -110,6 +110,20 @@ struct InvLam {
 
 cudaError_t launch_pixtab(int n_lambda, int H, int W, double dfx, double dfy, const InvLam &il, int tw, int th,
                           float2 *tab, cudaStream_t s);
+
+// ---- triangle primitive ------------------------------------------------------------------
+
+struct TriRec {     // 64 B per triangle
+    double v1[3];   // first vertex (the translation)
+    float M[6];     // rows of A^-T [r1; r2]: nu = M d, d = f - f_r
+    float r3[3];    // unit normal
+    float pad;
+};
+cudaError_t launch_tri_prep(const double *v, const float *opacity, const float *amp, long long n, int L, TriRec *rec,
+                            float *w, int *status, cudaStream_t s);
+cudaError_t launch_splat_tri(const TriRec *rec, const float *w, long long n, int L, int H, int W, double dfx,
+                             double dfy, const InvLam &il, int field_mode, int phase_match, float2 *out,
+                             cudaStream_t s);
 cudaError_t launch_splat_bwd(const BwdArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_grad_assemble(const GPre *gp, const float *ampc, const double *T_g, const int *invrec,
                                  const double *acc, const float *quat_in, long long n, int L, const GradArgs &G,

@@ -1,0 +1,259 @@
+// gws_tri.cu -- the triangle primitive of the supplement's section on polygon-based methods:
+// Eq. 10 with the canonical Gaussian replaced by the canonical triangle P = {(0,0), (1,0), (1,1)},
+// the 2D affine map A = [[1,1],[0,1]] V_o^-1 (affine theorem of Eq. 8: factor |det V_o|, argument
+// A^-T k_o) and the translation mu = v1, summed over triangles as in Eq. 12:
+//   u_hat(f) = c o |r3 . f| / f_z |det V_o| T(A^-T (r1 . d, r2 . d)) e^{-j 2 pi f . v1},  d = f - f_r.
+// T(nu) = int_P e^{-j 2 pi nu . x} dx is the second divided difference of exp at the vertex
+// phases z = j (0, -a, -(a + b)), a = 2 pi nu_x, b = 2 pi nu_y, evaluated in FP32 as
+//   (E[t1,t2] - E[t0,t1]) / (j (t2 - t0)),  E[p,q] = e^{j (p+q)/2} sin((q-p)/2) / ((q-p)/2),
+// with t0 <= t1 <= t2 the sorted phases when their spread exceeds TRI_SPREAD, else as the series
+// e^{j tbar} sum_k j^k h_k(t - tbar) / (k+2)! (h_k the complete homogeneous polynomials).
+// Dense: the spectrum of a triangle has no compact footprint.  One CTA per (tile, wavelength);
+// triangles stream through shared memory in chunks with per-(triangle, tile) FP64 phase anchors.
+#include "gws_prep.h"
+
+namespace gws {
+
+constexpr int TTW = 32, TTH = 16, TNT = 256;  // 2 pixels (columns c, c + 16) per thread
+constexpr float TRI_SPREAD = 0.5f;
+
+__global__ void k_tri_prep(const double *__restrict__ v, const float *__restrict__ opacity,
+                           const float *__restrict__ amp, long long n, int L, TriRec *__restrict__ rec,
+                           float *__restrict__ w, int *__restrict__ status) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *p = v + 9 * i;
+    double e2[3], e3[3];
+    for (int k = 0; k < 3; ++k) {
+        e2[k] = p[3 + k] - p[k];
+        e3[k] = p[6 + k] - p[k];
+    }
+    bool fin = true;
+    for (int k = 0; k < 9; ++k) fin = fin && isfinite(p[k]);
+    const double n2 = sqrt(e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]);
+    double nr[3] = {e2[1] * e3[2] - e2[2] * e3[1], e2[2] * e3[0] - e2[0] * e3[2], e2[0] * e3[1] - e2[1] * e3[0]};
+    const double nn = sqrt(nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
+    const double n3 = sqrt(e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2]);
+    const float o = opacity[i];
+    TriRec r;
+    // degenerate: an edge of zero length or the edges (nearly) parallel (sine of their angle < 1e-9)
+    if (!fin || !(n2 > 0.0) || !(nn > 1e-9 * n2 * n3) || !isfinite(o)) {
+        atomicOr(status, fin && isfinite(o) ? ST_BADVALUE : ST_NONFINITE);
+        for (int k = 0; k < 6; ++k) r.M[k] = 0.f;
+        r.r3[0] = r.r3[1] = r.r3[2] = 0.f;
+        r.v1[0] = r.v1[1] = r.v1[2] = 0.0;
+        rec[i] = r;
+        for (int l = 0; l < L; ++l) w[i * L + l] = 0.f;
+        return;
+    }
+    double r1[3], r3[3], r2[3];
+    for (int k = 0; k < 3; ++k) {
+        r1[k] = e2[k] / n2;
+        r3[k] = nr[k] / nn;
+    }
+    r2[0] = r3[1] * r1[2] - r3[2] * r1[1];
+    r2[1] = r3[2] * r1[0] - r3[0] * r1[2];
+    r2[2] = r3[0] * r1[1] - r3[1] * r1[0];
+    // V_o = [[p, q], [0, s]] (columns: vertices 2 and 3 in the triangle's frame), A = [[1,1],[0,1]] V_o^-1
+    const double vp = n2, vq = r1[0] * e3[0] + r1[1] * e3[1] + r1[2] * e3[2];
+    const double vs = r2[0] * e3[0] + r2[1] * e3[1] + r2[2] * e3[2];
+    // A^-1 = V_o [[1,1],[0,1]]^-1 = [[p, q - p], [0, s]], so A^-T = [[p, 0], [q - p, s]]
+    const double ait[2][2] = {{vp, 0.0}, {vq - vp, vs}};
+    for (int k = 0; k < 3; ++k) {
+        r.M[k] = (float)(ait[0][0] * r1[k] + ait[0][1] * r2[k]);
+        r.M[3 + k] = (float)(ait[1][0] * r1[k] + ait[1][1] * r2[k]);
+        r.r3[k] = (float)r3[k];
+        r.v1[k] = p[k];
+    }
+    rec[i] = r;
+    const double det = vp * vs;  // |det V_o| (s > 0 by construction)
+    for (int l = 0; l < L; ++l) w[i * L + l] = (float)(det * (double)o * (double)amp[i * L + l]);
+}
+
+// e^{j x} for |x| up to a few thousand radians: x - 2 pi round(x / 2 pi) first (FP32 rounding trick)
+__device__ __forceinline__ float2 cis_reduced(float x) {
+    const float k = __fadd_rn(fmaf(x, 0.15915494309189535f, 12582912.0f), -12582912.0f);
+    const float r = fmaf(k, -6.28318530717958647692f, x);
+    return make_float2(cos_approx(r), sin_approx(r));
+}
+
+// T(nu) of the canonical triangle from its sorted vertex phases t0 <= t1 <= t2 (z = j t)
+__device__ __forceinline__ float2 tri_canonical(float t0, float t1, float t2) {
+    const float sp = t2 - t0;
+    if (sp > TRI_SPREAD) {
+        // E[p,q] = e^{j (p+q)/2} sinc((q-p)/2)
+        const float h12 = 0.5f * (t2 - t1), h01 = 0.5f * (t1 - t0);
+        const float s12 = h12 > 1e-4f ? sin_approx(h12 - 6.28318530717958647692f *
+                                                       __fadd_rn(fmaf(h12, 0.15915494309189535f, 12582912.0f), -12582912.0f)) /
+                                            h12
+                                      : 1.f - h12 * h12 * (1.f / 6.f);
+        const float s01 = h01 > 1e-4f ? sin_approx(h01 - 6.28318530717958647692f *
+                                                       __fadd_rn(fmaf(h01, 0.15915494309189535f, 12582912.0f), -12582912.0f)) /
+                                            h01
+                                      : 1.f - h01 * h01 * (1.f / 6.f);
+        const float2 c12 = cis_reduced(0.5f * (t1 + t2)), c01 = cis_reduced(0.5f * (t0 + t1));
+        const float dr = s12 * c12.x - s01 * c01.x, di = s12 * c12.y - s01 * c01.y;
+        const float inv = 1.f / sp;  // (dr + j di) / (j sp) = (di - j dr) / sp
+        return make_float2(di * inv, -dr * inv);
+    }
+    const float tb = (t0 + t1 + t2) * (1.f / 3.f);
+    const float u0 = t0 - tb, u1 = t1 - tb, u2 = t2 - tb;
+    // h_k(u0) = u0^k, h_k(u0,u1) = h_k(u0) + u1 h_{k-1}(u0,u1), h_k(u0,u1,u2) = h_k(u0,u1) + u2 h_{k-1}(...)
+    float a = 1.f, b = 1.f, c = 1.f;
+    float re = 0.5f, im = 0.f;  // k = 0: 1 / 2!
+    const float inv_fact[8] = {1.f / 2.f, 1.f / 6.f, 1.f / 24.f, 1.f / 120.f, 1.f / 720.f, 1.f / 5040.f,
+                               1.f / 40320.f, 1.f / 362880.f};
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+        a *= u0;
+        b = fmaf(u1, b, a);
+        c = fmaf(u2, c, b);
+        const float t = c * inv_fact[k];
+        switch (k & 3) {  // j^k
+            case 0: re += t; break;
+            case 1: im += t; break;
+            case 2: re -= t; break;
+            default: im -= t; break;
+        }
+    }
+    const float2 e = cis_reduced(tb);
+    return make_float2(re * e.x - im * e.y, re * e.y + im * e.x);
+}
+
+struct TriConst {  // per (triangle, tile), FP32 except the anchor
+    float nu0x, nu0y, mxx, mxy, mxz, myx, myy, myz;  // nu = nu0 + M (dx, dy, dz)
+    float g0, r3x, r3y, r3z;                         // r3 . f = g0 + r3 . delta
+    float th0, tx, ty, tz;                           // phase = th0 + (tx dx + ty dy + tz dz)
+    float w;
+};
+
+__global__ void __launch_bounds__(TNT, 2) k_splat_tri(const TriRec *__restrict__ rec, const float *__restrict__ wgt,
+                                                      long long n, int L, int H, int W, double dfx, double dfy,
+                                                      InvLam il, int field_mode, int phase_match,
+                                                      float2 *__restrict__ out) {
+    __shared__ TriConst S[TNT];
+    const int tiles_x = (W + TTW - 1) / TTW;
+    const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x, l = blockIdx.y;
+    const int c_lo = tx * TTW, r_lo = ty * TTH;
+    const int c_hi = min(c_lo + TTW, W) - 1, r_hi = min(r_lo + TTH, H) - 1;
+    const double inv_lam = il.v[l], k2 = inv_lam * inv_lam;
+    int c_ref, r_ref;
+    tile_ref(c_lo, c_hi, r_lo, r_hi, H, W, dfx, dfy, k2, c_ref, r_ref);
+    const double f0x = (double)(c_ref - W / 2) * dfx, f0y = (double)(r_ref - H / 2) * dfy;
+    const double f0z = sqrt(fmax(k2 - (f0x * f0x + f0y * f0y), 0.0));
+    const int tid = threadIdx.x;
+    const int row = r_lo + tid / 16;
+    float dx[2], dz[2], ifz[2], acc_re[2] = {0.f, 0.f}, acc_im[2] = {0.f, 0.f};
+    float sum_re[2] = {0.f, 0.f}, sum_im[2] = {0.f, 0.f}, cmp_re[2] = {0.f, 0.f}, cmp_im[2] = {0.f, 0.f};
+    bool ok[2];
+    const double fy = (double)(row - H / 2) * dfy;
+    const float dy = (float)((double)(row - r_ref) * dfy);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int col = c_lo + (tid % 16) + 16 * h;
+        const double fx = (double)(col - W / 2) * dfx;
+        const double rho2 = fx * fx + fy * fy;
+        ok[h] = row < H && col < W && rho2 < k2;
+        const double fz = ok[h] ? sqrt(k2 - rho2) : 1.0;
+        dx[h] = (float)((double)(col - c_ref) * dfx);
+        dz[h] = ok[h] ? (float)(fz - f0z) : 0.f;
+        ifz[h] = ok[h] ? (float)(1.0 / fz) : 0.f;
+    }
+    for (long long c0 = 0; c0 < n; c0 += TNT) {
+        const int nc = (int)min((long long)TNT, n - c0);
+        __syncthreads();
+        if (tid < nc) {
+            const TriRec r = rec[c0 + tid];
+            TriConst &T = S[tid];
+            const double d0z = f0z - inv_lam;  // d = f - f_r at the tile reference
+            T.nu0x = (float)(r.M[0] * f0x + r.M[1] * f0y + r.M[2] * d0z);
+            T.nu0y = (float)(r.M[3] * f0x + r.M[4] * f0y + r.M[5] * d0z);
+            T.mxx = r.M[0];
+            T.mxy = r.M[1];
+            T.mxz = r.M[2];
+            T.myx = r.M[3];
+            T.myy = r.M[4];
+            T.myz = r.M[5];
+            T.g0 = (float)(r.r3[0] * f0x + r.r3[1] * f0y + r.r3[2] * f0z);
+            T.r3x = r.r3[0];
+            T.r3y = r.r3[1];
+            T.r3z = r.r3[2];
+            double cyc = -(f0x * r.v1[0] + f0y * r.v1[1] + f0z * r.v1[2]);
+            if (phase_match) cyc += r.v1[2] * inv_lam;
+            cyc -= rint(cyc);
+            T.th0 = (float)(kTwoPi * cyc);
+            T.tx = (float)(-kTwoPi * r.v1[0]);
+            T.ty = (float)(-kTwoPi * r.v1[1]);
+            T.tz = (float)(-kTwoPi * r.v1[2]);
+            T.w = wgt[(c0 + tid) * L + l];
+        }
+        __syncthreads();
+        for (int k = 0; k < nc; ++k) {
+            const TriConst &T = S[k];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float nx = fmaf(T.mxz, dz[h], fmaf(T.mxy, dy, fmaf(T.mxx, dx[h], T.nu0x)));
+                const float ny = fmaf(T.myz, dz[h], fmaf(T.myy, dy, fmaf(T.myx, dx[h], T.nu0y)));
+                // vertex phases of e^{-j 2 pi nu . x} at (0,0), (1,0), (1,1): 0, -a, -(a + b)
+                const float a = 6.28318530717958647692f * nx, ab = 6.28318530717958647692f * (nx + ny);
+                const float p1 = -a, p2 = -ab;
+                const float t0 = fminf(0.f, fminf(p1, p2)), t2 = fmaxf(0.f, fmaxf(p1, p2));
+                const float t1 = 0.f + p1 + p2 - t0 - t2;
+                const float2 tc = tri_canonical(t0, t1, t2);
+                const float jac = fabsf(fmaf(T.r3z, dz[h], fmaf(T.r3y, dy, fmaf(T.r3x, dx[h], T.g0)))) * ifz[h];
+                const float2 e = cis_reduced(fmaf(T.tz, dz[h], fmaf(T.ty, dy, fmaf(T.tx, dx[h], T.th0))));
+                const float s = T.w * jac;
+                acc_re[h] = fmaf(s, tc.x * e.x - tc.y * e.y, acc_re[h]);
+                acc_im[h] = fmaf(s, tc.x * e.y + tc.y * e.x, acc_im[h]);
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // TwoSum-compensated merge of the chunk
+            float t = sum_re[h] + acc_re[h], bp = t - sum_re[h];
+            cmp_re[h] += (sum_re[h] - (t - bp)) + (acc_re[h] - bp);
+            sum_re[h] = t;
+            t = sum_im[h] + acc_im[h];
+            bp = t - sum_im[h];
+            cmp_im[h] += (sum_im[h] - (t - bp)) + (acc_im[h] - bp);
+            sum_im[h] = t;
+            acc_re[h] = acc_im[h] = 0.f;
+        }
+    }
+    if (row >= H) return;
+    const long long hw = (long long)H * W;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int col = c_lo + (tid % 16) + 16 * h;
+        if (col >= W) continue;
+        float re = ok[h] ? sum_re[h] + cmp_re[h] : 0.f, im = ok[h] ? sum_im[h] + cmp_im[h] : 0.f;
+        if (field_mode) {  // centred-DFT pre-modulation e^{-j 2 pi (m r0 / H + n c0 / W)}
+            long long num = mod_num2(row, H / 2, 1, col, W / 2, 1, H, W);
+            if (2 * num > hw) num -= hw;
+            float sn, cs;
+            sincospif(-2.0f * (float)num / (float)hw, &sn, &cs);
+            const float r2 = re * cs - im * sn;
+            im = re * sn + im * cs;
+            re = r2;
+        }
+        out[(size_t)l * hw + (size_t)row * W + col] = make_float2(re, im);
+    }
+}
+
+cudaError_t launch_tri_prep(const double *v, const float *opacity, const float *amp, long long n, int L, TriRec *rec,
+                            float *w, int *status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_tri_prep<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(v, opacity, amp, n, L, rec, w, status);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_splat_tri(const TriRec *rec, const float *w, long long n, int L, int H, int W, double dfx,
+                             double dfy, const InvLam &il, int field_mode, int phase_match, float2 *out,
+                             cudaStream_t s) {
+    const int tiles = ((W + TTW - 1) / TTW) * ((H + TTH - 1) / TTH);
+    k_splat_tri<<<dim3(tiles, L), TNT, 0, s>>>(rec, w, n, L, H, W, dfx, dfy, il, field_mode, phase_match, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace gws

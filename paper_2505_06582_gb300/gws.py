@@ -61,6 +61,10 @@ class _GaussiansOut(C.Structure):
                 ("amp", C.c_void_p)]
 
 
+class _Triangles(C.Structure):
+    _fields_ = [("vertices", C.c_void_p), ("opacity", C.c_void_p), ("amp", C.c_void_p)]
+
+
 class _WorldGaussians(C.Structure):
     _fields_ = [("mean", C.c_void_p), ("quat", C.c_void_p), ("scale", C.c_void_p), ("sh_opacity", C.c_void_p),
                 ("opacity", C.c_void_p), ("sh_degree", C.c_int), ("sh_stride", C.c_int)]
@@ -77,7 +81,8 @@ _lib_lock = threading.Lock()
 EXPORTS = ["gws_opts_default", "gws_status_string", "gws_version", "gws_workspace_size", "gws_prepare",
            "gws_forward", "gws_forward_batched", "gws_backward", "gws_encode", "gws_get_device_status",
            "gws_depth_order", "gws_transmittance", "gws_footprints", "gws_last_launch_count", "gws_autotune",
-           "gws_kernel_time_ms", "gws_footprint_pairs", "gws_encode_noalloc", "gws_holographics"]
+           "gws_kernel_time_ms", "gws_footprint_pairs", "gws_encode_noalloc", "gws_holographics",
+           "gws_triangles_workspace_size", "gws_forward_triangles"]
 
 
 def lib_path() -> str:
@@ -386,6 +391,34 @@ def autotune(g: Gaussians, slm: Slm, workspace=None, **kw) -> int:
     _check(lib.gws_autotune(C.byref(g._c()), C.c_int64(g.n), C.byref(slm._c()), C.byref(opts),
                             C.c_void_p(scratch.data_ptr()), C.byref(best)), "gws_autotune")
     return int(best.value)
+
+
+def forward_triangles(vertices: torch.Tensor, opacity: torch.Tensor, amp: torch.Tensor, slm: Slm,
+                      out: torch.Tensor | None = None, workspace=None, **kw) -> torch.Tensor:
+    """Field (or spectrum) of triangles (gws_forward_triangles): vertices float64 [n,3,3] (rows
+    v1, v2, v3), opacity float32 [n], amp float32 [n,L], all contiguous CUDA tensors."""
+    lib = load()
+    n = int(vertices.shape[0])
+    for name, t, dt, shape in (("vertices", vertices, torch.float64, (n, 3, 3)), ("opacity", opacity, torch.float32, (n,)),
+                               ("amp", amp, torch.float32, (n, slm.n_lambda))):
+        if t.dtype != dt or tuple(t.shape) != shape or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError(f"{name}: expected contiguous CUDA {dt} {shape}, got {t.dtype} {tuple(t.shape)}")
+    dev = vertices.device
+    if out is None:
+        out = torch.empty((slm.n_lambda, slm.H, slm.W), dtype=torch.complex64, device=dev)
+    opts = make_opts(**kw)
+    nbytes = C.c_size_t(0)
+    sc = slm._c()
+    _check(lib.gws_triangles_workspace_size(C.c_int64(n), C.byref(sc), C.byref(opts), C.byref(nbytes)),
+           "gws_triangles_workspace_size")
+    ws = workspace if workspace is not None else _WS.get(int(nbytes.value), dev)
+    if ws.numel() < nbytes.value:
+        raise GwsError(2, "workspace too small")
+    opts.workspace, opts.workspace_bytes = C.c_void_p(ws.data_ptr()), ws.numel()
+    tri = _Triangles(vertices.data_ptr(), opacity.data_ptr(), amp.data_ptr())
+    _check(lib.gws_forward_triangles(C.byref(tri), C.c_int64(n), C.byref(sc), C.byref(opts),
+                                     C.c_void_p(out.data_ptr())), "gws_forward_triangles")
+    return out
 
 
 @dataclass

@@ -31,7 +31,7 @@ import numpy as np
 
 __all__ = [
     "SLM", "Scene", "uniform_scene", "surface_scene", "config_scene", "batched_sizes",
-    "cotangent", "random_field", "CONFIGS", "WorldScene", "world_scene",
+    "cotangent", "random_field", "CONFIGS", "WorldScene", "world_scene", "triangle_scene",
 ]
 
 
@@ -285,6 +285,23 @@ def world_scene(seed: int, n: int, slm: SLM, n_surfaces=8, depth=(1.5, 3.0), fov
                      [0.0, 0.0, a, bz]])
     return WorldScene(mean, q, scale, sh.astype(np.float32), amp, view, fx, fy, cx, cy, holo,
                       {"kind": "world", "seed": seed, "surfaces": n_surfaces})
+
+
+def triangle_scene(seed: int, n: int, slm: SLM, size_px=3.0, **surface_kw):
+    """Triangle soup (vertices float64 [n,3,3], opacity float32 [n], amp float32 [n, n_lambda]):
+    one small triangle per point of ``surface_scene`` in its tangent plane, random shape, edges
+    about ``size_px`` pixels."""
+    sc = surface_scene(seed, n, slm, **surface_kw)
+    rng = np.random.default_rng(seed + 7919)
+    q = sc.quat.astype(np.float64)
+    w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    r1 = np.stack([1 - 2 * (y * y + z * z), 2 * (x * y + w * z), 2 * (x * z - w * y)], 1)
+    r2 = np.stack([2 * (x * y - w * z), 1 - 2 * (x * x + z * z), 2 * (y * z + w * x)], 1)
+    ang = rng.uniform(0, 2 * math.pi, (sc.n, 3)) + np.array([0.0, 2.1, 4.2])
+    rad = size_px * slm.pitch_x * rng.uniform(0.5, 1.2, (sc.n, 3))
+    verts = sc.mean[:, None, :] + rad[:, :, None] * (np.cos(ang)[:, :, None] * r1[:, None, :]
+                                                     + np.sin(ang)[:, :, None] * r2[:, None, :])
+    return verts, sc.opacity, sc.amp
 
 
 RGB = (638e-9, 520e-9, 450e-9)

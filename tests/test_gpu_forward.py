@@ -338,3 +338,24 @@ def test_batched_multi_scene_workload():
         assert rel_l2(got, ref) < TOLMX
         single = gws.forward(gs[k], slm, domain=gws.DOMAIN_SPECTRUM)
         assert torch.equal(single, outs[k])
+
+
+def test_isotropic_point_gaussians():
+    # the point-cloud special case (s_u = s_v, no rotation): against the oracle, and unchanged by
+    # any rotation about the SLM normal (an isotropic disk has no in-plane orientation)
+    slm = SLM(64, 80, 8e-6, 8e-6, (638e-9, 450e-9))
+    rng = np.random.default_rng(21)
+    n = 40
+    mean = np.stack([rng.uniform(-2e-4, 2e-4, n), rng.uniform(-2e-4, 2e-4, n), rng.uniform(1e-3, 4e-3, n)], 1)
+    s = rng.uniform(8e-6, 24e-6, n).astype(np.float32)
+    quat = np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1))
+    amp = rng.uniform(0.2, 1.0, (n, 2)).astype(np.float32)
+    opa = rng.uniform(0.2, 1.0, n).astype(np.float32)
+    sc = make_scene(mean, quat, np.stack([s, s], 1), opa, amp)
+    got = gws.forward(dev(sc), gws.Slm.of(slm)).cpu().numpy()
+    want = O.field(sc, slm)
+    assert max(per_lambda_rel(got, want)) < TOLMX
+    ang = rng.uniform(-np.pi, np.pi, n)
+    qz = np.stack([np.cos(ang / 2), 0 * ang, 0 * ang, np.sin(ang / 2)], 1).astype(np.float32)
+    rot = gws.forward(dev(make_scene(mean, qz, np.stack([s, s], 1), opa, amp)), gws.Slm.of(slm)).cpu().numpy()
+    assert max(per_lambda_rel(rot, got)) < 1e-5
