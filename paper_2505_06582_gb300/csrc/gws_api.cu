@@ -661,8 +661,15 @@ static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, in
         CU(radix_sort<unsigned long long>(ik0, ik1, iv0, iv1, n_items, 0, 32 + seg_bits(n_seg), at<unsigned>(o, L.hist),
                                           s));
         CU(cudaMemsetAsync(at<int>(o, L.queue), 0, 16, s));
+        // per-pixel (f_z - f0_z, log2(1/f_z)) of this configuration's tiles, once per call (FP64)
+        InvLam il;
+        std::memset(&il, 0, sizeof il);
+        for (int l = 0; l < nl; ++l) il.v[l] = 1.0 / slm->wavelengths[l];
+        float2 *ftab = at<float2>(o, L.pixtab);
+        CU(launch_pixtab(nl, H, W, dfx, dfy, il, tc.tw, tc.th, ftab, s));
         SplatArgs a;
         std::memset(&a, 0, sizeof a);
+        a.pixtab = ftab;
         a.rec = rec;
         a.items = iv0;
         a.item_count = icount;

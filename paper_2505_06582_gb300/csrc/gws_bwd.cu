@@ -110,8 +110,9 @@ __device__ __forceinline__ float warp_transpose_reduce16(float v[16], int lane) 
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-// per-pixel table in the natural layout for tw x th tiles (the exact blend's accumulation):
-// (f_z - f0_z of the pixel's tile, log2(1 / f_z)); (0, -inf) where evanescent
+// per-pixel table in the natural layout for tw x th tiles (the forward splat's prologue, the
+// exact blend's and partial coherence's accumulation): (f_z - f0_z of the pixel's tile,
+// log2(1 / f_z)); (0, -inf) where evanescent
 __global__ void k_pixtab(int n_lambda, int H, int W, double dfx, double dfy, InvLam inv_lam, int tw, int th,
                          float2 *__restrict__ tab) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -58,6 +58,7 @@ struct SplatArgs {
     int phase_match;
     unsigned long long timeout;
     unsigned debug;
+    const float2 *pixtab;  // [lambda][H][W]: (f_z - f0_z of the pixel's tile, log2(1/f_z)) for these tiles
     void *out[GWS_MAX_SCENES];
 };
 

@@ -49,7 +49,38 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
     s = t;
 }
 
-template <int TW, int TH, int PX, int CHUNK, int STAGES>
+// One listed record over this thread's PH pixel pairs (packed f32x2): the Gaussian factor and
+// the phase of Eq. 10 from the per-(record, tile) scalars sv[0..3], accumulated into acc.
+template <int PH>
+__device__ __forceinline__ void splat_record(const float4 *__restrict__ sv, float dy, const float2 *dx, const float2 *dz,
+                                             const float2 *lfz, float2 *acc_re, float2 *acc_im) {
+    const float4 Ar = sv[0], Br = sv[1], Gr = sv[2], Mr = sv[3];
+    const float2 ar = pair(fmaf(Ar.y, dy, Ar.w)), br = pair(fmaf(Br.y, dy, Br.w));
+    const float2 gr = pair(fmaf(Gr.y, dy, Gr.w)), tr = pair(fmaf(Mr.y, dy, Mr.w));
+    const float2 ax = pair(Ar.x), az = pair(Ar.z), bx = pair(Br.x), bz = pair(Br.z);
+    const float2 gx = pair(Gr.x), gz = pair(Gr.z), tx2 = pair(Mr.x), tz = pair(Mr.z);
+#pragma unroll
+    for (int h = 0; h < PH; ++h) {
+        const float2 a = __ffma2_rn(az, dz[h], __ffma2_rn(ax, dx[h], ar));
+        const float2 b = __ffma2_rn(bz, dz[h], __ffma2_rn(bx, dx[h], br));
+        const float2 g = __ffma2_rn(gz, dz[h], __ffma2_rn(gx, dx[h], gr));
+        const float2 t = __ffma2_rn(tz, dz[h], __ffma2_rn(tx2, dx[h], tr));
+        // |g| / f_z 2^-(a^2 + b^2) = g (sign(g) 2^-(a^2 + b^2 + log2 f_z))
+        const float2 u = __ffma2_rn(a, a, __ffma2_rn(b, b, lfz[h]));
+        const float2 amp = __fmul2_rn(g, make_float2(with_sign_of(ex2_approx(-u.x), g.x),
+                                                     with_sign_of(ex2_approx(-u.y), g.y)));
+        // t (radians) minus 2 pi round(t / 2 pi), rounding on the FP32 pipe (+-1.5 * 2^23)
+        const float2 kr = __fadd2_rn(__ffma2_rn(t, pair(0.15915494309189535f), pair(12582912.0f)),
+                                     pair(-12582912.0f));
+        const float2 ang = __ffma2_rn(kr, pair(-6.28318530717958647692f), t);
+        acc_re[h] = __ffma2_rn(amp, make_float2(cos_approx(ang.x), cos_approx(ang.y)), acc_re[h]);
+        acc_im[h] = __ffma2_rn(amp, make_float2(sin_approx(ang.x), sin_approx(ang.y)), acc_im[h]);
+    }
+}
+
+// RU: listed records evaluated per iteration (2: two independent accumulator sets for more
+// instruction-level parallelism; needs the register room of the 4-pixel configuration)
+template <int TW, int TH, int PX, int CHUNK, int STAGES, int RU>
 __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_constant__ SplatArgs A) {
     constexpr int NT = (TW / PX) * TH;
     constexpr int NW = NT / 32;          // warps = row bands of the tile
@@ -100,25 +131,24 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
         const double f0z = sqrt(fmax(k2 - (f0x * f0x + f0y * f0y), 0.0));
         const float f0xf = (float)f0x, f0yf = (float)f0y, f0zf = (float)f0z, dz0f = (float)(f0z - inv_lam);
 
-        // this thread's pixels: row prow, columns pcol0 .. pcol0 + PX - 1; f_z and f_z - f0_z in FP64
+        // this thread's pixels: row prow, columns pcol0 .. pcol0 + PX - 1; (f_z - f0_z, log2(1/f_z))
+        // from the per-call table built in FP64 for these tiles (k_pixtab)
         const int prow = r_lo + tid / (TW / PX);
         const int pcol0 = c_lo + (tid % (TW / PX)) * PX;
         const float dfxf = (float)A.dfx, dfyf = (float)A.dfy;
         const float dy = (float)((double)(prow - r_ref) * A.dfy);
-        const double fyd = (double)(prow - A.H / 2) * A.dfy;
+        const float2 *prow_tab = A.pixtab + ((size_t)l * A.H + (prow < A.H ? prow : 0)) * A.W;
         // pixels p = 2 h + {0, 1} form the f32x2 pair h of the packed arithmetic
         constexpr int PH = PX / 2;
         float2 dx[PH], dz[PH], lfz[PH];
 #pragma unroll
         for (int p = 0; p < PX; ++p) {
             const int col = pcol0 + p;
-            const double fxd = (double)(col - A.W / 2) * A.dfx;
-            const double rho2 = fxd * fxd + fyd * fyd;
-            const bool ok = prow < A.H && col < A.W && rho2 < k2;
-            const double fz = ok ? sqrt(k2 - rho2) : 1.0;
+            const float2 pt = (prow < A.H && col < A.W) ? prow_tab[col] : make_float2(0.f, -INFINITY);
+            const bool ok = pt.y > -INFINITY;  // (0, -inf): evanescent or outside the grid
             const float vx = (float)(col - c_ref) * dfxf;
-            const float vl = ok ? (float)log2(fz) : INFINITY;  // log2 f_z: 2^-(a^2 + b^2 + log2 f_z) = f_z^-1 2^-(a^2 + b^2)
-            const float vz = ok ? (float)(fz - f0z) : 0.f;
+            const float vl = ok ? -pt.y : INFINITY;  // log2 f_z: 2^-(a^2 + b^2 + log2 f_z) = f_z^-1 2^-(a^2 + b^2)
+            const float vz = ok ? pt.x : 0.f;
             if (p & 1) {
                 dx[p / 2].y = vx;
                 lfz[p / 2].y = vl;
@@ -146,10 +176,10 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
             }
         }
 
-        float2 acc_re[PH], acc_im[PH];
+        float2 acc_re[PH], acc_im[PH], acc2_re[PH], acc2_im[PH];
         float sum_re[PX], sum_im[PX], cmp_re[PX], cmp_im[PX];
 #pragma unroll
-        for (int h = 0; h < PH; ++h) acc_re[h] = acc_im[h] = make_float2(0.f, 0.f);
+        for (int h = 0; h < PH; ++h) acc_re[h] = acc_im[h] = acc2_re[h] = acc2_im[h] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int p = 0; p < PX; ++p) sum_re[p] = sum_im[p] = cmp_re[p] = cmp_im[p] = 0.f;
 
@@ -228,30 +258,21 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
             for (int v = 0; v < NW; ++v) {
                 const int cnt = s_cnt[warp][v];
                 const unsigned char *lst = s_list + (warp * NW + v) * 32;
-                for (int i = 0; i < cnt; ++i) {
-                    const int k = lst[i];
-                    const float4 Ar = s_sv[k * 4 + 0], Br = s_sv[k * 4 + 1], Gr = s_sv[k * 4 + 2], Mr = s_sv[k * 4 + 3];
-                    const float2 ar = pair(fmaf(Ar.y, dy, Ar.w)), br = pair(fmaf(Br.y, dy, Br.w));
-                    const float2 gr = pair(fmaf(Gr.y, dy, Gr.w)), tr = pair(fmaf(Mr.y, dy, Mr.w));
-                    const float2 ax = pair(Ar.x), az = pair(Ar.z), bx = pair(Br.x), bz = pair(Br.z);
-                    const float2 gx = pair(Gr.x), gz = pair(Gr.z), tx2 = pair(Mr.x), tz = pair(Mr.z);
-#pragma unroll
-                    for (int h = 0; h < PH; ++h) {
-                        const float2 a = __ffma2_rn(az, dz[h], __ffma2_rn(ax, dx[h], ar));
-                        const float2 b = __ffma2_rn(bz, dz[h], __ffma2_rn(bx, dx[h], br));
-                        const float2 g = __ffma2_rn(gz, dz[h], __ffma2_rn(gx, dx[h], gr));
-                        const float2 t = __ffma2_rn(tz, dz[h], __ffma2_rn(tx2, dx[h], tr));
-                        // |g| / f_z 2^-(a^2 + b^2) = g (sign(g) 2^-(a^2 + b^2 + log2 f_z))
-                        const float2 u = __ffma2_rn(a, a, __ffma2_rn(b, b, lfz[h]));
-                        const float2 amp = __fmul2_rn(g, make_float2(with_sign_of(ex2_approx(-u.x), g.x),
-                                                                     with_sign_of(ex2_approx(-u.y), g.y)));
-                        // t (radians) minus 2 pi round(t / 2 pi), rounding on the FP32 pipe (+-1.5 * 2^23)
-                        const float2 kr = __fadd2_rn(__ffma2_rn(t, pair(0.15915494309189535f), pair(12582912.0f)),
-                                                     pair(-12582912.0f));
-                        const float2 ang = __ffma2_rn(kr, pair(-6.28318530717958647692f), t);
-                        acc_re[h] = __ffma2_rn(amp, make_float2(cos_approx(ang.x), cos_approx(ang.y)), acc_re[h]);
-                        acc_im[h] = __ffma2_rn(amp, make_float2(sin_approx(ang.x), sin_approx(ang.y)), acc_im[h]);
+                int i = 0;
+                if (RU == 2) {
+                    for (; i + 1 < cnt; i += 2) {
+                        splat_record<PH>(s_sv + lst[i] * 4, dy, dx, dz, lfz, acc_re, acc_im);
+                        splat_record<PH>(s_sv + lst[i + 1] * 4, dy, dx, dz, lfz, acc2_re, acc2_im);
                     }
+                }
+                for (; i < cnt; ++i) splat_record<PH>(s_sv + lst[i] * 4, dy, dx, dz, lfz, acc_re, acc_im);
+            }
+            if (RU == 2) {
+#pragma unroll
+                for (int h = 0; h < PH; ++h) {
+                    acc_re[h] = __fadd2_rn(acc_re[h], acc2_re[h]);
+                    acc_im[h] = __fadd2_rn(acc_im[h], acc2_im[h]);
+                    acc2_re[h] = acc2_im[h] = make_float2(0.f, 0.f);
                 }
             }
 #pragma unroll
@@ -305,7 +326,7 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
 
 // ---- tile configurations (autotuned) ----------------------------------------------------
 
-template <int TW, int TH, int PX>
+template <int TW, int TH, int PX, int RU = 1>
 struct SplatCfg {
     static constexpr int NT = (TW / PX) * TH;
     static constexpr int CHUNK = NT, STAGES = 3;
@@ -318,15 +339,15 @@ struct SplatCfg {
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-        e = cudaFuncSetAttribute(k_splat_mixed<TW, TH, PX, CHUNK, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        e = cudaFuncSetAttribute(k_splat_mixed<TW, TH, PX, CHUNK, STAGES, RU>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
         return e;
     }
     static cudaError_t launch(const SplatArgs &a, int grid, cudaStream_t s) {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
-        k_splat_mixed<TW, TH, PX, CHUNK, STAGES><<<grid, NT, smem, s>>>(a);
+        k_splat_mixed<TW, TH, PX, CHUNK, STAGES, RU><<<grid, NT, smem, s>>>(a);
         count_launches(1);
         return cudaGetLastError();
     }
@@ -336,10 +357,12 @@ cudaError_t prepare_splat_kernels() {
     cudaError_t e = SplatCfg<64, 32, 8>::prepare();
     if (e == cudaSuccess) e = SplatCfg<32, 32, 4>::prepare();
     if (e == cudaSuccess) e = SplatCfg<128, 16, 8>::prepare();
+    if (e == cudaSuccess) e = SplatCfg<32, 32, 4, 2>::prepare();
     return e;
 }
 
-static const TileCfg kCfgs[] = {{1, 64, 32}, {2, 32, 32}, {3, 128, 16}};
+// id, tile width, tile height (4: the 32x32 tile with two records per iteration)
+static const TileCfg kCfgs[] = {{1, 64, 32}, {2, 32, 32}, {3, 128, 16}, {4, 32, 32}};
 
 int n_tile_cfgs() { return (int)(sizeof(kCfgs) / sizeof(kCfgs[0])); }
 TileCfg tile_cfg(int id) {
@@ -355,6 +378,7 @@ cudaError_t launch_splat_mixed(int cfg, const SplatArgs &a, int grid, cudaStream
     switch (cfg) {
         case 2: return SplatCfg<32, 32, 4>::launch(a, grid, s);
         case 3: return SplatCfg<128, 16, 8>::launch(a, grid, s);
+        case 4: return SplatCfg<32, 32, 4, 2>::launch(a, grid, s);
         default: return SplatCfg<64, 32, 8>::launch(a, grid, s);
     }
 }

@@ -1,7 +1,9 @@
 // probe_rates.cu -- unit-rate microbenchmarks for the roofline denominators: FP32 FMA (scalar and packed
-// f32x2, with and without a negated addend), MUFU ex2 / sin, FP64 DFMA
+// f32x2, with and without a negated addend), MUFU ex2 / sin, FP64 DFMA; and the absolute error of
+// sin/cos.approx against FP64, with and without the splats' argument reduction
 // (CUDA events; every access in bounds, no waits).  Build: nvcc -O3 -gencode arch=compute_103a,code=sm_103a probe_rates.cu
 #include <cstdio>
+#include <cstring>
 #include <cuda_runtime.h>
 #define CK(x) do{cudaError_t e=(x); if(e!=cudaSuccess){printf("CUDA %s @%d\n",cudaGetErrorString(e),__LINE__); return 1;}}while(0)
 constexpr int ITERS=4096;
@@ -53,6 +55,23 @@ __global__ void k_dfma(double* out, double a, double b){
   for(int i=0;i<ITERS/8;i++){ x0=fma(x0,a,b); x1=fma(x1,a,b); x2=fma(x2,a,b); x3=fma(x3,a,b);}
   out[blockIdx.x*blockDim.x+threadIdx.x]=x0+x1+x2+x3;
 }
+// accuracy of sin/cos.approx against FP64 on [-X, X]: unreduced arguments, and after the FP32
+// reduction t - 2 pi round(t / 2 pi) (+-1.5 2^23 rounding) that the splats use
+__device__ __forceinline__ float cs_(float x){float y; asm("cos.approx.ftz.f32 %0, %1;":"=f"(y):"f"(x)); return y;}
+__device__ __forceinline__ float sn_(float x){float y; asm("sin.approx.ftz.f32 %0, %1;":"=f"(y):"f"(x)); return y;}
+__global__ void k_sin_err(float X, int n, unsigned long long* err_raw, unsigned long long* err_red){
+  int i = blockIdx.x*blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float x = -X + (2.0f*X) * ((float)i + 0.5f) / (float)n;
+  const double xs = (double)x;
+  const double ts = sin(xs), tc = cos(xs);
+  const float kr = __fadd_rn(fmaf(x, 0.15915494309189535f, 12582912.0f), -12582912.0f);
+  const float r = fmaf(kr, -6.28318530717958647692f, x);
+  const double e1 = fmax(fabs((double)sn_(x) - ts), fabs((double)cs_(x) - tc));
+  const double e2 = fmax(fabs((double)sn_(r) - ts), fabs((double)cs_(r) - tc));
+  atomicMax(err_raw, (unsigned long long)__double_as_longlong(e1));  // non-negative doubles order as integers
+  atomicMax(err_red, (unsigned long long)__double_as_longlong(e2));
+}
 int main(){
   cudaDeviceProp p; CK(cudaGetDeviceProperties(&p,0));
   int clk=0, memclk=0; cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, 0); cudaDeviceGetAttribute(&memclk, cudaDevAttrMemoryClockRate, 0);
@@ -77,6 +96,16 @@ int main(){
     double sin_rate=(double)n*ITERS*8/(ms*1e-3); printf("sin.approx /s %.4g per SM per clk %.2f\n", sin_rate, sin_rate/p.multiProcessorCount/(clk*1e3));
     k_dfma<<<blocks,threads>>>(od,0.999,0.001); CK(cudaEventRecord(e0)); k_dfma<<<blocks,threads>>>(od,0.999,0.001); CK(cudaEventRecord(e1)); CK(cudaEventSynchronize(e1)); cudaEventElapsedTime(&ms,e0,e1);
     double d_rate=(double)n*(ITERS/8)*4/(ms*1e-3); printf("fp64 dfma/s %.4g per SM per clk %.3f\n", d_rate, d_rate/p.multiProcessorCount/(clk*1e3));
+  }
+  unsigned long long *eb; CK(cudaMalloc(&eb, 16));
+  const float Xs[] = {3.14159265f, 31.4159265f, 314.159265f, 1000.0f};
+  for (float X : Xs) {
+    CK(cudaMemset(eb, 0, 16));
+    const int n = 1 << 24;
+    k_sin_err<<<n / 256, 256>>>(X, n, eb, eb + 1);
+    unsigned long long h[2]; CK(cudaMemcpy(h, eb, 16, cudaMemcpyDeviceToHost));
+    double e[2]; memcpy(e, h, 16);
+    printf("sin/cos.approx max abs error on [-%g, %g]: unreduced %.3g, reduced %.3g\n", X, X, e[0], e[1]);
   }
   CK(cudaDeviceSynchronize()); printf("ok\n"); return 0;
 }
