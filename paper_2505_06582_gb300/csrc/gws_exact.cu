@@ -111,15 +111,14 @@ __global__ void __launch_bounds__((ETW / EPX) * ETH) k_exact_accum(const float2 
         }
     }
     __syncthreads();
-    const int row = r_lo + threadIdx.x / (ETW / EPX);
-    const int col0 = c_lo + (threadIdx.x % (ETW / EPX)) * EPX;
-    if (row >= H) return;
     const long long hw = (long long)H * W;
-    const float dyf = (float)((double)(row - s_rref) * dfy);
+    // pixel q = threadIdx.x + 256 p of the tile: a warp covers 32 consecutive columns of a row
 #pragma unroll
     for (int p = 0; p < EPX; ++p) {
-        const int col = col0 + p;
-        if (col >= W) break;
+        const int q = threadIdx.x + (ETW / EPX) * ETH * p;
+        const int row = r_lo + q / ETW, col = c_lo + q % ETW;
+        if (row >= H || col >= W) continue;
+        const float dyf = (float)((double)(row - s_rref) * dfy);
         const long long pix = (long long)row * W + col;
         const float2 pt = pixtab[(size_t)l * hw + pix];
         if (!(pt.y > -INFINITY)) continue;  // evanescent: H = 0

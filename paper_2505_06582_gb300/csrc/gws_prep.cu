@@ -577,48 +577,65 @@ struct Cx<double> {
 // without the constant); 2: backward post-modulation (adjoint of the pre-modulation, with
 // the constant and the scale)
 template <typename R>
-__global__ void k_modulate(typename Cx<R>::T *__restrict__ data, int n_slices, int H, int W, double scale, int mode) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void modulate_pixel(typename Cx<R>::T *__restrict__ data, int n_slices, int H, int W,
+                                               double scale, int mode, int r, int c) {
     const long long hw = (long long)H * W;
-    if (idx >= hw * n_slices) return;
-    const long long pix = idx % hw;
-    const int r = (int)(pix / W), c = (int)(pix % W);
     const int h2 = H / 2, w2 = W / 2;
-    // angle = num / (H W) cycles, num an exact integer (see mod_num2)
-    long long num;
-    double sc = 1.0;
-    if (mode == 0) {  // e^{j2pi(m0 r0/H + n0 c0/W)} e^{-j2pi(m0 r/H + n0 c/W)}
-        num = mod_num2(h2, h2, 1, w2, w2, 1, H, W) - mod_num2(h2, r, 1, w2, c, 1, H, W);
-        sc = scale;
-    } else if (mode == 1) {  // e^{+j2pi(m0 r/H + n0 c/W)}
-        num = mod_num2(h2, r, 1, w2, c, 1, H, W);
-    } else if (mode == 2) {  // e^{-j2pi(m0 r0/H + n0 c0/W)} e^{+j2pi(m r0/H + n c0/W)}
-        num = mod_num2(r, h2, 1, c, w2, 1, H, W) - mod_num2(h2, h2, 1, w2, w2, 1, H, W);
-        sc = scale;
-    } else {  // forward pre-modulation e^{-j2pi(m r0/H + n c0/W)} (natural-layout spectrum -> cuFFT input)
-        num = -mod_num2(r, h2, 1, c, w2, 1, H, W);
-    }
-    if (num < 0) num += hw;
-    if (2 * num > hw) num -= hw;  // |angle| <= 1/2 cycle
-    typename Cx<R>::T v = data[idx];
     R sn, cs;
-    if (sizeof(R) == 8) {
-        double s8, c8;
-        sincospi(2.0 * (double)num / (double)hw, &s8, &c8);
-        sn = (R)s8;
-        cs = (R)c8;
+    R sc = (mode == 0 || mode == 2) ? (R)scale : (R)1;
+    if (((H | W) & 1) == 0) {
+        // even H, W: m0 r / H + n0 c / W = (r + c) / 2 cycles, so every factor is (-1)^(r + c), times
+        // (-1)^(H/2 + W/2) for the origin term of modes 0 and 2 -- exact, no trigonometry
+        const int k = r + c + ((mode == 0 || mode == 2) ? h2 + w2 : 0);
+        sn = (R)0;
+        cs = (k & 1) ? (R)-1 : (R)1;
     } else {
-        float s4, c4;
-        sincospif(2.0f * (float)num * (1.0f / (float)hw), &s4, &c4);
-        sn = (R)s4;
-        cs = (R)c4;
+        // angle = num / (H W) cycles, num an exact integer (see mod_num2)
+        long long num;
+        if (mode == 0) {  // e^{j2pi(m0 r0/H + n0 c0/W)} e^{-j2pi(m0 r/H + n0 c/W)}
+            num = mod_num2(h2, h2, 1, w2, w2, 1, H, W) - mod_num2(h2, r, 1, w2, c, 1, H, W);
+        } else if (mode == 1) {  // e^{+j2pi(m0 r/H + n0 c/W)}
+            num = mod_num2(h2, r, 1, w2, c, 1, H, W);
+        } else if (mode == 2) {  // e^{-j2pi(m0 r0/H + n0 c0/W)} e^{+j2pi(m r0/H + n c0/W)}
+            num = mod_num2(r, h2, 1, c, w2, 1, H, W) - mod_num2(h2, h2, 1, w2, w2, 1, H, W);
+        } else {  // forward pre-modulation e^{-j2pi(m r0/H + n c0/W)} (natural-layout spectrum -> cuFFT input)
+            num = -mod_num2(r, h2, 1, c, w2, 1, H, W);
+        }
+        if (num < 0) num += hw;
+        if (2 * num > hw) num -= hw;  // |angle| <= 1/2 cycle
+        if (sizeof(R) == 8) {
+            double s8, c8;
+            sincospi(2.0 * (double)num / (double)hw, &s8, &c8);
+            sn = (R)s8;
+            cs = (R)c8;
+        } else {
+            float s4, c4;
+            sincospif(2.0f * (float)num * (1.0f / (float)hw), &s4, &c4);
+            sn = (R)s4;
+            cs = (R)c4;
+        }
     }
-    const R re = (R)sc * (v.x * cs - v.y * sn);
-    const R im = (R)sc * (v.x * sn + v.y * cs);
-    v.x = re;
-    v.y = im;
-    data[idx] = v;
+    sn *= sc;
+    cs *= sc;
+    typename Cx<R>::T *p = data + (size_t)r * W + c;
+#pragma unroll 4
+    for (int sl = 0; sl < n_slices; ++sl) {
+        typename Cx<R>::T v = p[(size_t)sl * hw];
+        const R re = v.x * cs - v.y * sn;
+        v.y = v.x * sn + v.y * cs;
+        v.x = re;
+        p[(size_t)sl * hw] = v;
+    }
 }
+
+template <typename R>
+__global__ void k_modulate(typename Cx<R>::T *__restrict__ data, int n_slices, int H, int W, double scale, int mode) {
+    // one thread per (row, column): the factor is the same in every slice; rows stride by gridDim.y
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= W) return;
+    for (int r = blockIdx.y; r < H; r += gridDim.y) modulate_pixel<R>(data, n_slices, H, W, scale, mode, r, c);
+}
+
 
 // ---------------------------------------------------------------------------------------
 // double-phase encoding (supplement, phase encoding; the garbled formula read as
@@ -775,10 +792,11 @@ cudaError_t launch_modulate(void *data, int prec64, int n_slices, int H, int W, 
                             cudaStream_t s) {
     const long long n = (long long)n_slices * H * W;
     if (n <= 0) return cudaSuccess;
+    const dim3 grid(nblk(W, 256), (unsigned)std::min(H, 65535));
     if (prec64)
-        k_modulate<double><<<nblk(n, 256), 256, 0, s>>>((double2 *)data, n_slices, H, W, scale, mode);
+        k_modulate<double><<<grid, 256, 0, s>>>((double2 *)data, n_slices, H, W, scale, mode);
     else
-        k_modulate<float><<<nblk(n, 256), 256, 0, s>>>((float2 *)data, n_slices, H, W, scale, mode);
+        k_modulate<float><<<grid, 256, 0, s>>>((float2 *)data, n_slices, H, W, scale, mode);
     count_launches(1);
     return cudaGetLastError();
 }

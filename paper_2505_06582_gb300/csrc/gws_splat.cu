@@ -308,13 +308,20 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
                 if (col < A.W) {
                     float re = sum_re[p] + cmp_re[p], im = sum_im[p] + cmp_im[p];
                     if (A.field_mode) {  // e^{-j2pi(m r0/H + n c0/W)}, the angle an exact integer over H W
-                        long long num = mod_num2(prow, A.H / 2, 1, col, A.W / 2, 1, A.H, A.W);
-                        if (2 * num > hw) num -= hw;
-                        float sn, cs;
-                        sincospif(-2.0f * (float)num * inv_hw, &sn, &cs);
-                        const float r2 = re * cs - im * sn;
-                        im = re * sn + im * cs;
-                        re = r2;
+                        if (((A.H | A.W) & 1) == 0) {  // even grid: (-1)^(r + c) exactly
+                            if ((prow + col) & 1) {
+                                re = -re;
+                                im = -im;
+                            }
+                        } else {
+                            long long num = mod_num2(prow, A.H / 2, 1, col, A.W / 2, 1, A.H, A.W);
+                            if (2 * num > hw) num -= hw;
+                            float sn, cs;
+                            sincospif(-2.0f * (float)num * inv_hw, &sn, &cs);
+                            const float r2 = re * cs - im * sn;
+                            im = re * sn + im * cs;
+                            re = r2;
+                        }
                     }
                     out[col] = make_float2(re, im);
                 }

@@ -227,13 +227,20 @@ __global__ void __launch_bounds__(TNT, 2) k_splat_tri(const TriRec *__restrict__
         if (col >= W) continue;
         float re = ok[h] ? sum_re[h] + cmp_re[h] : 0.f, im = ok[h] ? sum_im[h] + cmp_im[h] : 0.f;
         if (field_mode) {  // centred-DFT pre-modulation e^{-j 2 pi (m r0 / H + n c0 / W)}
-            long long num = mod_num2(row, H / 2, 1, col, W / 2, 1, H, W);
-            if (2 * num > hw) num -= hw;
-            float sn, cs;
-            sincospif(-2.0f * (float)num / (float)hw, &sn, &cs);
-            const float r2 = re * cs - im * sn;
-            im = re * sn + im * cs;
-            re = r2;
+            if (((H | W) & 1) == 0) {  // even grid: (-1)^(r + c) exactly
+                if ((row + col) & 1) {
+                    re = -re;
+                    im = -im;
+                }
+            } else {
+                long long num = mod_num2(row, H / 2, 1, col, W / 2, 1, H, W);
+                if (2 * num > hw) num -= hw;
+                float sn, cs;
+                sincospif(-2.0f * (float)num / (float)hw, &sn, &cs);
+                const float r2 = re * cs - im * sn;
+                im = re * sn + im * cs;
+                re = r2;
+            }
         }
         out[(size_t)l * hw + (size_t)row * W + col] = make_float2(re, im);
     }
