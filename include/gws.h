@@ -267,8 +267,8 @@ GWS_API gws_status gws_footprint_pairs(const gws_gaussians *g, int64_t n, const 
 GWS_API int gws_last_launch_count(void);
 
 /* Autotuner of the MIXED splat: runs each tile configuration (1: 64x32, 2: 32x32, 3: 128x16
- * frequencies per CTA tile; 4: 32x32 evaluating two records per iteration) twice on this scene
- * with field_scratch (complex64
+ * frequencies per CTA tile; 4: 32x32 evaluating two records per iteration; 5: 32x32 at three
+ * CTAs per SM) twice on this scene with field_scratch (complex64
  * [n_lambda][H][W]) as output, times the splat with CUDA events, and keeps the fastest for
  * this (H, W, n_lambda) in an in-process table used whenever opts.tile_cfg == 0.  Returns
  * its id in *best_cfg.  Synchronises the stream; not capturable. */

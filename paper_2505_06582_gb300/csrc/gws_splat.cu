@@ -80,8 +80,8 @@ __device__ __forceinline__ void splat_record(const float4 *__restrict__ sv, floa
 
 // RU: listed records evaluated per iteration (2: two independent accumulator sets for more
 // instruction-level parallelism; needs the register room of the 4-pixel configuration)
-template <int TW, int TH, int PX, int CHUNK, int STAGES, int RU>
-__global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_constant__ SplatArgs A) {
+template <int TW, int TH, int PX, int CHUNK, int STAGES, int RU, int MINB>
+__global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __grid_constant__ SplatArgs A) {
     constexpr int NT = (TW / PX) * TH;
     constexpr int NW = NT / 32;          // warps = row bands of the tile
     constexpr int RPW = 32 / (TW / PX);  // tile rows per warp
@@ -333,10 +333,11 @@ __global__ void __launch_bounds__((TW / PX) * TH, 2) k_splat_mixed(const __grid_
 
 // ---- tile configurations (autotuned) ----------------------------------------------------
 
-template <int TW, int TH, int PX, int RU = 1>
+// MINB: CTAs per SM the launch bounds aim at (3 needs <= 85 registers and the 2-stage ring)
+template <int TW, int TH, int PX, int RU = 1, int STAGES = 3, int MINB = 2>
 struct SplatCfg {
     static constexpr int NT = (TW / PX) * TH;
-    static constexpr int CHUNK = NT, STAGES = 3;
+    static constexpr int CHUNK = NT;
     static constexpr size_t smem = sizeof(Rec) * STAGES * CHUNK + sizeof(float4) * 4 * CHUNK + (size_t)(NT / 32) * NT;
     // the opt-in shared-memory size is a per-device function attribute: set it once per
     // device (gws_prepare or the first call), not while a stream is being captured
@@ -346,7 +347,7 @@ struct SplatCfg {
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-        e = cudaFuncSetAttribute(k_splat_mixed<TW, TH, PX, CHUNK, STAGES, RU>,
+        e = cudaFuncSetAttribute(k_splat_mixed<TW, TH, PX, CHUNK, STAGES, RU, MINB>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
         return e;
@@ -354,7 +355,7 @@ struct SplatCfg {
     static cudaError_t launch(const SplatArgs &a, int grid, cudaStream_t s) {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
-        k_splat_mixed<TW, TH, PX, CHUNK, STAGES, RU><<<grid, NT, smem, s>>>(a);
+        k_splat_mixed<TW, TH, PX, CHUNK, STAGES, RU, MINB><<<grid, NT, smem, s>>>(a);
         count_launches(1);
         return cudaGetLastError();
     }
@@ -365,27 +366,27 @@ cudaError_t prepare_splat_kernels() {
     if (e == cudaSuccess) e = SplatCfg<32, 32, 4>::prepare();
     if (e == cudaSuccess) e = SplatCfg<128, 16, 8>::prepare();
     if (e == cudaSuccess) e = SplatCfg<32, 32, 4, 2>::prepare();
+    if (e == cudaSuccess) e = SplatCfg<32, 32, 4, 1, 2, 3>::prepare();
     return e;
 }
 
-// id, tile width, tile height (4: the 32x32 tile with two records per iteration)
-static const TileCfg kCfgs[] = {{1, 64, 32}, {2, 32, 32}, {3, 128, 16}, {4, 32, 32}};
+// id, tile width, tile height (4: the 32x32 tile with two records per iteration; 5: the 32x32
+// tile at three CTAs per SM with a 2-stage ring)
+static const TileCfg kCfgs[] = {{1, 64, 32}, {2, 32, 32}, {3, 128, 16}, {4, 32, 32}, {5, 32, 32}};
 
 int n_tile_cfgs() { return (int)(sizeof(kCfgs) / sizeof(kCfgs[0])); }
 TileCfg tile_cfg(int id) {
     if (id < 1 || id > n_tile_cfgs()) id = 1;
     return kCfgs[id - 1];
 }
-int splat_mixed_ctas_per_sm(int cfg) {
-    (void)cfg;
-    return 2;
-}
+int splat_mixed_ctas_per_sm(int cfg) { return cfg == 5 ? 3 : 2; }
 
 cudaError_t launch_splat_mixed(int cfg, const SplatArgs &a, int grid, cudaStream_t s) {
     switch (cfg) {
         case 2: return SplatCfg<32, 32, 4>::launch(a, grid, s);
         case 3: return SplatCfg<128, 16, 8>::launch(a, grid, s);
         case 4: return SplatCfg<32, 32, 4, 2>::launch(a, grid, s);
+        case 5: return SplatCfg<32, 32, 4, 1, 2, 3>::launch(a, grid, s);
         default: return SplatCfg<64, 32, 8>::launch(a, grid, s);
     }
 }

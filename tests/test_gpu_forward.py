@@ -60,7 +60,7 @@ def test_forward_field_matches_oracle(name, slm, kind, seed, n, blend):
     assert max(per_lambda_rel(fmx, ref)) < TOLMX
 
 
-@pytest.mark.parametrize("tile_cfg", [1, 2, 3, 4])
+@pytest.mark.parametrize("tile_cfg", [1, 2, 3, 4, 5])
 def test_spectrum_domain_and_every_tile_config(tile_cfg):
     slm = SLM(96, 160, 8e-6, 8e-6, (638e-9, 520e-9, 450e-9))
     sc = surface_scene(7, 120, slm, n_surfaces=3)
@@ -287,7 +287,7 @@ def test_autotune_picks_a_config_and_stays_correct():
     sc = surface_scene(30, 300, slm, n_surfaces=3)
     g = dev(sc)
     best = gws.autotune(g, slm)
-    assert best in (1, 2, 3, 4)
+    assert best in (1, 2, 3, 4, 5)
     u = gws.forward(g, slm, domain=gws.DOMAIN_SPECTRUM).cpu().numpy()  # tile_cfg 0 -> the tuned one
     assert max(per_lambda_rel(u, O.spectrum(sc, slm))) < TOLMX
 
