@@ -110,7 +110,7 @@ struct Layout {
     size_t status, queue, amax, gpre, ampc, dkey0, dkey1, dval0, dval1, skey0, skey1, hist, tsorted, tg, tdata;
     size_t rec64, w64, fkey0, fkey1, fval0, fval1, rec, Rr, ikey0, ikey1, ival0, ival1, icount, invrec, gspec, bacc;
     size_t pixtab, gtiles, dT, tq;
-    size_t ex_U, ex_T, ex_arr, ex_inner, ex_inner_bytes;
+    size_t ex_U, ex_T, ex_arr;
     size_t pc_kappa, pc_ysum;  // partial coherence: the kernel pattern [L][H][W] and sum_f Y^2 [L]
     int ex_B;
     size_t cufft, total;
@@ -209,7 +209,7 @@ static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *sl
         L->gtiles = P.take(bwd_table_bytes(nl, slm->H, slm->W));
         L->dT = P.take(sizeof(double) * n);
     }
-    L->ex_U = L->ex_T = L->ex_arr = L->ex_inner = L->ex_inner_bytes = 0;
+    L->ex_U = L->ex_T = L->ex_arr = 0;
     L->pc_kappa = L->pc_ysum = 0;
     L->ex_B = 0;
     size_t fft_work = 0;
@@ -225,17 +225,9 @@ static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *sl
         } else {
             L->ex_T = P.take(sizeof(float) * nl * hw);
         }
-        L->ex_arr = P.take((size_t)B * (24 + 16 + 8 + 4 + 4 * nl + 8 + 4 * nl + 4 + 24) + 256 * 9);
-        gws_opts inner = *o;  // the batch's fields: the order-invariant forward of B one-Gaussian scenes
-        inner.blend = GWS_BLEND_OIT;
-        inner.domain = GWS_DOMAIN_FIELD;
-        Layout Li;
-        gws_status st = plan_layout(B, B, slm, &inner, &Li, true);
-        if (st != GWS_OK) return st;
-        L->ex_inner_bytes = Li.total;
-        L->ex_inner = P.take(Li.total);
-        Plan p;  // the exact path always transforms (forward DFT of each batch of masked fields, final inverse)
-        st = get_plan(slm->H, slm->W, nl, 0, &p);
+        L->ex_arr = P.take((size_t)B * (24 + 16 + 8 + 4 + 4 * nl + 8 + 4 * nl + 4 + 24 + 36) + 256 * 10);
+        Plan p;  // the batch path always transforms (each batch's fields both ways, the final inverse)
+        gws_status st = get_plan(slm->H, slm->W, nl, 0, &p);
         if (st != GWS_OK) return st;
         fft_work = std::max(fft_work, p.work);
         st = get_plan(slm->H, slm->W, B * nl, 0, &p);
@@ -425,9 +417,21 @@ static int num_sms() {
 static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, int n_scenes, const gws_slm *slm,
                                const gws_opts *o, void *const *out);
 
+// One FFT over nb slices of L [H][W] planes: the cached batched plan when the batch is full,
+// else slice by slice.
+static gws_status batch_fft(const Plan &p, int H, int W, int nl, int nb, int B, float2 *U, void *work, int dir,
+                            cudaStream_t s) {
+    Plan pb;
+    if (nb == B && cached_plan(H, W, B * nl, 0, &pb)) return exec_fft(pb, U, work, 0, dir, s);
+    const long long hw = (long long)H * W;
+    for (int k = 0; k < nb; ++k) GS(exec_fft(p, U + (size_t)k * nl * hw, work, 0, dir, s));
+    return GWS_OK;
+}
+
 // Exact alpha wave blending (Algorithm S2), front to back in batches of B Gaussians; see
-// gws_exact.cu.  The batch's fields at their own planes come from the batched forward (one
-// single-Gaussian scene each, depth component of the mean zeroed, c = o = 1).
+// gws_exact.cu.  The batch's fields at their own planes: each Gaussian's dense spectrum (Eq. 10
+// with the depth component of the mean zeroed, c = o = 1; k_single_spectra) and one batched
+// inverse FFT.
 static gws_status exact_forward(const gws_gaussians *scene, long long n, const gws_slm *slm, const gws_opts *o,
                                 const Layout &L, const Front &F, void *out, cudaStream_t s) {
     const int nl = slm->n_lambda, H = slm->H, W = slm->W;
@@ -447,6 +451,7 @@ static gws_status exact_forward(const gws_gaussians *scene, long long n, const g
     E.amp = E.opacity + B;
     E.co = E.amp + (size_t)B * nl;
     E.ok = E.co + (size_t)B * nl;
+    E.rr = E.ok + B;
     E.mu = nullptr;
     InvLam il;
     std::memset(&il, 0, sizeof il);
@@ -455,42 +460,26 @@ static gws_status exact_forward(const gws_gaussians *scene, long long n, const g
     CU(launch_pixtab(nl, H, W, dfx, dfy, il, 64, 32, pixtab, s));  // the tiles of k_exact_accum
     CU(cudaMemsetAsync(acc, 0, sizeof(float2) * (size_t)nl * hw, s));
     CU(launch_fill(Tm, (long long)nl * hw, 1.f, s));
-    gws_opts inner = *o;
-    inner.blend = GWS_BLEND_OIT;
-    inner.domain = GWS_DOMAIN_FIELD;
-    inner.debug_flags &= ~(unsigned)GWS_DEBUG_TIME_KERNELS;
-    inner.workspace = at<char>(o, L.ex_inner);
-    inner.workspace_bytes = L.ex_inner_bytes;
     Plan p;
     GS(get_plan(H, W, nl, 0, &p));
-    std::vector<gws_gaussians> gb(B);
-    std::vector<int64_t> ones(B, 1);
-    std::vector<void *> outs(B);
-    for (int k = 0; k < B; ++k) {
-        gb[k].mean = E.mean + 3 * k;
-        gb[k].quat = E.quat + 4 * k;
-        gb[k].scale = E.scale + 2 * k;
-        gb[k].opacity = E.opacity + k;
-        gb[k].amp = E.amp + (size_t)k * nl;
-        outs[k] = U + (size_t)k * nl * hw;
-    }
+    // even grids: the centred modulations around the mask cancel to constants (see k_exact_mask)
+    const bool even = ((H | W) & 1) == 0;
+    const float sgn0 = ((H / 2 + W / 2) & 1) ? -1.f : 1.f;
+    const float uscale = even ? (float)(dfx * dfy) * sgn0 : 1.f;
+    const float vscale = even ? (float)(slm->pitch_x * slm->pitch_y) * sgn0 : 1.f;
     timer_mark(o, GWS_TIMER_SPLAT_FWD, 0, s);  // the whole front-to-back loop
     for (long long b0 = 0; b0 < n; b0 += B) {
         const int nb = (int)std::min<long long>(B, n - b0);
         CU(launch_exact_gather(F.sorted, b0, nb, scene, nl, E, 0, s));
-        GS(forward_impl(gb.data(), ones.data(), nb, slm, &inner, outs.data()));
-        CU(launch_exact_mask(U, Tm, E, nb, nl, hw, o->alpha_min, o->t_binarize, s));
+        CU(launch_single_spectra(E, nb, nl, H, W, dfx, dfy, il, pixtab, U, s));
+        GS(batch_fft(p, H, W, nl, nb, B, U, at<char>(o, L.cufft), CUFFT_INVERSE, s));
+        if (!even) CU(launch_modulate(U, 0, nb * nl, H, W, dfx * dfy, 0, s));
+        CU(launch_exact_mask(U, Tm, E, nb, nl, hw, o->alpha_min, o->t_binarize, uscale, s));
         // centred forward DFT scaled by px py: the spectrum of each masked field
-        CU(launch_modulate(U, 0, nb * nl, H, W, 1.0, 1, s));
-        Plan pb;
-        if (nb == B && cached_plan(H, W, B * nl, 0, &pb)) {
-            GS(exec_fft(pb, U, at<char>(o, L.cufft), 0, CUFFT_FORWARD, s));
-        } else {
-            for (int k = 0; k < nb; ++k)
-                GS(exec_fft(p, U + (size_t)k * nl * hw, at<char>(o, L.cufft), 0, CUFFT_FORWARD, s));
-        }
-        CU(launch_modulate(U, 0, nb * nl, H, W, slm->pitch_x * slm->pitch_y, 2, s));
-        CU(launch_exact_accum(U, acc, pixtab, E, nb, nl, H, W, dfx, dfy, il, s));
+        if (!even) CU(launch_modulate(U, 0, nb * nl, H, W, 1.0, 1, s));
+        GS(batch_fft(p, H, W, nl, nb, B, U, at<char>(o, L.cufft), CUFFT_FORWARD, s));
+        if (!even) CU(launch_modulate(U, 0, nb * nl, H, W, slm->pitch_x * slm->pitch_y, 2, s));
+        CU(launch_exact_accum(U, acc, pixtab, E, nb, nl, H, W, dfx, dfy, il, even ? 1 : 0, vscale, s));
     }
     timer_mark(o, GWS_TIMER_SPLAT_FWD, 1, s);
     timer_mark(o, GWS_TIMER_FFT, 0, s);
@@ -505,8 +494,8 @@ static gws_status exact_forward(const gws_gaussians *scene, long long n, const g
 }
 
 // One frame of partially coherent GWS (Eq. 14 summed as Eq. 12): batches of B Gaussians; each
-// batch's fields at the origin on their own planes (the order-invariant forward of B one-Gaussian
-// scenes), times c o kappa, back to the spectrum by a centred forward DFT (scale px py), and
+// batch's fields at the origin on their own planes (dense one-Gaussian spectra and a batched
+// inverse FFT), times c o kappa, back to the spectrum by a centred forward DFT (scale px py), and
 // accumulated with the ramps e^{-j 2 pi f . mu}; a final centred inverse DFT gives the field.
 static gws_status pc_forward(const gws_gaussians *scene, long long n, const gws_slm *slm, const gws_opts *o,
                              const Layout &L, const Front &F, void *out, cudaStream_t s) {
@@ -529,6 +518,7 @@ static gws_status pc_forward(const gws_gaussians *scene, long long n, const gws_
     E.amp = E.opacity + B;
     E.co = E.amp + (size_t)B * nl;
     E.ok = E.co + (size_t)B * nl;
+    E.rr = E.ok + B;
     InvLam il;
     std::memset(&il, 0, sizeof il);
     for (int l = 0; l < nl; ++l) il.v[l] = 1.0 / slm->wavelengths[l];
@@ -545,39 +535,22 @@ static gws_status pc_forward(const gws_gaussians *scene, long long n, const gws_
     float2 *pixtab = at<float2>(o, L.pixtab);
     CU(launch_pixtab(nl, H, W, dfx, dfy, il, 64, 32, pixtab, s));  // the tiles of the accumulation
     CU(cudaMemsetAsync(acc, 0, sizeof(float2) * (size_t)nl * hw, s));
-    gws_opts inner = *o;
-    inner.blend = GWS_BLEND_OIT;
-    inner.domain = GWS_DOMAIN_FIELD;
-    inner.phase_match = 0;  // applied with the ramps
-    inner.debug_flags &= ~(unsigned)GWS_DEBUG_TIME_KERNELS;
-    inner.workspace = at<char>(o, L.ex_inner);
-    inner.workspace_bytes = L.ex_inner_bytes;
-    std::vector<gws_gaussians> gb(B);
-    std::vector<int64_t> ones(B, 1);
-    std::vector<void *> outs(B);
-    for (int k = 0; k < B; ++k) {
-        gb[k].mean = E.mean + 3 * k;
-        gb[k].quat = E.quat + 4 * k;
-        gb[k].scale = E.scale + 2 * k;
-        gb[k].opacity = E.opacity + k;
-        gb[k].amp = E.amp + (size_t)k * nl;
-        outs[k] = U + (size_t)k * nl * hw;
-    }
+    const bool even = ((H | W) & 1) == 0;
+    const float sgn0 = ((H / 2 + W / 2) & 1) ? -1.f : 1.f;
+    const float uscale = even ? (float)(dfx * dfy) * sgn0 : 1.f;
+    const float vscale = even ? (float)(slm->pitch_x * slm->pitch_y) * sgn0 : 1.f;
     for (long long b0 = 0; b0 < n; b0 += B) {
         const int nb = (int)std::min<long long>(B, n - b0);
         CU(launch_exact_gather(F.sorted, b0, nb, scene, nl, E, 1, s));
-        GS(forward_impl(gb.data(), ones.data(), nb, slm, &inner, outs.data()));
-        CU(launch_pc_apply(U, kappa, ysum, E, nb, nl, hw, s));
-        CU(launch_modulate(U, 0, nb * nl, H, W, 1.0, 1, s));
-        Plan pb;
-        if (nb == B && cached_plan(H, W, B * nl, 0, &pb)) {
-            GS(exec_fft(pb, U, at<char>(o, L.cufft), 0, CUFFT_FORWARD, s));
-        } else {
-            for (int k = 0; k < nb; ++k)
-                GS(exec_fft(p, U + (size_t)k * nl * hw, at<char>(o, L.cufft), 0, CUFFT_FORWARD, s));
-        }
-        CU(launch_modulate(U, 0, nb * nl, H, W, slm->pitch_x * slm->pitch_y, 2, s));
-        CU(launch_pc_accum(U, acc, pixtab, E, nb, nl, H, W, dfx, dfy, il, o->phase_match ? 1 : 0, s));
+        CU(launch_single_spectra(E, nb, nl, H, W, dfx, dfy, il, pixtab, U, s));
+        GS(batch_fft(p, H, W, nl, nb, B, U, at<char>(o, L.cufft), CUFFT_INVERSE, s));
+        if (!even) CU(launch_modulate(U, 0, nb * nl, H, W, dfx * dfy, 0, s));
+        CU(launch_pc_apply(U, kappa, ysum, E, nb, nl, hw, uscale, s));
+        if (!even) CU(launch_modulate(U, 0, nb * nl, H, W, 1.0, 1, s));
+        GS(batch_fft(p, H, W, nl, nb, B, U, at<char>(o, L.cufft), CUFFT_FORWARD, s));
+        if (!even) CU(launch_modulate(U, 0, nb * nl, H, W, slm->pitch_x * slm->pitch_y, 2, s));
+        CU(launch_pc_accum(U, acc, pixtab, E, nb, nl, H, W, dfx, dfy, il, o->phase_match ? 1 : 0, even ? 1 : 0, vscale,
+                           s));
     }
     timer_mark(o, GWS_TIMER_SPLAT_FWD, 1, s);
     timer_mark(o, GWS_TIMER_FFT, 0, s);

@@ -25,6 +25,20 @@ __global__ void k_exact_gather(const unsigned *__restrict__ sorted, long long b0
     E.mean[3 * k + 2] = 0.0;
     if (pc)
         for (int c = 0; c < 3; ++c) E.mu[3 * k + c] = mean[3 * i + c];
+    {  // the one-Gaussian record of k_single_spectra (c = o = T = 1)
+        double q[4] = {quat[4 * i], quat[4 * i + 1], quat[4 * i + 2], quat[4 * i + 3]};
+        const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        for (int m = 0; m < 4; ++m) q[m] /= qn;
+        double r1[3], r2[3], r3[3];
+        quat_cols<double>(q, r1, r2, r3);
+        const double su = scale[2 * i], sv = scale[2 * i + 1];
+        const double ku = kKappa * su, kv = kKappa * sv, w = kTwoPi * su * sv;
+        for (int m = 0; m < 3; ++m) {
+            E.rr[9 * k + m] = (float)(ku * r1[m]);
+            E.rr[9 * k + 3 + m] = (float)(kv * r2[m]);
+            E.rr[9 * k + 6 + m] = (float)(w * r3[m]);
+        }
+    }
     for (int m = 0; m < 4; ++m) E.quat[4 * k + m] = quat[4 * i + m];
     E.scale[2 * k] = scale[2 * i];
     E.scale[2 * k + 1] = scale[2 * i + 1];
@@ -37,25 +51,111 @@ __global__ void k_exact_gather(const unsigned *__restrict__ sorted, long long b0
     E.ok[k] = opacity[i];
 }
 
+// The batch's fields at their own planes, in spectrum form: Eq. 10 for each one-Gaussian scene
+// (c = o = T = 1, the mean from the gather) at every grid frequency -- no footprint truncation --
+// times the centred-DFT pre-modulation, ready for one batched inverse FFT.  One CTA per (64 x 32
+// tile, batch slot k, wavelength l): FP64 record and phase anchor at the tile's reference
+// frequency, FP32 deltas per pixel (the per-pixel table gives f_z - f0_z and log2(1/f_z)).
+constexpr int SKB = 8;  // one-Gaussian scenes per CTA of k_single_spectra
+
+__global__ void __launch_bounds__(256) k_single_spectra(ExactBatch E, int nb, int L, int H, int W, double dfx,
+                                                        double dfy, InvLam il, const float2 *__restrict__ pixtab,
+                                                        float2 *__restrict__ U) {
+    __shared__ float s_c[SKB][16];  // r1', r2', r3', -2 pi mu, a0, b0, g0, theta0
+    __shared__ double s_f0[3];
+    __shared__ int s_ref[2];
+    const int tiles_x = (W + 63) / 64;
+    const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
+    const int l = blockIdx.y, k0 = blockIdx.z * SKB;
+    const int nk = min(SKB, nb - k0);
+    const int c_lo = tx * 64, r_lo = ty * 32;
+    const double inv_lam = il.v[l];
+    if (threadIdx.x == 0) {
+        const int c_hi = min(c_lo + 64, W) - 1, r_hi = min(r_lo + 32, H) - 1;
+        int c_ref, r_ref;
+        tile_ref(c_lo, c_hi, r_lo, r_hi, H, W, dfx, dfy, inv_lam * inv_lam, c_ref, r_ref);
+        const double f0x = (double)(c_ref - W / 2) * dfx, f0y = (double)(r_ref - H / 2) * dfy;
+        s_f0[0] = f0x;
+        s_f0[1] = f0y;
+        s_f0[2] = sqrt(fmax(inv_lam * inv_lam - (f0x * f0x + f0y * f0y), 0.0));
+        s_ref[0] = c_ref;
+        s_ref[1] = r_ref;
+    }
+    __syncthreads();
+    if (threadIdx.x < nk) {
+        const int k = k0 + threadIdx.x;
+        float *c = s_c[threadIdx.x];
+        for (int m = 0; m < 9; ++m) c[m] = E.rr[9 * k + m];
+        const double mu[3] = {E.mean[3 * k], E.mean[3 * k + 1], E.mean[3 * k + 2]};
+        for (int m = 0; m < 3; ++m) c[9 + m] = (float)(-kTwoPi * mu[m]);
+        const float fx = (float)s_f0[0], fy = (float)s_f0[1], fz = (float)s_f0[2], dz = (float)(s_f0[2] - inv_lam);
+        c[12] = fmaf(c[2], dz, fmaf(c[1], fy, c[0] * fx));  // d = f - f_r at the reference
+        c[13] = fmaf(c[5], dz, fmaf(c[4], fy, c[3] * fx));
+        c[14] = fmaf(c[8], fz, fmaf(c[7], fy, c[6] * fx));
+        double cyc = -(s_f0[0] * mu[0] + s_f0[1] * mu[1] + s_f0[2] * mu[2]);
+        cyc -= rint(cyc);
+        c[15] = (float)(kTwoPi * cyc);
+    }
+    __syncthreads();
+    const long long hw = (long long)H * W;
+    const bool even = ((H | W) & 1) == 0;
+    const float2 *tab = pixtab + (size_t)l * hw;
+    // pixel q = threadIdx.x + 256 p of the tile: a warp covers 32 consecutive columns of a row
+#pragma unroll 2
+    for (int p = 0; p < 8; ++p) {
+        const int qq = threadIdx.x + 256 * p;
+        const int row = r_lo + qq / 64, col = c_lo + qq % 64;
+        if (row >= H || col >= W) continue;
+        const size_t pix = (size_t)row * W + col;
+        const float2 pt = tab[pix];
+        const float dx = (float)((double)(col - s_ref[0]) * dfx), dy = (float)((double)(row - s_ref[1]) * dfy);
+        float cs = 1.f, sn = 0.f;  // the centred-DFT pre-modulation e^{-j2pi(m r0/H + n c0/W)}
+        if (even) {
+            cs = ((row + col) & 1) ? -1.f : 1.f;
+        } else {
+            long long num = mod_num2(row, H / 2, 1, col, W / 2, 1, H, W);
+            if (2 * num > hw) num -= hw;
+            sincospif(-2.0f * (float)num / (float)hw, &sn, &cs);
+        }
+        for (int kk = 0; kk < nk; ++kk) {
+            const float *c = s_c[kk];
+            const float a = fmaf(c[2], pt.x, fmaf(c[1], dy, fmaf(c[0], dx, c[12])));
+            const float b = fmaf(c[5], pt.x, fmaf(c[4], dy, fmaf(c[3], dx, c[13])));
+            const float g = fmaf(c[8], pt.x, fmaf(c[7], dy, fmaf(c[6], dx, c[14])));
+            const float t = fmaf(c[11], pt.x, fmaf(c[10], dy, fmaf(c[9], dx, c[15])));
+            // |g| / f_z 2^-(a^2 + b^2) (pt.y = log2(1/f_z); -inf where evanescent)
+            const float amp = fabsf(g) * ex2_approx(-fmaf(a, a, fmaf(b, b, -pt.y)));
+            const float kr = __fadd_rn(fmaf(t, 0.15915494309189535f, 12582912.0f), -12582912.0f);
+            const float ang = fmaf(kr, -6.28318530717958647692f, t);
+            const float re = amp * cos_approx(ang), im = amp * sin_approx(ang);
+            U[((size_t)(k0 + kk) * L + l) * hw + pix] = make_float2(re * cs - im * sn, re * sn + im * cs);
+        }
+    }
+}
+
 __global__ void k_fill(float *__restrict__ p, long long n, float v) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
 }
 
 // per pixel, in depth order over the batch: v_k = c_k o_k T u_k (in place), then T *= 1 - alpha_k
+// uscale: the true field is uscale U (1 after the post-modulation; on even grids, where the post-
+// and pre-modulations around the mask cancel to a constant, U is the raw inverse FFT and
+// uscale = dfx dfy (-1)^(H/2 + W/2))
 __global__ void k_exact_mask(float2 *__restrict__ U, float *__restrict__ Tm, ExactBatch E, int nb, int L, long long hw,
-                             float t_eps, float t_bin) {
+                             float t_eps, float t_bin, float uscale) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= hw * L) return;
     const int l = (int)(idx / hw);
     const long long pix = idx % hw;
     float T = Tm[idx];
+    const float au = fabsf(uscale);
     for (int k = 0; k < nb; ++k) {
         float2 *up = U + ((size_t)k * L + l) * hw + pix;
         const float2 u = *up;
-        const float s = E.co[k * L + l] * T;
+        const float s = E.co[k * L + l] * T * uscale;
         *up = make_float2(s * u.x, s * u.y);
-        float a = E.ok[k] * sqrtf(u.x * u.x + u.y * u.y);
+        float a = E.ok[k] * au * sqrtf(u.x * u.x + u.y * u.y);
         if (!(a > t_eps)) a = 0.f;
         if (t_bin > 0.f) a = a > t_bin ? 1.f : 0.f;
         T *= 1.f - a;
@@ -68,11 +168,13 @@ constexpr int ETW = 64, ETH = 32, EPX = 8;  // the tiles of the per-pixel table 
 // acc(f) += sum_k V_k(f) exp(-j 2 pi f_z z_k), f_z z_k = f0_z z_k (FP64, per tile) + (f_z - f0_z) z_k (FP32).
 // FULL (partial coherence): the whole ramp exp(-j 2 pi f . mu_k) (x exp(+j 2 pi mu_z / lambda) with
 // phase matching), anchored the same way: f . mu = f0 . mu (FP64) + (f - f0) . mu (FP32).
+// V is the raw forward FFT times vscale, and with fold also times (-1)^(r + c) (the even-grid
+// post-modulation folded in); otherwise the already post-modulated spectrum (vscale = 1).
 template <bool FULL>
 __global__ void __launch_bounds__((ETW / EPX) * ETH) k_exact_accum(const float2 *__restrict__ V, float2 *__restrict__ acc,
                                                                    const float2 *__restrict__ pixtab, ExactBatch E,
                                                                    int nb, int L, int H, int W, double dfx, double dfy,
-                                                                   InvLam il, int phase_match) {
+                                                                   InvLam il, int phase_match, int fold, float vscale) {
     __shared__ float s_th[GWS_MAX_SCENES], s_mz[GWS_MAX_SCENES], s_mx[GWS_MAX_SCENES], s_my[GWS_MAX_SCENES];
     __shared__ double s_f0z, s_f0x, s_f0y;
     __shared__ int s_cref, s_rref;
@@ -123,7 +225,7 @@ __global__ void __launch_bounds__((ETW / EPX) * ETH) k_exact_accum(const float2 
         const float2 pt = pixtab[(size_t)l * hw + pix];
         if (!(pt.y > -INFINITY)) continue;  // evanescent: H = 0
         const float dxf = (float)((double)(col - s_cref) * dfx);
-        float2 a = acc[(size_t)l * hw + pix];
+        float2 a = make_float2(0.f, 0.f);
         for (int k = 0; k < nb; ++k) {
             const float2 v = V[((size_t)k * L + l) * hw + pix];
             const float t = FULL ? fmaf(s_mz[k], pt.x, fmaf(s_my[k], dyf, fmaf(s_mx[k], dxf, s_th[k])))
@@ -135,7 +237,11 @@ __global__ void __launch_bounds__((ETW / EPX) * ETH) k_exact_accum(const float2 
             a.x = fmaf(v.x, cs, fmaf(-v.y, sn, a.x));
             a.y = fmaf(v.x, sn, fmaf(v.y, cs, a.y));
         }
-        acc[(size_t)l * hw + pix] = a;
+        const float sg = (fold && ((row + col) & 1)) ? -vscale : vscale;
+        float2 cur = acc[(size_t)l * hw + pix];
+        cur.x = fmaf(sg, a.x, cur.x);
+        cur.y = fmaf(sg, a.y, cur.y);
+        acc[(size_t)l * hw + pix] = cur;
     }
 }
 
@@ -210,15 +316,19 @@ __global__ void __launch_bounds__(256) k_pc_kernel(float2 *__restrict__ K, doubl
     }
 }
 
+// grid (pixel blocks, k L + l): no index division per value
 __global__ void k_pc_apply(float2 *__restrict__ U, const float2 *__restrict__ kappa, const double *__restrict__ ysum,
-                           ExactBatch E, int nb, int L, long long hw) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= hw * L * nb) return;
-    const int kl = (int)(idx / hw);  // k * L + l
+                           ExactBatch E, int nb, int L, long long hw, float uscale) {
+    __shared__ float s_s;
+    const int kl = blockIdx.y;  // k * L + l
     const int l = kl % L;
-    const long long pix = idx % hw;
-    const float s = E.co[kl] * (float)(1.0 / sqrt(ysum[l]));
+    if (threadIdx.x == 0) s_s = E.co[kl] * uscale * (float)(1.0 / sqrt(ysum[l]));  // FP64 once per block
+    __syncthreads();
+    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= hw) return;
+    const float s = s_s;
     const float2 a = kappa[(size_t)l * hw + pix];
+    const size_t idx = (size_t)kl * hw + pix;
     const float2 u = U[idx];
     U[idx] = make_float2(s * (u.x * a.x - u.y * a.y), s * (u.x * a.y + u.y * a.x));
 }
@@ -240,17 +350,27 @@ cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_single_spectra(const ExactBatch &E, int nb, int L, int H, int W, double dfx, double dfy,
+                                  const InvLam &il, const float2 *pixtab, float2 *U, cudaStream_t s) {
+    const int tiles = ((W + 63) / 64) * ((H + 31) / 32);
+    k_single_spectra<<<dim3(tiles, L, (nb + SKB - 1) / SKB), 256, 0, s>>>(E, nb, L, H, W, dfx, dfy, il, pixtab, U);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_exact_mask(float2 *U, float *T, const ExactBatch &E, int nb, int L, long long hw, float t_eps,
-                              float t_bin, cudaStream_t s) {
-    k_exact_mask<<<nblk(hw * L, 256), 256, 0, s>>>(U, T, E, nb, L, hw, t_eps, t_bin);
+                              float t_bin, float uscale, cudaStream_t s) {
+    k_exact_mask<<<nblk(hw * L, 256), 256, 0, s>>>(U, T, E, nb, L, hw, t_eps, t_bin, uscale);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_exact_accum(const float2 *V, float2 *acc, const float2 *pixtab, const ExactBatch &E, int nb, int L,
-                               int H, int W, double dfx, double dfy, const InvLam &il, cudaStream_t s) {
+                               int H, int W, double dfx, double dfy, const InvLam &il, int fold, float vscale,
+                               cudaStream_t s) {
     const int tiles = ((W + ETW - 1) / ETW) * ((H + ETH - 1) / ETH);
-    k_exact_accum<false><<<dim3(tiles, L), (ETW / EPX) * ETH, 0, s>>>(V, acc, pixtab, E, nb, L, H, W, dfx, dfy, il, 0);
+    k_exact_accum<false><<<dim3(tiles, L), (ETW / EPX) * ETH, 0, s>>>(V, acc, pixtab, E, nb, L, H, W, dfx, dfy, il, 0,
+                                                                      fold, vscale);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -265,17 +385,18 @@ cudaError_t launch_pc_kernel(float2 *K, double *ysum, int sh_l, int sh_m, unsign
 }
 
 cudaError_t launch_pc_apply(float2 *U, const float2 *kappa, const double *ysum, const ExactBatch &E, int nb, int L,
-                            long long hw, cudaStream_t s) {
-    k_pc_apply<<<nblk(hw * L * nb, 256), 256, 0, s>>>(U, kappa, ysum, E, nb, L, hw);
+                            long long hw, float uscale, cudaStream_t s) {
+    k_pc_apply<<<dim3(nblk(hw, 256), nb * L), 256, 0, s>>>(U, kappa, ysum, E, nb, L, hw, uscale);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pc_accum(const float2 *V, float2 *acc, const float2 *pixtab, const ExactBatch &E, int nb, int L,
-                            int H, int W, double dfx, double dfy, const InvLam &il, int phase_match, cudaStream_t s) {
+                            int H, int W, double dfx, double dfy, const InvLam &il, int phase_match, int fold,
+                            float vscale, cudaStream_t s) {
     const int tiles = ((W + ETW - 1) / ETW) * ((H + ETH - 1) / ETH);
     k_exact_accum<true><<<dim3(tiles, L), (ETW / EPX) * ETH, 0, s>>>(V, acc, pixtab, E, nb, L, H, W, dfx, dfy, il,
-                                                                     phase_match);
+                                                                     phase_match, fold, vscale);
     count_launches(1);
     return cudaGetLastError();
 }

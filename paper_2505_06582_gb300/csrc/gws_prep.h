@@ -45,6 +45,7 @@ struct ExactBatch {  // one batch of exact blending (Gaussians in depth order)
     float *co;       // [B][L] c o
     float *ok;       // [B] o
     double *mu;      // [B][3] the means (partial coherence: the inner fields sit at the origin)
+    float *rr;       // [B][9] kappa s_u r1, kappa s_v r2, 2 pi s_u s_v r3 (the one-Gaussian record)
 };
 // pc = 0: exact blending (the means keep x, y; depth zeroed); pc = 1: partial coherence (means zeroed)
 cudaError_t launch_exact_gather(const unsigned *sorted, long long b0, int nb, const gws_gaussians *g, int L,
@@ -56,16 +57,21 @@ cudaError_t launch_pc_kernel(float2 *K, double *ysum, int sh_l, int sh_m, unsign
                              const InvLam &il, cudaStream_t s);
 // w_k = c_k o_k u_k kappa / sqrt(ysum) in place, for the batch's fields U [nb][L][H][W]
 cudaError_t launch_pc_apply(float2 *U, const float2 *kappa, const double *ysum, const ExactBatch &E, int nb, int L,
-                            long long hw, cudaStream_t s);
+                            long long hw, float uscale, cudaStream_t s);
+// the batch's one-Gaussian spectra (Eq. 10, c = o = T = 1, dense) with the centred pre-modulation,
+// U [nb][L][H][W]; pixtab: the natural-layout table for 64 x 32 tiles
+cudaError_t launch_single_spectra(const ExactBatch &E, int nb, int L, int H, int W, double dfx, double dfy,
+                                  const InvLam &il, const float2 *pixtab, float2 *U, cudaStream_t s);
 // acc += sum_k V_k(f) e^{-j 2 pi f . mu_k} (x e^{+j 2 pi mu_z / lambda} with phase matching)
 cudaError_t launch_pc_accum(const float2 *V, float2 *acc, const float2 *pixtab, const ExactBatch &E, int nb, int L,
-                            int H, int W, double dfx, double dfy, const InvLam &il, int phase_match,
-                            cudaStream_t s);
+                            int H, int W, double dfx, double dfy, const InvLam &il, int phase_match, int fold,
+                            float vscale, cudaStream_t s);
 cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s);
 cudaError_t launch_exact_mask(float2 *U, float *T, const ExactBatch &E, int nb, int L, long long hw, float t_eps,
-                              float t_bin, cudaStream_t s);
+                              float t_bin, float uscale, cudaStream_t s);
 cudaError_t launch_exact_accum(const float2 *V, float2 *acc, const float2 *pixtab, const ExactBatch &E, int nb, int L,
-                               int H, int W, double dfx, double dfy, const InvLam &il, cudaStream_t s);
+                               int H, int W, double dfx, double dfy, const InvLam &il, int fold, float vscale,
+                               cudaStream_t s);
 
 cudaError_t launch_encode(const void *field, int prec64, int n_lambda, int H, int W, unsigned long long *amax2,
                           double amp_scale, float *out, cudaStream_t s);
