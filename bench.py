@@ -58,9 +58,12 @@ def parse():
                    help="named workload of paper_2505_06582_gb300.scenes.CONFIGS (default: the headline)")
     p.add_argument("--prec", default="mixed", choices=["mixed", "fp64"],
                    help="fp64: the plain FP64 comparison path (forward + encode only)")
-    p.add_argument("--blend", default="oit", choices=["oit", "sorted", "exact"],
-                   help="oit (Eq. 12, the headline), sorted (depth-sorted T at the centres) or exact (Algorithm S2,"
-                        " forward + encode only)")
+    p.add_argument("--blend", default="oit", choices=["oit", "sorted", "exact", "partial"],
+                   help="oit (Eq. 12, the headline), sorted (depth-sorted T at the centres), exact (Algorithm S2,"
+                        " forward + encode only) or partial (one partially coherent frame, Eq. 14, forward + encode"
+                        " only)")
+    p.add_argument("--pc-l", type=int, default=1, help="partial: degree of the angular kernel's SH")
+    p.add_argument("--pc-m", type=int, default=1, help="partial: order of the angular kernel's SH")
     p.add_argument("--traffic-mb", type=float, default=None,
                    help="DRAM bytes per splat launch from an ncu capture of this workload (MB)")
     p.add_argument("--front-end", action="store_true",
@@ -233,13 +236,15 @@ def run_ours(args):
         g = gws.Gaussians.from_scene(scene, dev)
     fp64 = args.prec == "fp64"
     prec = gws.PREC_FP64 if fp64 else gws.PREC_MIXED
-    blend = {"oit": gws.BLEND_OIT, "sorted": gws.BLEND_SORTED_T, "exact": gws.BLEND_EXACT}[args.blend]
-    have_bwd = not fp64 and args.blend != "exact"
+    blend = {"oit": gws.BLEND_OIT, "sorted": gws.BLEND_SORTED_T, "exact": gws.BLEND_EXACT,
+             "partial": gws.BLEND_PARTIAL_COHERENT}[args.blend]
+    have_bwd = not fp64 and args.blend not in ("exact", "partial")
+    pc_kw = dict(pc_l=args.pc_l, pc_m=args.pc_m, pc_seed=1) if args.blend == "partial" else {}
     cot = torch.as_tensor(cotangent(11, slm), device=dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     gws.prepare(S)
-    ws = torch.empty(gws.workspace_size([g.n], S, gws.make_opts(prec=prec, blend=blend)), dtype=torch.uint8,
+    ws = torch.empty(gws.workspace_size([g.n], S, gws.make_opts(prec=prec, blend=blend, **pc_kw)), dtype=torch.uint8,
                      device=dev)
     # autotune the splat tile on a strided 10% sample of the scene (outside the timed region)
     sub = gws.Gaussians(*(getattr(g, k)[::10].contiguous() for k in ("mean", "quat", "scale", "opacity", "amp")))
@@ -255,6 +260,7 @@ def run_ours(args):
         kw = dict(timers) if timed_kernels else {}
         kw["prec"] = prec
         kw["blend"] = blend
+        kw.update(pc_kw)
         launches = 0
         t_front = None
         if front is not None:
@@ -344,7 +350,7 @@ def run_ours(args):
             gd, _ = gws.holographics(wd, front["cam"], front["holo"], compact=False)
         else:
             gd = gws.Gaussians(dbuf["mean"], dbuf["quat"], dbuf["scale"], dbuf["opacity"], dbuf["amp"])
-        gws.forward(gd, S, out=field, workspace=ws, prec=prec, blend=blend)
+        gws.forward(gd, S, out=field, workspace=ws, prec=prec, blend=blend, **pc_kw)
         gws.encode(field, S, out=phase, workspace=ws)
         phase_host.copy_(phase, non_blocking=True)
         if have_bwd:
@@ -375,10 +381,27 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": None if traffic_mb is None else traffic_mb * 1e6,
                 "peak_basis": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median sampled) x {per_clk:.2f} pairs/clk/SM, " + basis}
 
-    rooflines = {"splat_fwd": roof(
-        "k_splat_fp64" if fp64 else "k_splat_mixed", splat, FWD_PAIRS_PER_CLK,
-        "MUFU bound (ex2 + sin + cos per pair)" + (" (FP32/MUFU peak; the FP64 path runs on the FP64 pipe)" if fp64 else ""),
-        args.traffic_mb if args.traffic_mb is not None else (SPLAT_TRAFFIC_MB if full_size else None))}
+    if args.blend in ("exact", "partial"):
+        # the batch loop (one-Gaussian spectra, batched inverse FFT, mask or kernel product, batched
+        # forward FFT, accumulation) moves each (Gaussian, wavelength, pixel) value 8 times at 8 B:
+        # spectra write, inverse FFT read + write, mask read + write, forward FFT read + write,
+        # accumulation read; cuFFT's internal passes are not counted
+        hbm_pk = 6785.9
+        try:
+            hbm_pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        except (OSError, KeyError, ValueError):
+            pass
+        lb = 64.0 * g.n * S.H * S.W * S.n_lambda
+        ach = lb / (splat * 1e-3) / 1e9
+        rooflines = {"splat_fwd": {"kernel": "batch loop (k_single_spectra, cuFFT, k_exact_mask / k_pc_apply, "
+                                             "k_exact_accum)", "bound": "hbm", "achieved": ach, "peak": hbm_pk,
+                                   "unit": "GB/s", "frac": ach / hbm_pk, "traffic": None,
+                                   "note": "64 algorithmic bytes per (Gaussian, wavelength, pixel)"}}
+    else:
+        rooflines = {"splat_fwd": roof(
+            "k_splat_fp64" if fp64 else "k_splat_mixed", splat, FWD_PAIRS_PER_CLK,
+            "MUFU bound (ex2 + sin + cos per pair)" + (" (FP32/MUFU peak; the FP64 path runs on the FP64 pipe)" if fp64 else ""),
+            args.traffic_mb if args.traffic_mb is not None else (SPLAT_TRAFFIC_MB if full_size else None))}
     if bwd_ms:
         rooflines["splat_bwd"] = roof("k_splat_bwd", dom_ms["splat_bwd"], BWD_PAIRS_PER_CLK,
                                       "FP32 bound (36 lane-ops per pair at 128 lanes/clk/SM; MUFU bound 6.4)",

@@ -29,6 +29,7 @@ CASES = [
     (SLM(40, 56, 1e-6, 1e-6, (520e-9, 450e-9)), 6, 1, -1, 3, 1),
     (SLM(40, 56, 1e-6, 1e-6, (638e-9,)), 6, 2, -2, 4, 7),
     (SLM(33, 45, 1.2e-6, 1e-6, (520e-9,)), 5, 3, 0, 9, 2),
+    (SLM(50, 64, 8e-6, 8e-6, (520e-9,)), 6, 1, 0, 4, 3),  # H/2 + W/2 odd: the folded constant is negative
 ]
 
 

@@ -70,3 +70,14 @@ def test_exact_rejects_unsupported_combinations():
     with pytest.raises(gws.GwsError) as e:
         gws.forward_batched([dev(sc)], slm, blend=gws.BLEND_EXACT)
     assert e.value.code == 6
+
+
+@pytest.mark.parametrize("H,W", [(50, 64), (45, 61)], ids=["even_origin_sign", "odd"])
+def test_exact_grid_parities(H, W):
+    # 50 x 64: H/2 + W/2 odd, so the folded modulation constant is negative; 45 x 61: odd sizes,
+    # where the explicit modulation passes run
+    slm = SLM(H, W, 8e-6, 8e-6, (520e-9,))
+    sc = surface_scene(71, 16, slm, n_surfaces=2, scale_median_px=3.0)
+    ref = O.idft(O.exact_awb(sc, slm), slm.pitch_x, slm.pitch_y)
+    got = gws.forward(dev(sc), slm, blend=gws.BLEND_EXACT, exact_batch=5).cpu().numpy()
+    assert rel_l2(got[0], ref[0]) < TOL
