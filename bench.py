@@ -37,14 +37,14 @@ WORKLOAD = "headline_1m_1080p_3l"
 SPLAT_TRAFFIC_MB = 1609.9  # 1.54 GB read + 69.85 MB written
 BWD_TRAFFIC_MB = 722.7     # 421.5 MB read + 301.2 MB written (wavelength-major work items)
 # Per (Gaussian, frequency) pair: the forward needs ex2, sin and cos on the MUFU (32, 16, 16 per
-# SM per clock): 1 / (1/32 + 2/16) = 6.4 pairs/clk/SM; its 17 FP32 lane-ops (8 affine, 2 exponent,
-# 1 |g| e, 3 phase reduction, 1 sin/cos prescale, 2 accumulations) allow 128 / 17 = 7.5.  The
-# backward adds the gradient products and the 12 moment sums: 36 FP32 lane-ops per pair
-# (8 affine, 2 exponent, 3 phase reduction, 1 prescale, 2 sign(g) e products, 4 complex product,
-# 2 |g| products, 2 a'/b' products, 12 moments) -> 128 / 36 = 3.56 pairs/clk/SM, below its MUFU 6.4.
-# (The sin/cos argument scaling is counted once; counting it twice would lower both peaks.)
+# SM per clock): 1 / (1/32 + 2/16) = 6.4 pairs/clk/SM; its 14 FP32 lane-ops (8 affine, 2 exponent,
+# 1 |g| e, 1 sin/cos prescale, 2 accumulations; the phase is reduced once per (record, thread))
+# allow 128 / 14 = 9.1.  The backward adds the gradient products and the 12 moment sums: 30 FP32
+# lane-ops per pair (8 affine + 1 for arg G, 2 exponent, 1 prescale, 2 e cos / e sin, 2 |g|
+# products, 2 a'/b' products, 12 moments; G enters in polar form, the phase is reduced once per
+# (record, column)) -> 128 / 30 = 4.27 pairs/clk/SM, below its MUFU 6.4.
 FWD_PAIRS_PER_CLK = 6.4
-BWD_PAIRS_PER_CLK = 128.0 / 36.0
+BWD_PAIRS_PER_CLK = 128.0 / 30.0
 
 
 def parse():
@@ -407,7 +407,7 @@ def run_ours(args):
             args.traffic_mb if args.traffic_mb is not None else (SPLAT_TRAFFIC_MB if full_size else None))}
     if bwd_ms:
         rooflines["splat_bwd"] = roof("k_splat_bwd", dom_ms["splat_bwd"], BWD_PAIRS_PER_CLK,
-                                      "FP32 bound (36 lane-ops per pair at 128 lanes/clk/SM; MUFU bound 6.4)",
+                                      "FP32 bound (30 lane-ops per pair at 128 lanes/clk/SM; MUFU bound 6.4)",
                                       BWD_TRAFFIC_MB if full_size else None)
     if front_ms:
         dom_ms["front_end"] = statistics.median(front_ms)

@@ -975,14 +975,15 @@ gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, c
     InvLam il;
     std::memset(&il, 0, sizeof il);
     for (int l = 0; l < nl; ++l) il.v[l] = 1.0 / slm->wavelengths[l];
-    float4 *pixtab = at<float4>(opts, L.pixtab), *gtiles = at<float4>(opts, L.gtiles);
-    CU(launch_bwd_tables(nl, H, W, dfx, dfy, il, gsrc, gtiles, pixtab, s));
+    float4 *btab = at<float4>(opts, L.gtiles);
+    float2 *bps = at<float2>(opts, L.pixtab);
+    CU(launch_bwd_tables(nl, H, W, dfx, dfy, il, gsrc, btab, bps, s));
     CU(cudaMemsetAsync(at<int>(opts, L.queue), 0, 16, s));
     BwdArgs a;
     std::memset(&a, 0, sizeof a);
     a.rec = rec;
-    a.gtiles = gtiles;
-    a.pixtab = pixtab;
+    a.tab = btab;
+    a.ps = bps;
     a.acc = at<double>(opts, L.bacc);
     a.queue = at<int>(opts, L.queue);
     a.status = at<int>(opts, L.status);

@@ -6,11 +6,13 @@
 //
 // The spectra are recomputed, never stored.  A work item is a block of BB consecutive
 // records of one wavelength (footprint order, so a block's footprints are alike).  The CTA
-// walks the 64 x 32 frequency tiles of the block's footprint union; per tile it stages G and
-// a per-pixel table (f_z - f0_z, log2 f_z) in shared memory with cp.async from copies laid
-// out tile by tile (k_gtiles, k_pixtab_tiles: zero / +inf padded past the grid, so a tile is
-// one contiguous 16 KB block per array, and a lane's two columns c and c + 32 of a row sit
-// side by side for the packed f32x2 arithmetic), culls each record exactly, and one warp
+// walks the 64 x 32 frequency tiles of the block's footprint union; per tile it stages two
+// per-pixel tables in shared memory with cp.async from copies laid out tile by tile
+// (k_bwd_tables: (f_z - f0_z, log2 f_z - log2 |G|) and -arg G, padded past the grid so that a
+// tile is one contiguous block per table, and a lane's two columns c and c + 32 of a row sit
+// side by side for the packed f32x2 arithmetic): G enters in polar form, as a factor of the
+// exponential and a shift of the phase, so conj(G) P0 costs no complex product.  It culls
+// each record exactly, and one warp
 // takes one record over the tile (lane = column pair, rows in a loop), accumulating 16 FP32
 // partial sums per column; these are reduced across the warp and merged per tile into 13
 // FP64 totals per record in shared memory:
@@ -39,8 +41,8 @@ struct TileConst {  // geometry of the current tile, computed once by thread 0
 };
 
 struct BwdShared {
-    float4 g[2][BQ];   // [row][lane]: (Re G(c), Re G(c + 32), Im G(c), Im G(c + 32)), c = c_lo + lane
-    float4 px[2][BQ];  // [row][lane]: (dz(c), dz(c + 32), log2 f_z(c), log2 f_z(c + 32))
+    float4 t[2][BQ];   // [row][lane]: (dz(c), dz(c + 32), lw(c), lw(c + 32)), c = c_lo + lane, lw = log2(f_z / |G|)
+    float2 ps[2][BQ];  // [row][lane]: (-arg G(c), -arg G(c + 32))
     Rec rec[BB];
     float4 sv[BB][4];
     int2 rows[BB];  // per surviving record: the tile rows [x, y] its footprint's bounding box reaches
@@ -143,11 +145,14 @@ __global__ void k_pixtab(int n_lambda, int H, int W, double dfx, double dfy, Inv
     tab[idx] = v;
 }
 
-// The backward's tile-major copies, one float4 per (wavelength, tile, row, lane) holding the
-// columns c = c_lo + lane and c + 32 of the row.  Past the grid: G = 0 and log2 f_z = +inf, so
-// padded pixels add nothing.  Evanescent pixels: dz = 0, log2 f_z = +inf (2^-inf = 0).
-__global__ void k_pixtab_tiles(int n_lambda, int H, int W, double dfx, double dfy, InvLam inv_lam, int tiles_x,
-                               int tiles_y, float4 *__restrict__ tab) {
+// The backward's tile-major tables, one entry per (wavelength, tile, row, lane) holding the
+// columns c = c_lo + lane and c + 32 of the row: t = (dz(c), dz(c + 32), lw(c), lw(c + 32)) with
+// dz = f_z - f0_z (FP64, rounded) and lw = log2 f_z - log2 |G(f)|, and ps = -arg G, so that
+//   conj(G) f_z^-1 2^-(a'^2 + b'^2) e^{j phi} = 2^-(a'^2 + b'^2 + lw) e^{j (phi + ps)}.
+// Past the grid, where f is evanescent and where G = 0: dz = 0, lw = +inf (2^-inf = 0), ps = 0.
+__global__ void k_bwd_tables(const float2 *__restrict__ G, int n_lambda, int H, int W, double dfx, double dfy,
+                             InvLam inv_lam, int tiles_x, int tiles_y, float4 *__restrict__ tab,
+                             float2 *__restrict__ ps) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long per_l = (long long)tiles_x * tiles_y * BQ;
     if (idx >= per_l * n_lambda) return;
@@ -163,38 +168,24 @@ __global__ void k_pixtab_tiles(int n_lambda, int H, int W, double dfx, double df
     tile_ref(c_lo, c_hi, r_lo, r_hi, H, W, dfx, dfy, k2, c_ref, r_ref);
     const double f0x = (double)(c_ref - W / 2) * dfx, f0y = (double)(r_ref - H / 2) * dfy;
     const double f0z = sqrt(fmax(k2 - (f0x * f0x + f0y * f0y), 0.0));
-    float dz[2] = {0.f, 0.f}, lf[2] = {INFINITY, INFINITY};
+    float dz[2] = {0.f, 0.f}, lw[2] = {INFINITY, INFINITY}, ph[2] = {0.f, 0.f};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int c = c0 + 32 * h;
         if (r >= H || c >= W) continue;
         const double fx = (double)(c - W / 2) * dfx, fy = (double)(r - H / 2) * dfy;
         const double rho2 = fx * fx + fy * fy;
-        if (rho2 < k2) {
+        const float2 v = G[((size_t)l * H + r) * W + c];
+        const float m = hypotf(v.x, v.y);
+        if (rho2 < k2 && m > 0.f) {
             const double fz = sqrt(k2 - rho2);
             dz[h] = (float)(fz - f0z);
-            lf[h] = (float)log2(fz);
+            lw[h] = (float)(log2(fz) - (double)log2f(m));
+            ph[h] = -atan2f(v.y, v.x);
         }
     }
-    tab[idx] = make_float4(dz[0], dz[1], lf[0], lf[1]);
-}
-
-__global__ void k_gtiles(const float2 *__restrict__ G, int n_lambda, int H, int W, int tiles_x, int tiles_y,
-                         float4 *__restrict__ out) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long per_l = (long long)tiles_x * tiles_y * BQ;
-    if (idx >= per_l * n_lambda) return;
-    const int l = (int)(idx / per_l);
-    const long long rem = idx % per_l;
-    const int t = (int)(rem / BQ), q = (int)(rem % BQ);
-    const int r = (t / tiles_x) * BTH + q / 32, c0 = (t % tiles_x) * BTW + q % 32;
-    float2 v[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int c = c0 + 32 * h;
-        if (r < H && c < W) v[h] = G[((size_t)l * H + r) * W + c];
-    }
-    out[idx] = make_float4(v[0].x, v[1].x, v[0].y, v[1].y);
+    tab[idx] = make_float4(dz[0], dz[1], lw[0], lw[1]);
+    ps[idx] = make_float2(ph[0], ph[1]);
 }
 
 __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ BwdArgs A) {
@@ -250,16 +241,20 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
         const int ntx = S.tx1 - S.tx0 + 1, nty = S.ty1 - S.ty0 + 1;
         const int n_t = (ntx > 0 && nty > 0) ? ntx * nty : 0;
         const size_t ntiles = (size_t)A.tiles_x * A.tiles_y;
-        const float4 *gsl = A.gtiles + (size_t)l * ntiles * BQ;
-        const float4 *tsl = A.pixtab + (size_t)l * ntiles * BQ;
+        const float4 *tsl = A.tab + (size_t)l * ntiles * BQ;
+        const float2 *psl = A.ps + (size_t)l * ntiles * BQ;
 
         auto issue = [&](int t, int buf) {
             const size_t tile = (size_t)(S.ty0 + t / ntx) * A.tiles_x + (S.tx0 + t % ntx);
 #pragma unroll
             for (int i = 0; i < BQ / BNT; ++i) {
                 const int e = tid + BNT * i;
-                cp_async16(&S.g[buf][e], gsl + tile * BQ + e);
-                cp_async16(&S.px[buf][e], tsl + tile * BQ + e);
+                cp_async16(&S.t[buf][e], tsl + tile * BQ + e);
+            }
+#pragma unroll
+            for (int i = 0; i < BQ / (2 * BNT); ++i) {  // two float2 per 16-byte copy
+                const int e = 2 * (tid + BNT * i);
+                cp_async16(&S.ps[buf][e], psl + tile * BQ + e);
             }
         };
         if (n_t > 0) issue(0, 0);
@@ -337,7 +332,16 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                 const float2 ac = make_float2(fmaf(Ar.x, dx0, Ar.w), fmaf(Ar.x, dx1, Ar.w));
                 const float2 bc = make_float2(fmaf(Br.x, dx0, Br.w), fmaf(Br.x, dx1, Br.w));
                 const float2 gc = make_float2(fmaf(Gr.x, dx0, Gr.w), fmaf(Gr.x, dx1, Gr.w));
-                const float2 tc = make_float2(fmaf(Mr.x, dx0, Mr.w), fmaf(Mr.x, dx1, Mr.w));
+                // the phase at the lane's two columns on the tile's reference row, reduced to
+                // [-pi, pi] (t / 2 pi + 1.5 2^23, minus 1.5 2^23: the nearest turn count); the rows
+                // add |t_y dy| + |t_z dz| to it and the sum goes to sin/cos unreduced (the argument
+                // error of sin.approx grows like 1.2e-7 |t|)
+                float2 tc = make_float2(fmaf(Mr.x, dx0, Mr.w), fmaf(Mr.x, dx1, Mr.w));
+                {
+                    const float2 kt = __fadd2_rn(__ffma2_rn(tc, pair(0.15915494309189535f), pair(12582912.0f)),
+                                                 pair(-12582912.0f));
+                    tc = __ffma2_rn(kt, pair(-6.28318530717958647692f), tc);
+                }
                 const float2 ay = pair(Ar.y), az = pair(Ar.z), by = pair(Br.y), bz = pair(Br.z);
                 const float2 gy = pair(Gr.y), gz = pair(Gr.z), ty = pair(Mr.y), tz = pair(Mr.z);
                 float2 sp[4], sz[4], sy[4];
@@ -347,26 +351,18 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
 #pragma unroll 2
                 for (int row = row_lo; row <= row_hi; ++row) {
                     const float2 dy = pair(fmaf((float)row, dfyf, dyb));
-                    const float4 G4 = S.g[buf][32 * row + lane];
-                    const float4 P4 = S.px[buf][32 * row + lane];
-                    const float2 gr = make_float2(G4.x, G4.y), gi = make_float2(G4.z, G4.w);
-                    const float2 dz = make_float2(P4.x, P4.y), lf = make_float2(P4.z, P4.w);
+                    const float4 T4 = S.t[buf][32 * row + lane];
+                    const float2 ps = S.ps[buf][32 * row + lane];
+                    const float2 dz = make_float2(T4.x, T4.y), lw = make_float2(T4.z, T4.w);
                     const float2 a = __ffma2_rn(az, dz, __ffma2_rn(ay, dy, ac));
                     const float2 b = __ffma2_rn(bz, dz, __ffma2_rn(by, dy, bc));
                     const float2 g = __ffma2_rn(gz, dz, __ffma2_rn(gy, dy, gc));
-                    const float2 tt = __ffma2_rn(tz, dz, __ffma2_rn(ty, dy, tc));
-                    const float2 uq = __ffma2_rn(a, a, __ffma2_rn(b, b, lf));  // a'^2 + b'^2 + log2 f_z
-                    // round-to-nearest turn count: t / 2pi + 1.5 2^23, minus 1.5 2^23
-                    const float2 kr = __fadd2_rn(__ffma2_rn(tt, pair(0.15915494309189535f), pair(12582912.0f)),
-                                                 pair(-12582912.0f));
-                    const float2 ang = __ffma2_rn(kr, pair(-6.28318530717958647692f), tt);
+                    const float2 ang = __ffma2_rn(tz, dz, __fadd2_rn(__ffma2_rn(ty, dy, tc), ps));  // phi - arg G
+                    const float2 uq = __ffma2_rn(a, a, __ffma2_rn(b, b, lw));  // a'^2 + b'^2 + log2(f_z / |G|)
                     const float2 es = make_float2(with_sign_of(ex2_approx(-uq.x), g.x), with_sign_of(ex2_approx(-uq.y), g.y));
-                    const float2 kc = __fmul2_rn(es, make_float2(cos_approx(ang.x), cos_approx(ang.y)));
-                    const float2 ks = __fmul2_rn(es, make_float2(sin_approx(ang.x), sin_approx(ang.y)));
-                    // sign(g) P0 = sign(g) conj(G) f_z^-1 2^-(a'^2+b'^2) e^{j phi}
-                    const float2 Rg = __ffma2_rn(gr, kc, __fmul2_rn(gi, ks));
-                    const float2 gk = __fmul2_rn(gi, kc);
-                    const float2 Pi = __ffma2_rn(gr, ks, make_float2(-gk.x, -gk.y));
+                    // sign(g) P0 = sign(g) conj(G) f_z^-1 2^-(a'^2+b'^2) e^{j phi} = Rg + j Pi
+                    const float2 Rg = __fmul2_rn(es, make_float2(cos_approx(ang.x), cos_approx(ang.y)));
+                    const float2 Pi = __fmul2_rn(es, make_float2(sin_approx(ang.x), sin_approx(ang.y)));
                     const float2 R = __fmul2_rn(g, Rg), I = __fmul2_rn(g, Pi);  // |g| Re P0, |g| Im P0
                     const float2 X[4] = {__fmul2_rn(R, a), __fmul2_rn(R, b), Rg, I};
 #pragma unroll
@@ -484,12 +480,11 @@ cudaError_t launch_pixtab(int n_lambda, int H, int W, double dfx, double dfy, co
 }
 
 cudaError_t launch_bwd_tables(int n_lambda, int H, int W, double dfx, double dfy, const InvLam &il, const float2 *G,
-                              float4 *gtiles, float4 *pixtab, cudaStream_t s) {
+                              float4 *tab, float2 *ps, cudaStream_t s) {
     const int tx = bwd_tiles_x(W), ty = bwd_tiles_y(H);
     const long long n = (long long)n_lambda * tx * ty * BQ;
-    k_pixtab_tiles<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n_lambda, H, W, dfx, dfy, il, tx, ty, pixtab);
-    k_gtiles<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(G, n_lambda, H, W, tx, ty, gtiles);
-    count_launches(2);
+    k_bwd_tables<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(G, n_lambda, H, W, dfx, dfy, il, tx, ty, tab, ps);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -84,8 +84,8 @@ cudaError_t launch_splat_fp64(const Splat64Args &a, cudaStream_t s);
 
 struct BwdArgs {
     const Rec *rec;         // backward records (r3 unit, W separate), segment-major (single scene)
-    const float4 *gtiles;   // dL/du_SLM, tile-major column pairs (k_gtiles)
-    const float4 *pixtab;   // (f_z - f0_z of the pixel's tile, log2 f_z), tile-major column pairs
+    const float4 *tab;      // (f_z - f0_z of the pixel's tile, log2 f_z - log2 |dL/du_SLM|), tile-major column pairs
+    const float2 *ps;       // -arg dL/du_SLM, tile-major column pairs
     double *acc;            // [n_records][13] totals
     int *queue;
     int *status;
@@ -132,8 +132,8 @@ cudaError_t launch_grad_assemble(const GPre *gp, const float *ampc, const double
 int bwd_block_size();
 int bwd_tiles_x(int W);
 int bwd_tiles_y(int H);
-size_t bwd_table_bytes(int n_lambda, int H, int W);  // one tile-major table (G or the per-pixel table)
+size_t bwd_table_bytes(int n_lambda, int H, int W);  // one float4 tile-major table (the float2 one takes half)
 cudaError_t launch_bwd_tables(int n_lambda, int H, int W, double dfx, double dfy, const InvLam &il, const float2 *G,
-                              float4 *gtiles, float4 *pixtab, cudaStream_t s);
+                              float4 *tab, float2 *ps, cudaStream_t s);
 
 }  // namespace gws

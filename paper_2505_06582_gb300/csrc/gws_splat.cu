@@ -12,8 +12,9 @@
 //
 // Precision: the phase -f.mu reaches ~2e4 cycles.  Per (record, tile) it is split into an
 // FP64 anchor at the tile's reference frequency f0, reduced mod 1 in FP64, plus FP32
-// deltas (f - f0).mu inside the tile (|.| < ~20 cycles); the FP32 phase is reduced to
-// [-pi, pi] before sin/cos (the record carries -2 pi mu, the anchor is in radians).  f0 is
+// deltas (f - f0).mu inside the tile (|.| < ~20 cycles); per (record, thread) the FP32 phase at
+// the thread's middle column is reduced to [-pi, pi], and the pixels' phases (a few cycles
+// from it) go to sin/cos unreduced (the record carries -2 pi mu, the anchor is in radians).  f0 is
 // the centre of the tile's valid pixels; f_z and f_z - f0_z are formed in FP64 once per pixel
 // and item, and 1/f_z enters as log2(1/f_z) inside the exponent.  Per-chunk FP32 sums are
 // merged into a TwoSum-compensated FP32 total.
@@ -50,29 +51,33 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
 }
 
 // One listed record over this thread's PH pixel pairs (packed f32x2): the Gaussian factor and
-// the phase of Eq. 10 from the per-(record, tile) scalars sv[0..3], accumulated into acc.
+// the phase of Eq. 10 from the per-(record, tile) scalars sv[0..3], accumulated into acc.  The
+// linear forms are anchored at the thread's middle column (offset dxm from the tile's reference
+// frequency; the pixels sit at ddx from it), and the phase there is reduced to [-pi, pi] once per
+// record, so the per-pixel phase stays within |t_x ddx| + |t_z dz| + pi of zero and goes to
+// sin/cos unreduced (the argument error of sin.approx grows like 1.2e-7 |t|).
 template <int PH>
-__device__ __forceinline__ void splat_record(const float4 *__restrict__ sv, float dy, const float2 *dx, const float2 *dz,
-                                             const float2 *lfz, float2 *acc_re, float2 *acc_im) {
+__device__ __forceinline__ void splat_record(const float4 *__restrict__ sv, float dy, float dxm, const float2 *ddx,
+                                             const float2 *dz, const float2 *lfz, float2 *acc_re, float2 *acc_im) {
     const float4 Ar = sv[0], Br = sv[1], Gr = sv[2], Mr = sv[3];
-    const float2 ar = pair(fmaf(Ar.y, dy, Ar.w)), br = pair(fmaf(Br.y, dy, Br.w));
-    const float2 gr = pair(fmaf(Gr.y, dy, Gr.w)), tr = pair(fmaf(Mr.y, dy, Mr.w));
+    const float2 ar = pair(fmaf(Ar.x, dxm, fmaf(Ar.y, dy, Ar.w))), br = pair(fmaf(Br.x, dxm, fmaf(Br.y, dy, Br.w)));
+    const float2 gr = pair(fmaf(Gr.x, dxm, fmaf(Gr.y, dy, Gr.w)));
+    // t (radians) at the middle column minus 2 pi round(t / 2 pi), rounding on the FP32 pipe (+-1.5 * 2^23)
+    const float t0 = fmaf(Mr.x, dxm, fmaf(Mr.y, dy, Mr.w));
+    const float k0 = __fadd_rn(fmaf(t0, 0.15915494309189535f, 12582912.0f), -12582912.0f);
+    const float2 tr = pair(fmaf(k0, -6.28318530717958647692f, t0));
     const float2 ax = pair(Ar.x), az = pair(Ar.z), bx = pair(Br.x), bz = pair(Br.z);
     const float2 gx = pair(Gr.x), gz = pair(Gr.z), tx2 = pair(Mr.x), tz = pair(Mr.z);
 #pragma unroll
     for (int h = 0; h < PH; ++h) {
-        const float2 a = __ffma2_rn(az, dz[h], __ffma2_rn(ax, dx[h], ar));
-        const float2 b = __ffma2_rn(bz, dz[h], __ffma2_rn(bx, dx[h], br));
-        const float2 g = __ffma2_rn(gz, dz[h], __ffma2_rn(gx, dx[h], gr));
-        const float2 t = __ffma2_rn(tz, dz[h], __ffma2_rn(tx2, dx[h], tr));
+        const float2 a = __ffma2_rn(az, dz[h], __ffma2_rn(ax, ddx[h], ar));
+        const float2 b = __ffma2_rn(bz, dz[h], __ffma2_rn(bx, ddx[h], br));
+        const float2 g = __ffma2_rn(gz, dz[h], __ffma2_rn(gx, ddx[h], gr));
+        const float2 ang = __ffma2_rn(tz, dz[h], __ffma2_rn(tx2, ddx[h], tr));
         // |g| / f_z 2^-(a^2 + b^2) = g (sign(g) 2^-(a^2 + b^2 + log2 f_z))
         const float2 u = __ffma2_rn(a, a, __ffma2_rn(b, b, lfz[h]));
         const float2 amp = __fmul2_rn(g, make_float2(with_sign_of(ex2_approx(-u.x), g.x),
                                                      with_sign_of(ex2_approx(-u.y), g.y)));
-        // t (radians) minus 2 pi round(t / 2 pi), rounding on the FP32 pipe (+-1.5 * 2^23)
-        const float2 kr = __fadd2_rn(__ffma2_rn(t, pair(0.15915494309189535f), pair(12582912.0f)),
-                                     pair(-12582912.0f));
-        const float2 ang = __ffma2_rn(kr, pair(-6.28318530717958647692f), t);
         acc_re[h] = __ffma2_rn(amp, make_float2(cos_approx(ang.x), cos_approx(ang.y)), acc_re[h]);
         acc_im[h] = __ffma2_rn(amp, make_float2(sin_approx(ang.x), sin_approx(ang.y)), acc_im[h]);
     }
@@ -140,13 +145,14 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
         const float2 *prow_tab = A.pixtab + ((size_t)l * A.H + (prow < A.H ? prow : 0)) * A.W;
         // pixels p = 2 h + {0, 1} form the f32x2 pair h of the packed arithmetic
         constexpr int PH = PX / 2;
-        float2 dx[PH], dz[PH], lfz[PH];
+        float2 dx[PH], dz[PH], lfz[PH];  // dx: offsets from the thread's middle column
+        const float dxm = (float)(pcol0 + PX / 2 - c_ref) * dfxf;
 #pragma unroll
         for (int p = 0; p < PX; ++p) {
             const int col = pcol0 + p;
             const float2 pt = (prow < A.H && col < A.W) ? prow_tab[col] : make_float2(0.f, -INFINITY);
             const bool ok = pt.y > -INFINITY;  // (0, -inf): evanescent or outside the grid
-            const float vx = (float)(col - c_ref) * dfxf;
+            const float vx = (float)(p - PX / 2) * dfxf;
             const float vl = ok ? -pt.y : INFINITY;  // log2 f_z: 2^-(a^2 + b^2 + log2 f_z) = f_z^-1 2^-(a^2 + b^2)
             const float vz = ok ? pt.x : 0.f;
             if (p & 1) {
@@ -261,11 +267,11 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
                 int i = 0;
                 if (RU == 2) {
                     for (; i + 1 < cnt; i += 2) {
-                        splat_record<PH>(s_sv + lst[i] * 4, dy, dx, dz, lfz, acc_re, acc_im);
-                        splat_record<PH>(s_sv + lst[i + 1] * 4, dy, dx, dz, lfz, acc2_re, acc2_im);
+                        splat_record<PH>(s_sv + lst[i] * 4, dy, dxm, dx, dz, lfz, acc_re, acc_im);
+                        splat_record<PH>(s_sv + lst[i + 1] * 4, dy, dxm, dx, dz, lfz, acc2_re, acc2_im);
                     }
                 }
-                for (; i < cnt; ++i) splat_record<PH>(s_sv + lst[i] * 4, dy, dx, dz, lfz, acc_re, acc_im);
+                for (; i < cnt; ++i) splat_record<PH>(s_sv + lst[i] * 4, dy, dxm, dx, dz, lfz, acc_re, acc_im);
             }
             if (RU == 2) {
 #pragma unroll
