@@ -49,6 +49,8 @@ struct BwdShared {
     double tot[BB][NTOT];
     float red[BNT / 32][16];
     unsigned mask[BB / 32];
+    unsigned char list[BB];  // the surviving records of the current tile, in record order
+    int n_surv, next;        // their count; the next list entry a warp takes
     TileConst tc;
     int tx0, tx1, ty0, ty1;
     int item;
@@ -315,17 +317,28 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                 if (lane == 0) S.mask[warp] = bal;
             }
             __syncthreads();
+            if (tid < BB) {  // compact the survivors; warps then take them one by one
+                int before = 0;
+                for (int w = 0; w < tid / 32; ++w) before += __popc(S.mask[w]);
+                const unsigned m = S.mask[tid / 32];
+                if ((m >> lane) & 1u) S.list[before + __popc(m & ((1u << lane) - 1u))] = (unsigned char)tid;
+                if (tid == BB - 1) {
+                    S.n_surv = before + __popc(m);
+                    S.next = 0;
+                }
+            }
+            __syncthreads();
             const float dfxf = (float)A.dfx, dfyf = (float)A.dfy;
             const float dx0 = (float)(c_lo + lane - c_ref) * dfxf;  // the lane's columns c and c + 32
             const float dx1 = (float)(c_lo + lane + 32 - c_ref) * dfxf;
             const float dyb = (float)(r_lo - r_ref) * dfyf;
-            int q = 0;
-            for (int wi = 0; wi < BB / 32; ++wi) {
-              unsigned m = S.mask[wi];
-              while (m) {
-                const int k = wi * 32 + __ffs(m) - 1;
-                m &= m - 1u;
-                if ((q++ & (BNT / 32 - 1)) != warp) continue;
+            const int n_surv = S.n_surv;
+            for (;;) {
+                int j = 0;
+                if (lane == 0) j = atomicAdd(&S.next, 1);
+                j = __shfl_sync(0xffffffffu, j, 0);
+                if (j >= n_surv) break;
+                const int k = S.list[j];
                 const int2 rr = S.rows[k];
                 const int row_lo = rr.x, row_hi = rr.y;
                 const float4 Ar = S.sv[k][0], Br = S.sv[k][1], Gr = S.sv[k][2], Mr = S.sv[k][3];
@@ -348,7 +361,7 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
 #pragma unroll
                 for (int u = 0; u < 4; ++u) sp[u] = sz[u] = sy[u] = pair(0.f);
                 // one row = the lane's two columns as one f32x2 pair; two rows in flight
-#pragma unroll 2
+#pragma unroll 4
                 for (int row = row_lo; row <= row_hi; ++row) {
                     const float2 dy = pair(fmaf((float)row, dfyf, dyb));
                     const float4 T4 = S.t[buf][32 * row + lane];
@@ -395,7 +408,6 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                     S.tot[k][lane] += add;
                 }
                 __syncwarp();
-              }
             }
             __syncthreads();
         }

@@ -271,6 +271,7 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
                         splat_record<PH>(s_sv + lst[i + 1] * 4, dy, dxm, dx, dz, lfz, acc2_re, acc2_im);
                     }
                 }
+#pragma unroll 2
                 for (; i < cnt; ++i) splat_record<PH>(s_sv + lst[i] * 4, dy, dxm, dx, dz, lfz, acc_re, acc_im);
             }
             if (RU == 2) {
