@@ -6,7 +6,7 @@
 //
 // The spectra are recomputed, never stored.  A work item is a block of BB consecutive
 // records of one wavelength (footprint order, so a block's footprints are alike).  The CTA
-// walks the 64 x 32 frequency tiles of the block's footprint union; per tile it stages two
+// walks the 64 x 64 frequency tiles of the block's footprint union; per tile it stages two
 // per-pixel tables in shared memory with cp.async from copies laid out tile by tile
 // (k_bwd_tables: (f_z - f0_z, log2 f_z - log2 |G|) and -arg G, padded past the grid so that a
 // tile is one contiguous block per table, and a lane's two columns c and c + 32 of a row sit
@@ -26,7 +26,8 @@
 
 namespace gws {
 
-constexpr int BTW = 64, BTH = 32, BPX = BTW * BTH;
+constexpr int BTW = 64, BTH = 64, BPX = BTW * BTH;
+constexpr int BSEG = 32;     // rows per phase segment (the phase is re-anchored at each segment's middle row)
 constexpr int BQ = BPX / 2;  // float4 column pairs per tile and array
 constexpr int BB = 128;   // records per work item
 constexpr int BNT = 256;  // threads per CTA
@@ -41,8 +42,8 @@ struct TileConst {  // geometry of the current tile, computed once by thread 0
 };
 
 struct BwdShared {
-    float4 t[2][BQ];   // [row][lane]: (dz(c), dz(c + 32), lw(c), lw(c + 32)), c = c_lo + lane, lw = log2(f_z / |G|)
-    float2 ps[2][BQ];  // [row][lane]: (-arg G(c), -arg G(c + 32))
+    float4 t[BQ];   // [row][lane]: (dz(c), dz(c + 32), lw(c), lw(c + 32)), c = c_lo + lane, lw = log2(f_z / |G|)
+    float2 ps[BQ];  // [row][lane]: (-arg G(c), -arg G(c + 32))
     Rec rec[BB];
     float4 sv[BB][4];
     int2 rows[BB];  // per surviving record: the tile rows [x, y] its footprint's bounding box reaches
@@ -246,25 +247,23 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
         const float4 *tsl = A.tab + (size_t)l * ntiles * BQ;
         const float2 *psl = A.ps + (size_t)l * ntiles * BQ;
 
-        auto issue = [&](int t, int buf) {
-            const size_t tile = (size_t)(S.ty0 + t / ntx) * A.tiles_x + (S.tx0 + t % ntx);
-#pragma unroll
-            for (int i = 0; i < BQ / BNT; ++i) {
-                const int e = tid + BNT * i;
-                cp_async16(&S.t[buf][e], tsl + tile * BQ + e);
-            }
-#pragma unroll
-            for (int i = 0; i < BQ / (2 * BNT); ++i) {  // two float2 per 16-byte copy
-                const int e = 2 * (tid + BNT * i);
-                cp_async16(&S.ps[buf][e], psl + tile * BQ + e);
-            }
-        };
-        if (n_t > 0) issue(0, 0);
-        cp_async_commit();
+        // one buffer per table (the tables of a 64 x 64 tile take 48 KB): the copy of tile t
+        // overlaps its cull; the CTA's other resident CTA covers the rest of the wait
         for (int t = 0; t < n_t; ++t) {
-            const int buf = t & 1;
-            if (t + 1 < n_t) issue(t + 1, buf ^ 1);
-            cp_async_commit();
+            {
+                const size_t tile = (size_t)(S.ty0 + t / ntx) * A.tiles_x + (S.tx0 + t % ntx);
+#pragma unroll
+                for (int i = 0; i < BQ / BNT; ++i) {
+                    const int e = tid + BNT * i;
+                    cp_async16(&S.t[e], tsl + tile * BQ + e);
+                }
+#pragma unroll
+                for (int i = 0; i < BQ / (2 * BNT); ++i) {  // two float2 per 16-byte copy
+                    const int e = 2 * (tid + BNT * i);
+                    cp_async16(&S.ps[e], psl + tile * BQ + e);
+                }
+                cp_async_commit();
+            }
             if (tid == 0) {
                 TileConst &T = S.tc;
                 const int tx = S.tx0 + t % ntx, ty = S.ty0 + t / ntx;
@@ -281,7 +280,6 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                 T.y0 = (float)((double)(T.r_lo - A.H / 2) * A.dfy);
                 T.y1 = (float)((double)(r_hi - A.H / 2) * A.dfy);
             }
-            cp_async_wait1();
             __syncthreads();
             const int c_lo = S.tc.c_lo, r_lo = S.tc.r_lo, c_ref = S.tc.c_ref, r_ref = S.tc.r_ref;
             // cull + per-(record, tile) scalars
@@ -327,6 +325,7 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                     S.next = 0;
                 }
             }
+            cp_async_wait0();
             __syncthreads();
             const float dfxf = (float)A.dfx, dfyf = (float)A.dfy;
             const float dx0 = (float)(c_lo + lane - c_ref) * dfxf;  // the lane's columns c and c + 32
@@ -345,44 +344,52 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                 const float2 ac = make_float2(fmaf(Ar.x, dx0, Ar.w), fmaf(Ar.x, dx1, Ar.w));
                 const float2 bc = make_float2(fmaf(Br.x, dx0, Br.w), fmaf(Br.x, dx1, Br.w));
                 const float2 gc = make_float2(fmaf(Gr.x, dx0, Gr.w), fmaf(Gr.x, dx1, Gr.w));
-                // the phase at the lane's two columns on the tile's reference row, reduced to
-                // [-pi, pi] (t / 2 pi + 1.5 2^23, minus 1.5 2^23: the nearest turn count); the rows
-                // add |t_y dy| + |t_z dz| to it and the sum goes to sin/cos unreduced (the argument
-                // error of sin.approx grows like 1.2e-7 |t|)
-                float2 tc = make_float2(fmaf(Mr.x, dx0, Mr.w), fmaf(Mr.x, dx1, Mr.w));
-                {
-                    const float2 kt = __fadd2_rn(__ffma2_rn(tc, pair(0.15915494309189535f), pair(12582912.0f)),
-                                                 pair(-12582912.0f));
-                    tc = __ffma2_rn(kt, pair(-6.28318530717958647692f), tc);
-                }
+                // the phase at the lane's two columns on the tile's reference row (FP32 from the
+                // reduced FP64 anchor); per segment of BSEG rows it is moved to the segment's middle
+                // row and reduced to [-pi, pi] (t / 2 pi + 1.5 2^23, minus 1.5 2^23: the nearest turn
+                // count), and the rows' |t_y (dy - dy_s)| + |t_z dz| are added unreduced before sin/cos
+                // (the argument error of sin.approx grows like 1.2e-7 |t|)
+                const float2 tc = make_float2(fmaf(Mr.x, dx0, Mr.w), fmaf(Mr.x, dx1, Mr.w));
                 const float2 ay = pair(Ar.y), az = pair(Ar.z), by = pair(Br.y), bz = pair(Br.z);
                 const float2 gy = pair(Gr.y), gz = pair(Gr.z), ty = pair(Mr.y), tz = pair(Mr.z);
                 float2 sp[4], sz[4], sy[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) sp[u] = sz[u] = sy[u] = pair(0.f);
-                // one row = the lane's two columns as one f32x2 pair; two rows in flight
+                for (int seg = row_lo / BSEG; seg <= row_hi / BSEG; ++seg) {
+                    const int s_lo = max(row_lo, seg * BSEG), s_hi = min(row_hi, seg * BSEG + BSEG - 1);
+                    const float dys = fmaf((float)(seg * BSEG + BSEG / 2), dfyf, dyb);  // dy of the middle row
+                    const float dyrb = dyb - dys;
+                    float2 ts = __ffma2_rn(ty, pair(dys), tc);
+                    {
+                        const float2 kt = __fadd2_rn(__ffma2_rn(ts, pair(0.15915494309189535f), pair(12582912.0f)),
+                                                     pair(-12582912.0f));
+                        ts = __ffma2_rn(kt, pair(-6.28318530717958647692f), ts);
+                    }
+                    // one row = the lane's two columns as one f32x2 pair; four rows in flight
 #pragma unroll 4
-                for (int row = row_lo; row <= row_hi; ++row) {
-                    const float2 dy = pair(fmaf((float)row, dfyf, dyb));
-                    const float4 T4 = S.t[buf][32 * row + lane];
-                    const float2 ps = S.ps[buf][32 * row + lane];
-                    const float2 dz = make_float2(T4.x, T4.y), lw = make_float2(T4.z, T4.w);
-                    const float2 a = __ffma2_rn(az, dz, __ffma2_rn(ay, dy, ac));
-                    const float2 b = __ffma2_rn(bz, dz, __ffma2_rn(by, dy, bc));
-                    const float2 g = __ffma2_rn(gz, dz, __ffma2_rn(gy, dy, gc));
-                    const float2 ang = __ffma2_rn(tz, dz, __fadd2_rn(__ffma2_rn(ty, dy, tc), ps));  // phi - arg G
-                    const float2 uq = __ffma2_rn(a, a, __ffma2_rn(b, b, lw));  // a'^2 + b'^2 + log2(f_z / |G|)
-                    const float2 es = make_float2(with_sign_of(ex2_approx(-uq.x), g.x), with_sign_of(ex2_approx(-uq.y), g.y));
-                    // sign(g) P0 = sign(g) conj(G) f_z^-1 2^-(a'^2+b'^2) e^{j phi} = Rg + j Pi
-                    const float2 Rg = __fmul2_rn(es, make_float2(cos_approx(ang.x), cos_approx(ang.y)));
-                    const float2 Pi = __fmul2_rn(es, make_float2(sin_approx(ang.x), sin_approx(ang.y)));
-                    const float2 R = __fmul2_rn(g, Rg), I = __fmul2_rn(g, Pi);  // |g| Re P0, |g| Im P0
-                    const float2 X[4] = {__fmul2_rn(R, a), __fmul2_rn(R, b), Rg, I};
+                    for (int row = s_lo; row <= s_hi; ++row) {
+                        const float2 dy = pair(fmaf((float)row, dfyf, dyb));
+                        const float2 dyr = pair(fmaf((float)row, dfyf, dyrb));
+                        const float4 T4 = S.t[32 * row + lane];
+                        const float2 ps = S.ps[32 * row + lane];
+                        const float2 dz = make_float2(T4.x, T4.y), lw = make_float2(T4.z, T4.w);
+                        const float2 a = __ffma2_rn(az, dz, __ffma2_rn(ay, dy, ac));
+                        const float2 b = __ffma2_rn(bz, dz, __ffma2_rn(by, dy, bc));
+                        const float2 g = __ffma2_rn(gz, dz, __ffma2_rn(gy, dy, gc));
+                        const float2 ang = __ffma2_rn(tz, dz, __fadd2_rn(__ffma2_rn(ty, dyr, ts), ps));  // phi - arg G
+                        const float2 uq = __ffma2_rn(a, a, __ffma2_rn(b, b, lw));  // a'^2 + b'^2 + log2(f_z / |G|)
+                        const float2 es = make_float2(with_sign_of(ex2_approx(-uq.x), g.x), with_sign_of(ex2_approx(-uq.y), g.y));
+                        // sign(g) P0 = sign(g) conj(G) f_z^-1 2^-(a'^2+b'^2) e^{j phi} = Rg + j Pi
+                        const float2 Rg = __fmul2_rn(es, make_float2(cos_approx(ang.x), cos_approx(ang.y)));
+                        const float2 Pi = __fmul2_rn(es, make_float2(sin_approx(ang.x), sin_approx(ang.y)));
+                        const float2 R = __fmul2_rn(g, Rg), I = __fmul2_rn(g, Pi);  // |g| Re P0, |g| Im P0
+                        const float2 X[4] = {__fmul2_rn(R, a), __fmul2_rn(R, b), Rg, I};
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        sp[u] = __fadd2_rn(sp[u], X[u]);
-                        sy[u] = __ffma2_rn(X[u], dy, sy[u]);
-                        sz[u] = __ffma2_rn(X[u], dz, sz[u]);
+                        for (int u = 0; u < 4; ++u) {
+                            sp[u] = __fadd2_rn(sp[u], X[u]);
+                            sy[u] = __ffma2_rn(X[u], dy, sy[u]);
+                            sz[u] = __ffma2_rn(X[u], dz, sz[u]);
+                        }
                     }
                 }
                 float v[16];
