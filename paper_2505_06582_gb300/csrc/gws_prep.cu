@@ -645,16 +645,23 @@ __global__ void k_modulate(typename Cx<R>::T *__restrict__ data, int n_slices, i
 template <typename R>
 __global__ void k_amax(const typename Cx<R>::T *__restrict__ f, long long hw, unsigned long long *__restrict__ amax2) {
     const int l = blockIdx.y;
-    R m = 0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < hw; i += (long long)gridDim.x * blockDim.x) {
-        const typename Cx<R>::T v = f[(size_t)l * hw + i];
-        const R a = v.x * v.x + v.y * v.y;
-        m = a > m ? a : m;
+    const typename Cx<R>::T *fl = f + (size_t)l * hw;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    R m0 = 0, m1 = 0, m2 = 0, m3 = 0;  // four loads in flight per thread
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < hw; i += 4 * stride) {
+        const typename Cx<R>::T v0 = fl[i], v1 = fl[i + stride], v2 = fl[i + 2 * stride], v3 = fl[i + 3 * stride];
+        m0 = fmax(m0, v0.x * v0.x + v0.y * v0.y);
+        m1 = fmax(m1, v1.x * v1.x + v1.y * v1.y);
+        m2 = fmax(m2, v2.x * v2.x + v2.y * v2.y);
+        m3 = fmax(m3, v3.x * v3.x + v3.y * v3.y);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        R t = __shfl_xor_sync(0xffffffffu, m, o);
-        m = t > m ? t : m;
+    for (; i < hw; i += stride) {
+        const typename Cx<R>::T v = fl[i];
+        m0 = fmax(m0, v.x * v.x + v.y * v.y);
     }
+    R m = fmax(fmax(m0, m1), fmax(m2, m3));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) {
         unsigned long long bits =
             sizeof(R) == 8 ? (unsigned long long)__double_as_longlong((double)m) : (unsigned long long)__float_as_uint((float)m);
@@ -662,34 +669,37 @@ __global__ void k_amax(const typename Cx<R>::T *__restrict__ f, long long hw, un
     }
 }
 
+// DPAC (Sec. 5): one wavelength per grid row y, 32-bit pixel indices (H W < 2^31 is checked by
+// the API), four pixels per thread.
 template <typename R>
-__global__ void k_dpac(const typename Cx<R>::T *__restrict__ f, int n_lambda, int H, int W,
+__global__ void k_dpac(const typename Cx<R>::T *__restrict__ f, int H, int W,
                        const unsigned long long *__restrict__ amax2, double amp_scale, float *__restrict__ out) {
-    const long long hw = (long long)H * W;
-    const long long total = hw * n_lambda;
+    const int l = blockIdx.y;
+    const unsigned hw = (unsigned)H * (unsigned)W;
     const R pi = (R)kPi, tpi = (R)kTwoPi, inv_tpi = (R)(1.0 / kTwoPi);
+    R m2max;
+    if (amp_scale > 0) m2max = (R)(amp_scale * amp_scale);
+    else if (sizeof(R) == 8) m2max = (R)__longlong_as_double((long long)amax2[l]);
+    else m2max = (R)__uint_as_float((unsigned)amax2[l]);
+    const R inv_m2 = m2max > 0 ? (R)1 / m2max : (R)0;
+    const typename Cx<R>::T *fl = f + (size_t)l * hw;
+    float *ol = out + (size_t)l * hw;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const long long idx = ((long long)blockIdx.x * 4 + u) * blockDim.x + threadIdx.x;
-        if (idx >= total) break;
-        const int l = (int)(idx / hw);
-        const long long pix = idx % hw;
-        const int r = (int)(pix / W), c = (int)(pix % W);
-        R m2max;
-        if (amp_scale > 0) m2max = (R)(amp_scale * amp_scale);
-        else if (sizeof(R) == 8) m2max = (R)__longlong_as_double((long long)amax2[l]);
-        else m2max = (R)__uint_as_float((unsigned)amax2[l]);
-        const typename Cx<R>::T v = f[idx];
+        const unsigned pix = ((unsigned)blockIdx.x * 4u + (unsigned)u) * blockDim.x + threadIdx.x;
+        if (pix >= hw) break;
+        const unsigned r = pix / (unsigned)W, c = pix - r * (unsigned)W;
+        const typename Cx<R>::T v = fl[pix];
         const R m2 = v.x * v.x + v.y * v.y;
-        R a = m2max > 0 ? sqrt(m2 / m2max) : (R)0;
+        R a = sqrt(m2 * inv_m2);
         a = a > (R)1 ? (R)1 : a;
         const R phi = atan2(v.y, v.x);
         const R ac = acos(a);
-        R p = ((r + c) & 1) == 0 ? phi - ac : phi + ac;
+        R p = ((r + c) & 1u) == 0 ? phi - ac : phi + ac;
         p = p - tpi * floor((p + pi) * inv_tpi);
         if (p < -pi) p += tpi;
         if (p >= pi) p -= tpi;
-        out[idx] = (float)p;
+        ol[pix] = (float)p;
     }
 }
 
@@ -814,11 +824,11 @@ cudaError_t launch_encode(const void *field, int prec64, int n_lambda, int H, in
             k_amax<float><<<dim3(gx, n_lambda), 256, 0, s>>>((const float2 *)field, hw, amax2);
         count_launches(1);
     }
-    const long long n = hw * n_lambda;
+    const dim3 grid(nblk(hw, 1024), (unsigned)n_lambda);
     if (prec64)
-        k_dpac<double><<<nblk(n, 1024), 256, 0, s>>>((const double2 *)field, n_lambda, H, W, amax2, amp_scale, out);
+        k_dpac<double><<<grid, 256, 0, s>>>((const double2 *)field, H, W, amax2, amp_scale, out);
     else
-        k_dpac<float><<<nblk(n, 1024), 256, 0, s>>>((const float2 *)field, n_lambda, H, W, amax2, amp_scale, out);
+        k_dpac<float><<<grid, 256, 0, s>>>((const float2 *)field, H, W, amax2, amp_scale, out);
     count_launches(1);
     return cudaGetLastError();
 }
