@@ -5,7 +5,9 @@
 //   u_hat(f) = c o |r3 . f| / f_z |det V_o| T(A^-T (r1 . d, r2 . d)) e^{-j 2 pi f . v1},  d = f - f_r.
 // T(nu) = int_P e^{-j 2 pi nu . x} dx is the second divided difference of exp at the vertex
 // phases z = j (0, -a, -(a + b)), a = 2 pi nu_x, b = 2 pi nu_y, evaluated in FP32 as
-//   (E[t1,t2] - E[t0,t1]) / (j (t2 - t0)),  E[p,q] = e^{j (p+q)/2} sin((q-p)/2) / ((q-p)/2),
+//   (E[t1,t2] - E[t0,t1]) / (j (t2 - t0)),  E[p,q] = e^{j (p+q)/2} sin((q-p)/2) / ((q-p)/2)
+// (the record's phase added to (p+q)/2 before the cis; one approximate reciprocal for both sincs
+// and the 1 / (t2 - t0): 7 MUFU operations per pair),
 // with t0 <= t1 <= t2 the sorted phases when their spread exceeds TRI_SPREAD, else as the series
 // e^{j tbar} sum_k j^k h_k(t - tbar) / (k+2)! (h_k the complete homogeneous polynomials).
 // Dense: the spectrum of a triangle has no compact footprint.  One CTA per (tile, wavelength);
@@ -77,23 +79,26 @@ __device__ __forceinline__ float2 cis_reduced(float x) {
     return make_float2(cos_approx(r), sin_approx(r));
 }
 
-// T(nu) of the canonical triangle from its sorted vertex phases t0 <= t1 <= t2 (z = j t)
-__device__ __forceinline__ float2 tri_canonical(float t0, float t1, float t2) {
+// sin(h) / h for h >= 0 as a fraction (num, den): (sin h, h) with the argument reduced to
+// [-pi, pi] first, or (1, 1) below 1e-4 (where 1 - h^2 / 6 rounds to 1)
+__device__ __forceinline__ float2 sinc_frac(float h) {
+    if (!(h > 1e-4f)) return make_float2(1.f, 1.f);
+    const float k = __fadd_rn(fmaf(h, 0.15915494309189535f, 12582912.0f), -12582912.0f);
+    return make_float2(sin_approx(fmaf(k, -6.28318530717958647692f, h)), h);
+}
+
+// T(nu) e^{j th} of the canonical triangle from its sorted vertex phases t0 <= t1 <= t2 (z = j t)
+// and the record's phase th (both factors' phases are added before the one cis per term)
+__device__ __forceinline__ float2 tri_canonical_phased(float t0, float t1, float t2, float th) {
     const float sp = t2 - t0;
     if (sp > TRI_SPREAD) {
-        // E[p,q] = e^{j (p+q)/2} sinc((q-p)/2)
-        const float h12 = 0.5f * (t2 - t1), h01 = 0.5f * (t1 - t0);
-        const float s12 = h12 > 1e-4f ? sin_approx(h12 - 6.28318530717958647692f *
-                                                       __fadd_rn(fmaf(h12, 0.15915494309189535f, 12582912.0f), -12582912.0f)) /
-                                            h12
-                                      : 1.f - h12 * h12 * (1.f / 6.f);
-        const float s01 = h01 > 1e-4f ? sin_approx(h01 - 6.28318530717958647692f *
-                                                       __fadd_rn(fmaf(h01, 0.15915494309189535f, 12582912.0f), -12582912.0f)) /
-                                            h01
-                                      : 1.f - h01 * h01 * (1.f / 6.f);
-        const float2 c12 = cis_reduced(0.5f * (t1 + t2)), c01 = cis_reduced(0.5f * (t0 + t1));
-        const float dr = s12 * c12.x - s01 * c01.x, di = s12 * c12.y - s01 * c01.y;
-        const float inv = 1.f / sp;  // (dr + j di) / (j sp) = (di - j dr) / sp
+        // E[p,q] e^{j th} = e^{j ((p+q)/2 + th)} sinc((q-p)/2); the two sincs and 1 / sp share one
+        // reciprocal: (n12 d01 c12 - n01 d12 c01) / (d12 d01 sp)
+        const float2 f12 = sinc_frac(0.5f * (t2 - t1)), f01 = sinc_frac(0.5f * (t1 - t0));
+        const float2 c12 = cis_reduced(fmaf(0.5f, t1 + t2, th)), c01 = cis_reduced(fmaf(0.5f, t0 + t1, th));
+        const float w12 = f12.x * f01.y, w01 = f01.x * f12.y;
+        const float dr = fmaf(w12, c12.x, -w01 * c01.x), di = fmaf(w12, c12.y, -w01 * c01.y);
+        const float inv = __fdividef(1.f, f12.y * f01.y * sp);  // (dr + j di) / (j sp) = (di - j dr) / sp
         return make_float2(di * inv, -dr * inv);
     }
     const float tb = (t0 + t1 + t2) * (1.f / 3.f);
@@ -101,14 +106,14 @@ __device__ __forceinline__ float2 tri_canonical(float t0, float t1, float t2) {
     // h_k(u0) = u0^k, h_k(u0,u1) = h_k(u0) + u1 h_{k-1}(u0,u1), h_k(u0,u1,u2) = h_k(u0,u1) + u2 h_{k-1}(...)
     float a = 1.f, b = 1.f, c = 1.f;
     float re = 0.5f, im = 0.f;  // k = 0: 1 / 2!
-    const float inv_fact[8] = {1.f / 2.f, 1.f / 6.f, 1.f / 24.f, 1.f / 120.f, 1.f / 720.f, 1.f / 5040.f,
-                               1.f / 40320.f, 1.f / 362880.f};
+    float inv_fact = 0.5f;
 #pragma unroll
     for (int k = 1; k < 8; ++k) {
         a *= u0;
         b = fmaf(u1, b, a);
         c = fmaf(u2, c, b);
-        const float t = c * inv_fact[k];
+        inv_fact *= 1.f / (float)(k + 2);  // 1 / (k + 2)!, folded at compile time
+        const float t = c * inv_fact;
         switch (k & 3) {  // j^k
             case 0: re += t; break;
             case 1: im += t; break;
@@ -116,7 +121,7 @@ __device__ __forceinline__ float2 tri_canonical(float t0, float t1, float t2) {
             default: im -= t; break;
         }
     }
-    const float2 e = cis_reduced(tb);
+    const float2 e = cis_reduced(tb + th);
     return make_float2(re * e.x - im * e.y, re * e.y + im * e.x);
 }
 
@@ -190,21 +195,23 @@ __global__ void __launch_bounds__(TNT, 2) k_splat_tri(const TriRec *__restrict__
         __syncthreads();
         for (int k = 0; k < nc; ++k) {
             const TriConst &T = S[k];
+            // the row's share of the four affine forms, once per (triangle, thread)
+            const float bx = fmaf(T.mxy, dy, T.nu0x), by = fmaf(T.myy, dy, T.nu0y);
+            const float bg = fmaf(T.r3y, dy, T.g0), bt = fmaf(T.ty, dy, T.th0);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const float nx = fmaf(T.mxz, dz[h], fmaf(T.mxy, dy, fmaf(T.mxx, dx[h], T.nu0x)));
-                const float ny = fmaf(T.myz, dz[h], fmaf(T.myy, dy, fmaf(T.myx, dx[h], T.nu0y)));
+                const float nx = fmaf(T.mxz, dz[h], fmaf(T.mxx, dx[h], bx));
+                const float ny = fmaf(T.myz, dz[h], fmaf(T.myx, dx[h], by));
                 // vertex phases of e^{-j 2 pi nu . x} at (0,0), (1,0), (1,1): 0, -a, -(a + b)
-                const float a = 6.28318530717958647692f * nx, ab = 6.28318530717958647692f * (nx + ny);
-                const float p1 = -a, p2 = -ab;
+                const float p1 = -6.28318530717958647692f * nx, p2 = -6.28318530717958647692f * (nx + ny);
                 const float t0 = fminf(0.f, fminf(p1, p2)), t2 = fmaxf(0.f, fmaxf(p1, p2));
                 const float t1 = 0.f + p1 + p2 - t0 - t2;
-                const float2 tc = tri_canonical(t0, t1, t2);
-                const float jac = fabsf(fmaf(T.r3z, dz[h], fmaf(T.r3y, dy, fmaf(T.r3x, dx[h], T.g0)))) * ifz[h];
-                const float2 e = cis_reduced(fmaf(T.tz, dz[h], fmaf(T.ty, dy, fmaf(T.tx, dx[h], T.th0))));
-                const float s = T.w * jac;
-                acc_re[h] = fmaf(s, tc.x * e.x - tc.y * e.y, acc_re[h]);
-                acc_im[h] = fmaf(s, tc.x * e.y + tc.y * e.x, acc_im[h]);
+                const float th = fmaf(T.tz, dz[h], fmaf(T.tx, dx[h], bt));
+                const float2 v = tri_canonical_phased(t0, t1, t2, th);
+                const float jac = fabsf(fmaf(T.r3z, dz[h], fmaf(T.r3x, dx[h], bg))) * ifz[h];
+                const float sw = T.w * jac;
+                acc_re[h] = fmaf(sw, v.x, acc_re[h]);
+                acc_im[h] = fmaf(sw, v.y, acc_im[h]);
             }
         }
 #pragma unroll
