@@ -365,8 +365,8 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                                                      pair(-12582912.0f));
                         ts = __ffma2_rn(kt, pair(-6.28318530717958647692f), ts);
                     }
-                    // one row = the lane's two columns as one f32x2 pair; four rows in flight
-#pragma unroll 4
+                    // one row = the lane's two columns as one f32x2 pair; up to eight rows in flight
+#pragma unroll 8
                     for (int row = s_lo; row <= s_hi; ++row) {
                         const float2 dy = pair(fmaf((float)row, dfyf, dyb));
                         const float2 dyr = pair(fmaf((float)row, dfyf, dyrb));

@@ -160,7 +160,7 @@ def test_autograd_refocus_loss_matches_oracle():
     _cmp({k: p[k].grad for k in GROUPS}, ref)
 
 
-@pytest.mark.parametrize("cfg", ["c4_differentiable", "headline_1m_1080p_3l"])
+@pytest.mark.parametrize("cfg", ["c4_differentiable", "headline_1m_1080p_3l", "c2_precision_at_scale"])
 def test_full_size_backward_sampled_gaussians(cfg):
     sc, slm = config_scene(cfg)
     G = cotangent(21, slm)

@@ -361,6 +361,35 @@ def test_isotropic_point_gaussians():
     assert max(per_lambda_rel(rot, got)) < 1e-5
 
 
+def test_isotropic_points_tab3_shape():
+    # 15k isotropic point Gaussians (2 px, no rotation) at 1024x1280, 520 nm: sampled spectrum parity
+    # and the forward time (the point-cloud CGH of Tab. 3's comparison takes 2.47 s there)
+    slm = SLM(1024, 1280, 8e-6, 8e-6, (520e-9,))
+    rng = np.random.default_rng(22)
+    n = 15_000
+    mean = np.stack([rng.uniform(-0.5, 0.5, n) * slm.W * slm.pitch_x, rng.uniform(-0.5, 0.5, n) * slm.H * slm.pitch_y,
+                     rng.uniform(1e-3, 5e-3, n)], 1)
+    s = (2 * slm.pitch_x * np.exp(rng.normal(0.0, 0.3, n))).astype(np.float32)
+    quat = np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1))
+    sc = make_scene(mean, quat, np.stack([s, s], 1), rng.uniform(0.2, 1.0, n).astype(np.float32),
+                    rng.uniform(0.2, 1.0, (n, 1)).astype(np.float32))
+    g = dev(sc)
+    S = gws.Slm.of(slm)
+    u = gws.forward(g, S, domain=gws.DOMAIN_SPECTRUM)
+    lam, r, c = _samples(slm, 200, 23)
+    got = u[torch.as_tensor(lam, dtype=torch.long), torch.as_tensor(r, dtype=torch.long),
+            torch.as_tensor(c, dtype=torch.long)].cpu().numpy()
+    assert rel_l2(got, O.spectrum_at(sc, slm, lam, r, c)) < TOLMX
+    out = gws.forward(g, S)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    gws.forward(g, S, out=out)
+    e1.record()
+    e1.synchronize()
+    print(f"isotropic points, 15k @ 1024x1280 (forward to the field): {e0.elapsed_time(e1):.1f} ms")
+
+
 def test_precision_at_scale_3840x2160():
     """1M Gaussians on random surfaces at 3840x2160 x 3 wavelengths, 3.74 um pitch: the mixed path
     against the oracle at sampled frequencies (all Gaussians), and against the FP64 GPU path over
