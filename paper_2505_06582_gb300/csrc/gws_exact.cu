@@ -144,21 +144,31 @@ __global__ void k_fill(float *__restrict__ p, long long n, float v) {
 // uscale = dfx dfy (-1)^(H/2 + W/2))
 __global__ void k_exact_mask(float2 *__restrict__ U, float *__restrict__ Tm, ExactBatch E, int nb, int L, long long hw,
                              float t_eps, float t_bin, float uscale) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= hw * L) return;
-    const int l = (int)(idx / hw);
-    const long long pix = idx % hw;
+    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = blockIdx.y;
+    if (pix >= hw) return;
+    const long long idx = (long long)l * hw + pix;
     float T = Tm[idx];
     const float au = fabsf(uscale);
-    for (int k = 0; k < nb; ++k) {
-        float2 *up = U + ((size_t)k * L + l) * hw + pix;
-        const float2 u = *up;
-        const float s = E.co[k * L + l] * T * uscale;
-        *up = make_float2(s * u.x, s * u.y);
-        float a = E.ok[k] * au * sqrtf(u.x * u.x + u.y * u.y);
-        if (!(a > t_eps)) a = 0.f;
-        if (t_bin > 0.f) a = a > t_bin ? 1.f : 0.f;
-        T *= 1.f - a;
+    const size_t kstride = (size_t)L * hw;
+    float2 *base = U + idx;
+    constexpr int KB = 8;  // fields loaded ahead of their masking (the loads do not wait on the stores)
+    for (int k0 = 0; k0 < nb; k0 += KB) {
+        float2 u[KB];
+#pragma unroll
+        for (int j = 0; j < KB; ++j)
+            if (k0 + j < nb) u[j] = base[(size_t)(k0 + j) * kstride];
+#pragma unroll
+        for (int j = 0; j < KB; ++j) {
+            const int k = k0 + j;
+            if (k >= nb) break;
+            const float sc = E.co[k * L + l] * T * uscale;
+            base[(size_t)k * kstride] = make_float2(sc * u[j].x, sc * u[j].y);
+            float a = E.ok[k] * au * sqrtf(u[j].x * u[j].x + u[j].y * u[j].y);
+            if (!(a > t_eps)) a = 0.f;
+            if (t_bin > 0.f) a = a > t_bin ? 1.f : 0.f;
+            T *= 1.f - a;
+        }
     }
     Tm[idx] = T;
 }
@@ -360,7 +370,7 @@ cudaError_t launch_single_spectra(const ExactBatch &E, int nb, int L, int H, int
 
 cudaError_t launch_exact_mask(float2 *U, float *T, const ExactBatch &E, int nb, int L, long long hw, float t_eps,
                               float t_bin, float uscale, cudaStream_t s) {
-    k_exact_mask<<<nblk(hw * L, 256), 256, 0, s>>>(U, T, E, nb, L, hw, t_eps, t_bin, uscale);
+    k_exact_mask<<<dim3(nblk(hw, 256), (unsigned)L), 256, 0, s>>>(U, T, E, nb, L, hw, t_eps, t_bin, uscale);
     count_launches(1);
     return cudaGetLastError();
 }
