@@ -276,6 +276,12 @@ def run_ours(args):
         launches += gws.last_launch_count()
         t_splat = gws.kernel_time_ms(gws.TIMER_SPLAT_FWD) if timed_kernels else None
         t_fft = gws.kernel_time_ms(gws.TIMER_FFT) if timed_kernels else None
+        # everything of the forward call before the splat and after it but the FFT stage: validation,
+        # depth sort, transmittance, footprints and binning, records, the per-pixel table
+        t_prep = None
+        if timed_kernels:
+            t_tot = gws.kernel_time_ms(gws.TIMER_TOTAL)
+            t_prep = t_tot - t_splat - t_fft if t_tot > 0 else None
         gws.encode(field, S, out=phase, workspace=ws, **kw)
         launches += gws.last_launch_count()
         t_enc = gws.kernel_time_ms(gws.TIMER_ENCODE) if timed_kernels else None
@@ -287,7 +293,7 @@ def run_ours(args):
         if front is not None and timed_kernels:
             fe1.synchronize()
             t_front = fe0.elapsed_time(fe1)
-        return launches, t_splat, t_fft, t_enc, t_bwd, t_front
+        return launches, t_splat, t_fft, t_enc, t_bwd, t_front, t_prep
 
     step(False)
     torch.cuda.synchronize()
@@ -301,12 +307,13 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    times, splat_ms, fft_ms, enc_ms, bwd_ms, front_ms, launches = [], [], [], [], [], [], 0
+    times, splat_ms, fft_ms, enc_ms, bwd_ms, front_ms, prep_ms, launches = [], [], [], [], [], [], [], 0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
         flush.zero_()
         e0.record(stream)
-        n_l, ts, tf, te, tb, tfe = step(True)
+        n_l, ts, tf, te, tb, tfe, tp = step(True)
+        prep_ms.append(tp)
         if tfe is not None:
             front_ms.append(tfe)
         e1.record(stream)
@@ -373,6 +380,8 @@ def run_ours(args):
     sm_mhz = clk.get("sm_mhz") or 1440.0
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     dom_ms = {"splat_fwd": splat, "fft": statistics.median(fft_ms), "encode": statistics.median(enc_ms)}
+    if all(t is not None for t in prep_ms):
+        dom_ms["prep"] = statistics.median(prep_ms)
     if bwd_ms:
         dom_ms["splat_bwd"] = statistics.median(bwd_ms)
     full_size = args.workload == WORKLOAD and not fp64 and args.n is None and args.blend == "oit"
