@@ -16,7 +16,7 @@
 
 namespace gws {
 
-constexpr int TTW = 32, TTH = 16, TNT = 256;  // 2 pixels (columns c, c + 16) per thread
+constexpr int TTW = 32, TTH = 16, TNT = 256;  // 2 pixels (columns c, c + 16) per thread, one f32x2 pair
 constexpr float TRI_SPREAD = 0.5f;
 
 __global__ void k_tri_prep(const double *__restrict__ v, const float *__restrict__ opacity,
@@ -125,6 +125,23 @@ __device__ __forceinline__ float2 tri_canonical_phased(float t0, float t1, float
     return make_float2(re * e.x - im * e.y, re * e.y + im * e.x);
 }
 
+// The thread's two pixels as one f32x2 pair (h = 0, 1): sin(h)/h as (num, den) per pixel
+__device__ __forceinline__ void sinc_frac2(float2 h, float2 &num, float2 &den) {
+    const float2 k = __fadd2_rn(__ffma2_rn(h, pair(0.15915494309189535f), pair(12582912.0f)), pair(-12582912.0f));
+    const float2 a = __ffma2_rn(k, pair(-6.28318530717958647692f), h);
+    const bool bx = h.x > 1e-4f, by = h.y > 1e-4f;
+    num = make_float2(bx ? sin_approx(a.x) : 1.f, by ? sin_approx(a.y) : 1.f);
+    den = make_float2(bx ? h.x : 1.f, by ? h.y : 1.f);
+}
+
+// e^{j x} of both pixels: x - 2 pi round(x / 2 pi) first
+__device__ __forceinline__ void cis2(float2 x, float2 &re, float2 &im) {
+    const float2 k = __fadd2_rn(__ffma2_rn(x, pair(0.15915494309189535f), pair(12582912.0f)), pair(-12582912.0f));
+    const float2 r = __ffma2_rn(k, pair(-6.28318530717958647692f), x);
+    re = make_float2(cos_approx(r.x), cos_approx(r.y));
+    im = make_float2(sin_approx(r.x), sin_approx(r.y));
+}
+
 struct TriConst {  // per (triangle, tile), FP32 except the anchor
     float nu0x, nu0y, mxx, mxy, mxz, myx, myy, myz;  // nu = nu0 + M (dx, dy, dz)
     float g0, r3x, r3y, r3z;                         // r3 . f = g0 + r3 . delta
@@ -132,7 +149,7 @@ struct TriConst {  // per (triangle, tile), FP32 except the anchor
     float w;
 };
 
-__global__ void __launch_bounds__(TNT, 2) k_splat_tri(const TriRec *__restrict__ rec, const float *__restrict__ wgt,
+__global__ void __launch_bounds__(TNT, 4) k_splat_tri(const TriRec *__restrict__ rec, const float *__restrict__ wgt,
                                                       long long n, int L, int H, int W, double dfx, double dfy,
                                                       InvLam il, int field_mode, int phase_match,
                                                       float2 *__restrict__ out) {
@@ -148,7 +165,8 @@ __global__ void __launch_bounds__(TNT, 2) k_splat_tri(const TriRec *__restrict__
     const double f0z = sqrt(fmax(k2 - (f0x * f0x + f0y * f0y), 0.0));
     const int tid = threadIdx.x;
     const int row = r_lo + tid / 16;
-    float dx[2], dz[2], ifz[2], acc_re[2] = {0.f, 0.f}, acc_im[2] = {0.f, 0.f};
+    float dx[2], dz[2], ifz[2];
+    float2 acc_re = make_float2(0.f, 0.f), acc_im = make_float2(0.f, 0.f);
     float sum_re[2] = {0.f, 0.f}, sum_im[2] = {0.f, 0.f}, cmp_re[2] = {0.f, 0.f}, cmp_im[2] = {0.f, 0.f};
     bool ok[2];
     const double fy = (double)(row - H / 2) * dfy;
@@ -193,38 +211,63 @@ __global__ void __launch_bounds__(TNT, 2) k_splat_tri(const TriRec *__restrict__
             T.w = wgt[(c0 + tid) * L + l];
         }
         __syncthreads();
+        const float2 dxp = make_float2(dx[0], dx[1]), dzp = make_float2(dz[0], dz[1]);
+        const float2 ifzp = make_float2(ifz[0], ifz[1]);
         for (int k = 0; k < nc; ++k) {
             const TriConst &T = S[k];
-            // the row's share of the four affine forms, once per (triangle, thread)
-            const float bx = fmaf(T.mxy, dy, T.nu0x), by = fmaf(T.myy, dy, T.nu0y);
-            const float bg = fmaf(T.r3y, dy, T.g0), bt = fmaf(T.ty, dy, T.th0);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const float nx = fmaf(T.mxz, dz[h], fmaf(T.mxx, dx[h], bx));
-                const float ny = fmaf(T.myz, dz[h], fmaf(T.myx, dx[h], by));
-                // vertex phases of e^{-j 2 pi nu . x} at (0,0), (1,0), (1,1): 0, -a, -(a + b)
-                const float p1 = -6.28318530717958647692f * nx, p2 = -6.28318530717958647692f * (nx + ny);
-                const float t0 = fminf(0.f, fminf(p1, p2)), t2 = fmaxf(0.f, fmaxf(p1, p2));
-                const float t1 = 0.f + p1 + p2 - t0 - t2;
-                const float th = fmaf(T.tz, dz[h], fmaf(T.tx, dx[h], bt));
-                const float2 v = tri_canonical_phased(t0, t1, t2, th);
-                const float jac = fabsf(fmaf(T.r3z, dz[h], fmaf(T.r3x, dx[h], bg))) * ifz[h];
-                const float sw = T.w * jac;
-                acc_re[h] = fmaf(sw, v.x, acc_re[h]);
-                acc_im[h] = fmaf(sw, v.y, acc_im[h]);
+            // the row's share of the four affine forms, once per (triangle, thread); then both
+            // pixels as one packed f32x2 pair
+            const float2 bx = pair(fmaf(T.mxy, dy, T.nu0x)), by = pair(fmaf(T.myy, dy, T.nu0y));
+            const float2 bg = pair(fmaf(T.r3y, dy, T.g0)), bt = pair(fmaf(T.ty, dy, T.th0));
+            const float2 nx = __ffma2_rn(pair(T.mxz), dzp, __ffma2_rn(pair(T.mxx), dxp, bx));
+            const float2 ny = __ffma2_rn(pair(T.myz), dzp, __ffma2_rn(pair(T.myx), dxp, by));
+            const float2 th = __ffma2_rn(pair(T.tz), dzp, __ffma2_rn(pair(T.tx), dxp, bt));
+            const float2 ga = __ffma2_rn(pair(T.r3z), dzp, __ffma2_rn(pair(T.r3x), dxp, bg));
+            // vertex phases of e^{-j 2 pi nu . x} at (0,0), (1,0), (1,1): 0, -a, -(a + b), sorted
+            const float2 p1 = __fmul2_rn(nx, pair(-6.28318530717958647692f));
+            const float2 p2 = __fmul2_rn(__fadd2_rn(nx, ny), pair(-6.28318530717958647692f));
+            const float2 t0 = make_float2(fminf(0.f, fminf(p1.x, p2.x)), fminf(0.f, fminf(p1.y, p2.y)));
+            const float2 t2 = make_float2(fmaxf(0.f, fmaxf(p1.x, p2.x)), fmaxf(0.f, fmaxf(p1.y, p2.y)));
+            const float2 t1 = __fadd2_rn(__fadd2_rn(p1, p2), make_float2(-(t0.x + t2.x), -(t0.y + t2.y)));
+            const float2 sp = __fadd2_rn(t2, make_float2(-t0.x, -t0.y));
+            float2 vre, vim;
+            if (sp.x > TRI_SPREAD && sp.y > TRI_SPREAD) {
+                // E[p,q] e^{j th} = e^{j ((p+q)/2 + th)} sinc((q-p)/2), one reciprocal per pixel
+                float2 n12, d12, n01, d01, c12r, c12i, c01r, c01i;
+                sinc_frac2(__fmul2_rn(__fadd2_rn(t2, make_float2(-t1.x, -t1.y)), pair(0.5f)), n12, d12);
+                sinc_frac2(__fmul2_rn(__fadd2_rn(t1, make_float2(-t0.x, -t0.y)), pair(0.5f)), n01, d01);
+                cis2(__ffma2_rn(pair(0.5f), __fadd2_rn(t1, t2), th), c12r, c12i);
+                cis2(__ffma2_rn(pair(0.5f), __fadd2_rn(t0, t1), th), c01r, c01i);
+                const float2 w12 = __fmul2_rn(n12, d01), w01 = __fmul2_rn(n01, d12);
+                const float2 q1 = __fmul2_rn(w01, c01r), q2 = __fmul2_rn(w01, c01i);
+                const float2 dr = __ffma2_rn(w12, c12r, make_float2(-q1.x, -q1.y));
+                const float2 di = __ffma2_rn(w12, c12i, make_float2(-q2.x, -q2.y));
+                const float2 den = __fmul2_rn(__fmul2_rn(d12, d01), sp);
+                const float2 inv = make_float2(__fdividef(1.f, den.x), __fdividef(1.f, den.y));
+                vre = __fmul2_rn(di, inv);  // (dr + j di) / (j sp) = (di - j dr) / sp
+                vim = __fmul2_rn(make_float2(-dr.x, -dr.y), inv);
+            } else {  // a pixel near the spectrum's centre: each pixel on its own branch
+                const float2 v0 = tri_canonical_phased(t0.x, t1.x, t2.x, th.x);
+                const float2 v1 = tri_canonical_phased(t0.y, t1.y, t2.y, th.y);
+                vre = make_float2(v0.x, v1.x);
+                vim = make_float2(v0.y, v1.y);
             }
+            const float2 sw = __fmul2_rn(pair(T.w), __fmul2_rn(make_float2(fabsf(ga.x), fabsf(ga.y)), ifzp));
+            acc_re = __ffma2_rn(sw, vre, acc_re);
+            acc_im = __ffma2_rn(sw, vim, acc_im);
         }
+        const float are[2] = {acc_re.x, acc_re.y}, aim[2] = {acc_im.x, acc_im.y};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {  // TwoSum-compensated merge of the chunk
-            float t = sum_re[h] + acc_re[h], bp = t - sum_re[h];
-            cmp_re[h] += (sum_re[h] - (t - bp)) + (acc_re[h] - bp);
+            float t = sum_re[h] + are[h], bp = t - sum_re[h];
+            cmp_re[h] += (sum_re[h] - (t - bp)) + (are[h] - bp);
             sum_re[h] = t;
-            t = sum_im[h] + acc_im[h];
+            t = sum_im[h] + aim[h];
             bp = t - sum_im[h];
-            cmp_im[h] += (sum_im[h] - (t - bp)) + (acc_im[h] - bp);
+            cmp_im[h] += (sum_im[h] - (t - bp)) + (aim[h] - bp);
             sum_im[h] = t;
-            acc_re[h] = acc_im[h] = 0.f;
         }
+        acc_re = acc_im = make_float2(0.f, 0.f);
     }
     if (row >= H) return;
     const long long hw = (long long)H * W;
