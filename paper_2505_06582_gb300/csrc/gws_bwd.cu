@@ -12,10 +12,10 @@
 // tile is one contiguous block per table, and a lane's two columns c and c + 32 of a row sit
 // side by side for the packed f32x2 arithmetic): G enters in polar form, as a factor of the
 // exponential and a shift of the phase, so conj(G) P0 costs no complex product.  It culls
-// each record exactly, and one warp
-// takes one record over the tile (lane = column pair, rows in a loop), accumulating 16 FP32
-// partial sums per column; these are reduced across the warp and merged per tile into 13
-// FP64 totals per record in shared memory:
+// each record exactly and hands the survivors to its warps through a shared counter; a warp
+// takes one record over the tile (lane = column pair, rows in a loop, the phase re-anchored
+// per 32-row segment), accumulating 16 FP32 partial sums per column; these are reduced across
+// the warp and merged per tile into 13 FP64 totals per record in shared memory:
 //   TA = sum R a' d,  TB = sum R b' d,  TG = sum sign(g) Re(P0) f,  TI = sum I f,  SI = sum I,
 // with P0 = conj(G) f_z^-1 2^-(a'^2+b'^2) e^{j phi},  R = |g| Re(P0),  I = |g| Im(P0),
 // g = r3.f, d = f - f_r.  A record's totals are only touched by the warp holding it in the
@@ -28,7 +28,7 @@ namespace gws {
 
 constexpr int BTW = 64, BTH = 64, BPX = BTW * BTH;
 constexpr int BSEG = 32;     // rows per phase segment (the phase is re-anchored at each segment's middle row)
-constexpr int BQ = BPX / 2;  // float4 column pairs per tile and array
+constexpr int BQ = BPX / 2;  // column pairs per tile (entries of each table)
 constexpr int BB = 128;   // records per work item
 constexpr int BNT = 256;  // threads per CTA
 constexpr int NTOT = 13;
