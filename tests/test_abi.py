@@ -123,3 +123,68 @@ def test_null_arguments_rejected_before_any_launch():
     assert lib.gws_forward(C.byref(ok), C.c_int64(3), C.byref(s), C.byref(o), C.c_void_p(256)) == 2
     # encode: null field
     assert lib.gws_encode(None, C.byref(s), C.byref(o), C.c_void_p(256), C.c_float(0)) == 1
+
+
+def test_triangle_entry_points_check_arguments_on_host():
+    lib = gws.load()
+    wl = (C.c_double * 2)(6.38e-7, 4.5e-7)
+    s = gws._Slm(32, 48, 8e-6, 8e-6, 2, wl)
+    out = C.c_size_t(0)
+    assert lib.gws_triangles_workspace_size(C.c_int64(10), C.byref(s), C.byref(_opts()), None) == 1
+    assert lib.gws_triangles_workspace_size(C.c_int64(-1), C.byref(s), C.byref(_opts()), C.byref(out)) == 1
+    assert lib.gws_triangles_workspace_size(C.c_int64(10), C.byref(s), C.byref(_opts(prec=0)), C.byref(out)) == 6
+    sizes = []
+    for n in (0, 100, 10000):  # spectrum domain: the size needs no cuFFT plan (no GPU here)
+        assert lib.gws_triangles_workspace_size(C.c_int64(n), C.byref(s), C.byref(_opts(domain=1)),
+                                                C.byref(out)) == 0
+        sizes.append(out.value)
+    assert sizes == sorted(sizes) and sizes[0] < sizes[-1]
+    t = gws._Triangles(256, 256, 256)
+    o = _opts(domain=1)
+    assert lib.gws_forward_triangles(C.byref(t), C.c_int64(3), C.byref(s), C.byref(o), None) == 1
+    null = gws._Triangles(0, 256, 256)
+    assert lib.gws_forward_triangles(C.byref(null), C.c_int64(3), C.byref(s), C.byref(o), C.c_void_p(256)) == 1
+    assert lib.gws_forward_triangles(C.byref(t), C.c_int64(3), C.byref(s), C.byref(o), C.c_void_p(256)) == 2
+    o.workspace, o.workspace_bytes = C.c_void_p(256 + 16), 1 << 30
+    assert lib.gws_forward_triangles(C.byref(t), C.c_int64(3), C.byref(s), C.byref(o), C.c_void_p(256)) == 2
+
+
+def _camera(**kw):
+    cam = gws._Camera()
+    view = kw.get("view", [1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0])
+    for k in range(12):
+        cam.view[k] = view[k]
+    cam.fx, cam.fy, cam.cx, cam.cy = kw.get("fx", 500.0), 500.0, 320.0, 240.0
+    cam.projection, cam.z_near = kw.get("projection", 0), 0.1
+    return cam
+
+
+@pytest.mark.parametrize("bad", [
+    dict(sh_degree=4), dict(sh_degree=-1), dict(sh_degree=2, sh_stride=5), dict(projection=7),
+    dict(view=[float("nan")] + [0.0] * 11), dict(fx=float("inf")),
+    dict(holo=[0.0, 1, 0, 0, 0.0, 0, 1, 0, 0.0, 0, 0, 1]),       # A's first column zero
+    dict(holo=[1.0, 2.0, 0, 0, 0.0, 0.0, 1, 0, 0.0, 0.0, 0, 1]),  # A's xy columns parallel
+    dict(n=-1),
+])
+def test_holographics_checks_arguments_on_host(bad):
+    lib = gws.load()
+    w = gws._WorldGaussians(256, 256, 256, 256, 256, bad.get("sh_degree", 0), bad.get("sh_stride", 0))
+    cam = _camera(**{k: v for k, v in bad.items() if k in ("view", "fx", "projection")})
+    holo = (C.c_double * 12)(*bad.get("holo", [1e-5, 0, 0, 0, 0, 1e-5, 0, 0, 0, 0, 1e-3, 5e-3]))
+    out = gws._GaussiansOut(256, 256, 256, 256, 256)
+    st = lib.gws_holographics(C.byref(w), C.c_int64(bad.get("n", 4)), C.byref(cam), holo, C.byref(_opts()),
+                              C.byref(out), C.c_void_p(256))
+    assert st == 1
+
+
+def test_holographics_rejects_null_pointers_on_host():
+    lib = gws.load()
+    w = gws._WorldGaussians(256, 256, 256, 256, 256, 0, 0)
+    cam = _camera()
+    holo = (C.c_double * 12)(1e-5, 0, 0, 0, 0, 1e-5, 0, 0, 0, 0, 1e-3, 5e-3)
+    out = gws._GaussiansOut(256, 256, 256, 256, 256)
+    args = [C.byref(w), C.c_int64(4), C.byref(cam), holo, C.byref(_opts()), C.byref(out), C.c_void_p(256)]
+    for i in (0, 2, 3, 4, 5):
+        a = list(args)
+        a[i] = None
+        assert lib.gws_holographics(*a) == 1, i
