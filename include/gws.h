@@ -163,7 +163,15 @@ typedef struct {
     int pc_l, pc_m;          /* PARTIAL_COHERENT: degree 0..3 and order -l..l of the kernel's SH; default 0, 0 */
     uint64_t pc_seed;        /* PARTIAL_COHERENT: seed of the random phases; default 0 */
     uint64_t pc_frame;       /* PARTIAL_COHERENT: frame index t (independent phases per frame); default 0 */
+    int pc_frames;           /* PARTIAL_COHERENT: frames pc_frame .. pc_frame + pc_frames - 1 in one call
+                                (0 or 1: one frame; at most GWS_MAX_PC_FRAMES).  field_out then holds
+                                pc_frames x n_lambda x H x W values, frame-major; each batch's fields on
+                                their own planes are computed once and shared by the frames (the
+                                workspace holds one more batch of fields and a kernel pattern per frame).
+                                Every frame equals the single-frame call with that pc_frame. */
 } gws_opts;
+
+#define GWS_MAX_PC_FRAMES 64
 
 /* Fills *o with the defaults listed above (OIT, MIXED, FIELD). */
 GWS_API void gws_opts_default(gws_opts *o);

@@ -111,7 +111,8 @@ struct Layout {
     size_t rec64, w64, fkey0, fkey1, fval0, fval1, rec, Rr, ikey0, ikey1, ival0, ival1, icount, invrec, gspec, bacc;
     size_t pixtab, gtiles, dT, tq;
     size_t ex_U, ex_T, ex_arr;
-    size_t pc_kappa, pc_ysum;  // partial coherence: the kernel pattern [L][H][W] and sum_f Y^2 [L]
+    size_t pc_kappa, pc_ysum;  // partial coherence: the kernel patterns [F][L][H][W] and sum_f Y^2 [F][L]
+    size_t ex_U2;              // partial coherence over F > 1 frames: one frame's copy of the batch's fields
     int ex_B;
     size_t cufft, total;
     int tiles_x, tiles_y, n_tiles, cfg;
@@ -139,6 +140,8 @@ static int default_cfg(const gws_opts *o, const gws_slm *slm) {
     auto it = g_tuned.find(std::make_tuple(slm->H, slm->W, slm->n_lambda));
     return it != g_tuned.end() ? it->second : 1;
 }
+
+static int pc_frames(const gws_opts *o) { return o->pc_frames > 1 ? o->pc_frames : 1; }
 
 static int exact_batch(const gws_opts *o) {
     int B = o->exact_batch > 0 ? o->exact_batch : 128;
@@ -210,7 +213,7 @@ static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *sl
         L->dT = P.take(sizeof(double) * n);
     }
     L->ex_U = L->ex_T = L->ex_arr = 0;
-    L->pc_kappa = L->pc_ysum = 0;
+    L->pc_kappa = L->pc_ysum = L->ex_U2 = 0;
     L->ex_B = 0;
     size_t fft_work = 0;
     const bool pc = o->blend == GWS_BLEND_PARTIAL_COHERENT;
@@ -220,8 +223,10 @@ static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *sl
         const size_t hw = (size_t)slm->H * slm->W;
         L->ex_U = P.take(sizeof(float) * 2 * (size_t)B * nl * hw);
         if (pc) {
-            L->pc_kappa = P.take(sizeof(float) * 2 * nl * hw);
-            L->pc_ysum = P.take(sizeof(double) * nl);
+            const size_t nf = (size_t)pc_frames(o);
+            L->pc_kappa = P.take(sizeof(float) * 2 * nf * nl * hw);
+            L->pc_ysum = P.take(sizeof(double) * nf * nl);
+            if (nf > 1) L->ex_U2 = P.take(sizeof(float) * 2 * (size_t)B * nl * hw);
         } else {
             L->ex_T = P.take(sizeof(float) * nl * hw);
         }
@@ -272,6 +277,7 @@ static gws_status check_opts(const gws_opts *o) {
         o->blend != GWS_BLEND_PARTIAL_COHERENT)
         return GWS_ERR_INVALID_ARG;
     if (o->pc_l < 0 || o->pc_l > 3 || o->pc_m < -o->pc_l || o->pc_m > o->pc_l) return GWS_ERR_INVALID_ARG;
+    if (o->pc_frames < 0 || o->pc_frames > GWS_MAX_PC_FRAMES) return GWS_ERR_INVALID_ARG;
     if (!(o->t_binarize >= 0.f && o->t_binarize < 1.f) || o->exact_batch < 0) return GWS_ERR_INVALID_ARG;
     if (o->prec != GWS_PREC_FP64 && o->prec != GWS_PREC_MIXED) return GWS_ERR_INVALID_ARG;
     if (o->domain != GWS_DOMAIN_FIELD && o->domain != GWS_DOMAIN_SPECTRUM) return GWS_ERR_INVALID_ARG;
@@ -524,40 +530,53 @@ static gws_status pc_forward(const gws_gaussians *scene, long long n, const gws_
     for (int l = 0; l < nl; ++l) il.v[l] = 1.0 / slm->wavelengths[l];
     Plan p;
     GS(get_plan(H, W, nl, 0, &p));
-    timer_mark(o, GWS_TIMER_SPLAT_FWD, 0, s);  // the kernel pattern and the batch loop
-    // the frame's kernel pattern: kappa(x) = sum_f K(f) e^{j 2 pi f . x}, normalised in launch_pc_apply
-    CU(cudaMemsetAsync(ysum, 0, sizeof(double) * nl, s));
-    CU(launch_pc_kernel(kappa, ysum, o->pc_l, o->pc_m, (unsigned long long)o->pc_seed,
-                        (unsigned long long)o->pc_frame, nl, H, W, dfx, dfy, il, s));
-    CU(launch_modulate(kappa, 0, nl, H, W, 1.0, 3, s));
-    GS(exec_fft(p, kappa, at<char>(o, L.cufft), 0, CUFFT_INVERSE, s));
-    CU(launch_modulate(kappa, 0, nl, H, W, 1.0, 0, s));
+    timer_mark(o, GWS_TIMER_SPLAT_FWD, 0, s);  // the kernel patterns and the batch loop
+    // each frame's kernel pattern: kappa(x) = sum_f K(f) e^{j 2 pi f . x}, normalised in launch_pc_apply
+    const int nf = pc_frames(o);
+    const size_t slab = (size_t)nl * hw;
+    CU(cudaMemsetAsync(ysum, 0, sizeof(double) * nl * nf, s));
+    for (int f = 0; f < nf; ++f) {
+        float2 *kf = kappa + (size_t)f * slab;
+        CU(launch_pc_kernel(kf, ysum + (size_t)f * nl, o->pc_l, o->pc_m, (unsigned long long)o->pc_seed,
+                            (unsigned long long)o->pc_frame + (unsigned long long)f, nl, H, W, dfx, dfy, il, s));
+        CU(launch_modulate(kf, 0, nl, H, W, 1.0, 3, s));
+        GS(exec_fft(p, kf, at<char>(o, L.cufft), 0, CUFFT_INVERSE, s));
+        CU(launch_modulate(kf, 0, nl, H, W, 1.0, 0, s));
+    }
     float2 *pixtab = at<float2>(o, L.pixtab);
     CU(launch_pixtab(nl, H, W, dfx, dfy, il, 64, 32, pixtab, s));  // the tiles of the accumulation
-    CU(cudaMemsetAsync(acc, 0, sizeof(float2) * (size_t)nl * hw, s));
+    CU(cudaMemsetAsync(acc, 0, sizeof(float2) * slab * nf, s));
     const bool even = ((H | W) & 1) == 0;
     const float sgn0 = ((H / 2 + W / 2) & 1) ? -1.f : 1.f;
     const float uscale = even ? (float)(dfx * dfy) * sgn0 : 1.f;
     const float vscale = even ? (float)(slm->pitch_x * slm->pitch_y) * sgn0 : 1.f;
+    // one frame works on the batch's fields in place; several frames share them (computed once per
+    // batch) and work on a copy each
+    float2 *V = nf > 1 ? at<float2>(o, L.ex_U2) : U;
     for (long long b0 = 0; b0 < n; b0 += B) {
         const int nb = (int)std::min<long long>(B, n - b0);
         CU(launch_exact_gather(F.sorted, b0, nb, scene, nl, E, 1, s));
         CU(launch_single_spectra(E, nb, nl, H, W, dfx, dfy, il, pixtab, U, s));
         GS(batch_fft(p, H, W, nl, nb, B, U, at<char>(o, L.cufft), CUFFT_INVERSE, s));
         if (!even) CU(launch_modulate(U, 0, nb * nl, H, W, dfx * dfy, 0, s));
-        CU(launch_pc_apply(U, kappa, ysum, E, nb, nl, hw, uscale, s));
-        if (!even) CU(launch_modulate(U, 0, nb * nl, H, W, 1.0, 1, s));
-        GS(batch_fft(p, H, W, nl, nb, B, U, at<char>(o, L.cufft), CUFFT_FORWARD, s));
-        if (!even) CU(launch_modulate(U, 0, nb * nl, H, W, slm->pitch_x * slm->pitch_y, 2, s));
-        CU(launch_pc_accum(U, acc, pixtab, E, nb, nl, H, W, dfx, dfy, il, o->phase_match ? 1 : 0, even ? 1 : 0, vscale,
-                           s));
+        for (int f = 0; f < nf; ++f) {
+            CU(launch_pc_apply(U, V, kappa + (size_t)f * slab, ysum + (size_t)f * nl, E, nb, nl, hw, uscale, s));
+            if (!even) CU(launch_modulate(V, 0, nb * nl, H, W, 1.0, 1, s));
+            GS(batch_fft(p, H, W, nl, nb, B, V, at<char>(o, L.cufft), CUFFT_FORWARD, s));
+            if (!even) CU(launch_modulate(V, 0, nb * nl, H, W, slm->pitch_x * slm->pitch_y, 2, s));
+            CU(launch_pc_accum(V, acc + (size_t)f * slab, pixtab, E, nb, nl, H, W, dfx, dfy, il,
+                               o->phase_match ? 1 : 0, even ? 1 : 0, vscale, s));
+        }
     }
     timer_mark(o, GWS_TIMER_SPLAT_FWD, 1, s);
     timer_mark(o, GWS_TIMER_FFT, 0, s);
     if (o->domain == GWS_DOMAIN_FIELD) {
-        CU(launch_modulate(acc, 0, nl, H, W, 1.0, 3, s));
-        GS(exec_fft(p, acc, at<char>(o, L.cufft), 0, CUFFT_INVERSE, s));
-        CU(launch_modulate(acc, 0, nl, H, W, dfx * dfy, 0, s));
+        for (int f = 0; f < nf; ++f) {
+            float2 *af = acc + (size_t)f * slab;
+            CU(launch_modulate(af, 0, nl, H, W, 1.0, 3, s));
+            GS(exec_fft(p, af, at<char>(o, L.cufft), 0, CUFFT_INVERSE, s));
+            CU(launch_modulate(af, 0, nl, H, W, dfx * dfy, 0, s));
+        }
     }
     timer_mark(o, GWS_TIMER_FFT, 1, s);
     timer_mark(o, GWS_TIMER_TOTAL, 1, s);

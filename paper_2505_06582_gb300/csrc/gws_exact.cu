@@ -327,8 +327,8 @@ __global__ void __launch_bounds__(256) k_pc_kernel(float2 *__restrict__ K, doubl
 }
 
 // grid (pixel blocks, k L + l): no index division per value
-__global__ void k_pc_apply(float2 *__restrict__ U, const float2 *__restrict__ kappa, const double *__restrict__ ysum,
-                           ExactBatch E, int nb, int L, long long hw, float uscale) {
+__global__ void k_pc_apply(const float2 *Uin, float2 *Uout, const float2 *__restrict__ kappa,
+                           const double *__restrict__ ysum, ExactBatch E, int nb, int L, long long hw, float uscale) {
     __shared__ float s_s;
     const int kl = blockIdx.y;  // k * L + l
     const int l = kl % L;
@@ -339,8 +339,8 @@ __global__ void k_pc_apply(float2 *__restrict__ U, const float2 *__restrict__ ka
     const float s = s_s;
     const float2 a = kappa[(size_t)l * hw + pix];
     const size_t idx = (size_t)kl * hw + pix;
-    const float2 u = U[idx];
-    U[idx] = make_float2(s * (u.x * a.x - u.y * a.y), s * (u.x * a.y + u.y * a.x));
+    const float2 u = Uin[idx];
+    Uout[idx] = make_float2(s * (u.x * a.x - u.y * a.y), s * (u.x * a.y + u.y * a.x));
 }
 
 static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -394,9 +394,9 @@ cudaError_t launch_pc_kernel(float2 *K, double *ysum, int sh_l, int sh_m, unsign
     return cudaGetLastError();
 }
 
-cudaError_t launch_pc_apply(float2 *U, const float2 *kappa, const double *ysum, const ExactBatch &E, int nb, int L,
-                            long long hw, float uscale, cudaStream_t s) {
-    k_pc_apply<<<dim3(nblk(hw, 256), nb * L), 256, 0, s>>>(U, kappa, ysum, E, nb, L, hw, uscale);
+cudaError_t launch_pc_apply(const float2 *Uin, float2 *Uout, const float2 *kappa, const double *ysum,
+                            const ExactBatch &E, int nb, int L, long long hw, float uscale, cudaStream_t s) {
+    k_pc_apply<<<dim3(nblk(hw, 256), nb * L), 256, 0, s>>>(Uin, Uout, kappa, ysum, E, nb, L, hw, uscale);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -55,9 +55,10 @@ cudaError_t launch_exact_gather(const unsigned *sorted, long long b0, int nb, co
 cudaError_t launch_pc_kernel(float2 *K, double *ysum, int sh_l, int sh_m, unsigned long long seed,
                              unsigned long long frame, int L, int H, int W, double dfx, double dfy,
                              const InvLam &il, cudaStream_t s);
-// w_k = c_k o_k u_k kappa / sqrt(ysum) in place, for the batch's fields U [nb][L][H][W]
-cudaError_t launch_pc_apply(float2 *U, const float2 *kappa, const double *ysum, const ExactBatch &E, int nb, int L,
-                            long long hw, float uscale, cudaStream_t s);
+// w_k = c_k o_k u_k kappa / sqrt(ysum) for the batch's fields [nb][L][H][W], from Uin into Uout
+// (the same buffer for one frame; another when several frames share the batch's fields)
+cudaError_t launch_pc_apply(const float2 *Uin, float2 *Uout, const float2 *kappa, const double *ysum,
+                            const ExactBatch &E, int nb, int L, long long hw, float uscale, cudaStream_t s);
 // the batch's one-Gaussian spectra (Eq. 10, c = o = T = 1, dense) with the centred pre-modulation,
 // U [nb][L][H][W]; pixtab: the natural-layout table for 64 x 32 tiles
 cudaError_t launch_single_spectra(const ExactBatch &E, int nb, int L, int H, int W, double dfx, double dfy,

@@ -53,7 +53,7 @@ class _Opts(C.Structure):
                 ("debug_flags", C.c_uint32), ("timeout_cycles", C.c_uint64), ("stream", C.c_void_p),
                 ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t), ("t_binarize", C.c_float),
                 ("exact_batch", C.c_int), ("pc_l", C.c_int), ("pc_m", C.c_int), ("pc_seed", C.c_uint64),
-                ("pc_frame", C.c_uint64)]
+                ("pc_frame", C.c_uint64), ("pc_frames", C.c_int)]
 
 
 class _GaussiansOut(C.Structure):
@@ -197,7 +197,7 @@ _WS = _Workspace()
 
 def make_opts(blend=BLEND_OIT, prec=PREC_MIXED, domain=DOMAIN_FIELD, phase_match=False, trunc_eps=1e-5,
               alpha_min=1.0 / 255.0, tile_cfg=0, debug_flags=0, timeout_cycles=2_000_000_000, stream=None,
-              t_binarize=0.0, exact_batch=0, pc_l=0, pc_m=0, pc_seed=0, pc_frame=0):
+              t_binarize=0.0, exact_batch=0, pc_l=0, pc_m=0, pc_seed=0, pc_frame=0, pc_frames=0):
     lib = load()
     o = _Opts()
     lib.gws_opts_default(C.byref(o))
@@ -206,6 +206,7 @@ def make_opts(blend=BLEND_OIT, prec=PREC_MIXED, domain=DOMAIN_FIELD, phase_match
     o.debug_flags, o.timeout_cycles = int(debug_flags), int(timeout_cycles)
     o.t_binarize, o.exact_batch = float(t_binarize), int(exact_batch)
     o.pc_l, o.pc_m, o.pc_seed, o.pc_frame = int(pc_l), int(pc_m), int(pc_seed), int(pc_frame)
+    o.pc_frames = int(pc_frames)
     if stream is None:
         stream = torch.cuda.current_stream()
     o.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -237,14 +238,19 @@ def prepare(slm: Slm, n_scenes=1, **kw):
 
 
 def forward(g: Gaussians, slm: Slm, out: torch.Tensor | None = None, workspace=None, **kw) -> torch.Tensor:
-    """u_SLM field (or spectrum with domain=DOMAIN_SPECTRUM), complex [L,H,W]."""
+    """u_SLM field (or spectrum with domain=DOMAIN_SPECTRUM), complex [L,H,W]; with
+    blend=BLEND_PARTIAL_COHERENT and pc_frames=F > 1, the F frames' fields [F,L,H,W]."""
     lib = load()
     slm = Slm.of(slm)
     g.check(slm.n_lambda)
     opts = make_opts(**kw)
     dt = torch.complex128 if opts.prec == PREC_FP64 else torch.complex64
+    frames = opts.pc_frames if opts.blend == BLEND_PARTIAL_COHERENT and opts.pc_frames > 1 else 0
+    shape = ((frames,) if frames else ()) + (slm.n_lambda, slm.H, slm.W)
     if out is None:
-        out = torch.empty((slm.n_lambda, slm.H, slm.W), dtype=dt, device=g.mean.device)
+        out = torch.empty(shape, dtype=dt, device=g.mean.device)
+    elif out.numel() < math.prod(shape) or not out.is_contiguous():
+        raise GwsError(1, f"out must be a contiguous tensor of at least {shape}")
     ws = _attach_ws(opts, [g.n], slm, g.mean.device, workspace)
     _check(lib.gws_forward(C.byref(g._c()), C.c_int64(g.n), C.byref(slm._c()), C.byref(opts),
                            C.c_void_p(out.data_ptr())), "gws_forward")

@@ -74,7 +74,7 @@ def test_bad_slm_rejected_on_host(bad):
 
 @pytest.mark.parametrize("bad", [dict(blend=5), dict(prec=2), dict(domain=9), dict(trunc_eps=0.0),
                                  dict(trunc_eps=1.5), dict(alpha_min=-0.1), dict(timeout_cycles=0),
-                                 dict(tile_cfg=99)])
+                                 dict(tile_cfg=99), dict(pc_frames=-1), dict(pc_frames=65)])
 def test_bad_options_rejected_on_host(bad):
     lib = gws.load()
     wl = (C.c_double * 1)(5e-7)

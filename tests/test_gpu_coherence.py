@@ -56,6 +56,25 @@ def test_partial_coherence_batches_and_phase_match():
         assert rel_l2(got[k], want[k]) < TOL
 
 
+@pytest.mark.parametrize("slm", [SLM(48, 64, 8e-6, 8e-6, (638e-9, 520e-9)), SLM(33, 45, 1.2e-6, 1e-6, (520e-9,))])
+def test_partial_coherence_frames_in_one_call(slm):
+    # pc_frames = 3 shares each batch's fields among the frames: every frame equals its own call
+    zr = (1e-3, 3e-3) if slm.pitch_x > 4e-6 else (20e-6, 80e-6)
+    sc = uniform_scene(31, 9, slm, z_range=zr, scale_median_px=3.0)
+    kw = dict(blend=gws.BLEND_PARTIAL_COHERENT, pc_l=1, pc_m=1, pc_seed=3, exact_batch=4)
+    g = gws.Gaussians.from_scene(sc, "cuda")
+    S = gws.Slm.of(slm)
+    multi = gws.forward(g, S, pc_frame=2, pc_frames=3, **kw).cpu().numpy()
+    assert multi.shape == (3, slm.n_lambda, slm.H, slm.W)
+    for f in range(3):
+        one = gws.forward(g, S, pc_frame=2 + f, **kw).cpu().numpy()
+        for k in range(slm.n_lambda):
+            assert rel_l2(multi[f, k], one[k]) < 1e-6, (f, k)
+    want = PC.field(sc, slm, 1, 1, 3, 3)
+    for k in range(slm.n_lambda):
+        assert rel_l2(multi[1, k], want[k]) < TOL
+
+
 def test_partial_coherence_frames_are_deterministic_and_independent():
     slm = SLM(32, 32, 8e-6, 8e-6, (520e-9,))
     sc = uniform_scene(13, 4, slm, z_range=(1e-3, 2e-3), scale_median_px=3.0)
@@ -99,6 +118,15 @@ def test_partial_coherence_tab3_frame_time():
     e1.record()
     e1.synchronize()
     print(f"partial coherence, 15k Gaussians @ 1024x1280, one frame: {e0.elapsed_time(e1):.1f} ms")
+    # four frames in one call share each batch's fields
+    multi = gws.forward(g, S, pc_frames=4, **kw)
+    torch.cuda.synchronize()
+    e0.record()
+    gws.forward(g, S, out=multi, pc_frames=4, **kw)
+    e1.record()
+    e1.synchronize()
+    print(f"partial coherence, 15k Gaussians @ 1024x1280, four frames in one call: {e0.elapsed_time(e1) / 4:.1f} ms per frame")
+    assert torch.isfinite(torch.view_as_real(multi)).all()
     assert torch.isfinite(torch.view_as_real(out)).all()
     # the frame's energy: with E|kappa|^2 = 1 the mean intensity is close to the coherent field's
     coh = gws.forward(g, S)
