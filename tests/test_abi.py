@@ -188,3 +188,28 @@ def test_holographics_rejects_null_pointers_on_host():
         a = list(args)
         a[i] = None
         assert lib.gws_holographics(*a) == 1, i
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # every ctypes mirror in the binding has the C struct's field offsets and size (gcc on the header)
+    pairs = [("gws_gaussians", gws._Gaussians), ("gws_slm", gws._Slm), ("gws_opts", gws._Opts),
+             ("gws_gaussians_out", gws._GaussiansOut), ("gws_triangles", gws._Triangles),
+             ("gws_world_gaussians", gws._WorldGaussians), ("gws_camera", gws._Camera)]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "gws.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    assert os.system(f"gcc -I{os.path.join(ROOT, 'include')} {src} -o {exe}") == 0
+    got = {}
+    for line in os.popen(str(exe)).read().splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, py in pairs:
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
