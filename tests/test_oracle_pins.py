@@ -533,3 +533,116 @@ def test_exact_awb_binarized_disk_hides_what_is_behind():
     assert rel_l2(got, only_front) < 1e-9
     # without the disk the rear Gaussian shows through (soft alpha)
     assert rel_l2(O.exact_awb(both, slm), only_front) > 1e-3
+
+
+# ---------------------------------------------------------------------------------------
+# phase matching (Sec. 4.1 reference wave; supplement, hardware setup: each wavefront's
+# phase matched) and the per-pixel Gaussian exponent
+# ---------------------------------------------------------------------------------------
+
+def _phase_match_scene():
+    """Five Gaussians: untilted and tilted, off-axis, at three depths."""
+    return make_scene([[0, 0, 1.3e-3], [40e-6, -24e-6, 2.77e-3], [-56e-6, 8e-6, 4.1e-3], [16e-6, 30e-6, 2.77e-3],
+                       [-8e-6, -40e-6, 1.3e-3]],
+                      [[1, 0, 0, 0], qaxis([0, 0, 1], 0.7), qaxis([1, 0.3, 0], 0.5), qaxis([0.2, 1, 0], 0.9),
+                       qaxis([1, 1, 0.5], 1.2)],
+                      [[20e-6, 14e-6], [16e-6, 24e-6], [18e-6, 12e-6], [22e-6, 19e-6], [15e-6, 15e-6]],
+                      [0.9, 0.5, 0.7, 0.35, 0.8], [[0.6, 0.4], [0.9, 0.2], [0.3, 0.8], [0.5, 0.5], [0.7, 0.1]])
+
+
+def test_phase_match_dc_value_is_real_and_the_closed_form():
+    """With phase matching the on-axis plane wave f = 0 (f_z = 1/lam, d = f - f_r = 0) carries no
+    phase: every Gaussian's DC value is real and positive, W 2 pi s_u s_v |r3_z| (Eq. 10 at f = 0:
+    |r3.f| / f_z = |r3_z|, exp(0) = 1), whatever its depth and lateral position.  Without it the same
+    value carries the propagation phase exp(-j 2 pi mu_z / lam) (H(f, -mu_z) at f = 0, Eq. 4)."""
+    slm = SLM(32, 40, 8e-6, 8e-6, (638e-9, 450e-9))
+    sc = _phase_match_scene()
+    matched = O.spectrum(sc, slm, phase_match=True)
+    plain = O.spectrum(sc, slm, phase_match=False)
+    r, c = slm.H // 2, slm.W // 2
+    for l, lam in enumerate(slm.wavelengths):
+        want = 0.0
+        want_plain = 0.0 + 0.0j
+        for i in range(sc.n):
+            r3z = rotmat(sc.quat[i])[2, 2]
+            v = sc.amp[i, l] * sc.opacity[i] * 2 * math.pi * sc.scale[i, 0] * sc.scale[i, 1] * abs(r3z)
+            want += v
+            want_plain += v * np.exp(-2j * math.pi * sc.mean[i, 2] / lam)
+        got = matched[l, r, c]
+        assert abs(got.imag) < 1e-12 * want and got.real > 0
+        assert abs(got.real - want) < 1e-12 * want
+        # the oracle reduces the ~6e3-cycle phase mod 1 in FP64 first: 1e-10 covers the direct exp here
+        assert abs(plain[l, r, c] - want_plain) < 1e-10 * want
+        # each Gaussian alone (three depths): real and positive at DC
+        for i in range(sc.n):
+            one = O.spectrum(sc.subset([i]), slm, phase_match=True)[l, r, c]
+            assert one.real > 0 and abs(one.imag) < 1e-12 * one.real
+
+
+def test_phase_match_removes_the_carrier_from_the_propagation():
+    """A Gaussian moved by dz along the axis: its matched spectrum changes by the carrier-free
+    propagator exp(-j 2 pi (f_z - 1/lam) dz) (the matched field keeps the reference wave's phase
+    fixed at the Gaussian), while the plain spectrum changes by H(f, -dz) = exp(-j 2 pi f_z dz);
+    and matched / plain = exp(+j 2 pi mu_z / lam) Gaussian by Gaussian."""
+    slm = SLM(24, 30, 8e-6, 8e-6, (520e-9,))
+    lam = slm.wavelengths[0]
+    FX, FY, FZ = grid_freqs(slm, lam)
+    sc = _phase_match_scene()
+    for i in range(sc.n):
+        one = sc.subset([i])
+        moved = sc.subset([i])
+        dz = 0.37e-3 + 0.11e-3 * i
+        moved.mean[0, 2] += dz
+        m0 = O.spectrum(one, slm, phase_match=True)[0]
+        m1 = O.spectrum(moved, slm, phase_match=True)[0]
+        p0 = O.spectrum(one, slm)[0]
+        p1 = O.spectrum(moved, slm)[0]
+        scale = np.abs(m0).max()
+        assert np.abs(m1 - m0 * np.exp(-2j * math.pi * (FZ - 1 / lam) * dz)).max() < 1e-9 * scale
+        assert np.abs(p1 - p0 * np.exp(-2j * math.pi * FZ * dz)).max() < 1e-9 * scale
+        assert np.abs(m0 - p0 * np.exp(2j * math.pi * one.mean[0, 2] / lam)).max() < 1e-10 * scale
+
+
+def test_phase_match_gradients_match_central_differences():
+    """The backward with phase matching (its extra dL/dmu_z term) against central differences."""
+    slm = SLM(20, 24, 8e-6, 8e-6, (638e-9, 450e-9))
+    u = uniform_scene(17, 3, slm, scale_median_px=2.0)
+    sc = make_scene(u.mean, u.quat, u.scale, u.opacity, u.amp)
+    G = random_field(5, (slm.n_lambda, slm.H, slm.W)) * 1e8
+    g = O.backward_spectrum(sc, slm, G, phase_match=True)
+
+    def loss(s):
+        return float(np.real(np.vdot(G, O.spectrum(s, slm, phase_match=True))))
+
+    for field, scale in (("mean", 1e-5), ("quat", 1.0), ("opacity", 1.0)):
+        arr = getattr(sc, field)
+        fd = np.zeros_like(arr)
+        for idx in np.ndindex(arr.shape):
+            # matched, the axial phase is 2 pi (f_z - 1/lam) mu_z (|.| < 2e3 /m here) and the lateral
+            # one 2 pi f_xy.mu_xy (|f_xy| < 6.3e4 /m): a 1e-10 m step keeps the truncation error < 3e-9
+            h = 1e-10 if field == "mean" else 1e-6 * (abs(arr[idx]) + scale)
+            sp, sm = sc.subset(np.arange(sc.n)), sc.subset(np.arange(sc.n))
+            getattr(sp, field)[idx] += h
+            getattr(sm, field)[idx] -= h
+            fd[idx] = (loss(sp) - loss(sm)) / (2 * h)
+        assert rel_l2(g[field], fd) < 1e-6, field
+
+
+def test_single_terms_exponent_is_minus_log_of_the_gaussian_factor():
+    """The exponent E the oracle reports per pixel (the footprint tests bound exp(-E) by the
+    truncation threshold) equals -ln of the same call's |term| with the amplitude factors of Eq. 10
+    divided out: |term| = 2 pi s_u s_v |r3.f| / f_z exp(-E)."""
+    slm = SLM(40, 48, 8e-6, 8e-6, (520e-9,))
+    lam = slm.wavelengths[0]
+    FX, FY, FZ = grid_freqs(slm, lam)
+    for q, s in ((qaxis([1, 0.2, 0], 0.6), (9e-6, 5e-6)), (qaxis([0, 0, 1], 0.3), (6e-6, 7e-6)),
+                 (qaxis([0.3, 1, 0.1], 1.1), (4e-6, 8e-6))):
+        mu = np.array([12e-6, -20e-6, 2.5e-3])
+        term, E = O.single_terms(mu, q, np.array(s), lam, slm.H, slm.W, slm.pitch_x, slm.pitch_y)
+        r3 = rotmat(q)[:, 2]
+        g = np.abs(r3[0] * FX + r3[1] * FY + r3[2] * FZ)
+        pref = 2 * math.pi * s[0] * s[1] * g / FZ
+        ok = (np.abs(term) > 1e-250) & (g > 1e-6 * FZ)
+        assert ok.sum() > 0.9 * ok.size
+        assert np.abs(E[ok] + np.log(np.abs(term[ok]) / pref[ok])).max() < 1e-9 * max(1.0, E[ok].max())
+        assert E.min() >= 0
