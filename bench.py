@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "holograms/s (1M Gaussians, 1920x1080, 3 λ) fwd & fwd+bwd; Gaussian·freq-px/s"
 WORKLOAD = "headline_1m_1080p_3l"
 # DRAM bytes (read + write) of one launch of each splat on the headline workload, from
-# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` (profiles/k_splat_*__headline_1m_1080p_3l.md)
+# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` of the kernels as they stand
 SPLAT_TRAFFIC_MB = 1553.2  # 1.48 GB read + 73.17 MB written
 BWD_TRAFFIC_MB = 688.1     # 393.88 MB read + 294.21 MB written (wavelength-major work items, 64x64 tiles)
 # Per (Gaussian, frequency) pair: the forward needs ex2, sin and cos on the MUFU (32, 16, 16 per
