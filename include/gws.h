@@ -231,8 +231,12 @@ GWS_API gws_status gws_encode(const void *field, const gws_slm *slm, const gws_o
  *   - Its scratch (one slot per wavelength for the maximum amplitude) is a fixed array of
  *     GWS_NOALLOC_MAX_LAMBDA slots inside the library; every GPU that loads the library holds
  *     it until the process exits.  More wavelengths -> GWS_ERR_INVALID_ARG.
- *   - The first call on a device looks up the array's device address (set-up, once per
- *     device, with that device current): make that first call before any stream capture.
+ *   - Each call made outside a stream capture looks up the array's device address on the
+ *     current device (so a context rebuilt after cudaDeviceReset is served too) and remembers
+ *     it; a call made while opts->stream is being captured uses the remembered address, so
+ *     the first call on a device must come before any capture (else GWS_ERR_CUDA).
+ *   - Argument checks are gws_encode's (same status for the same bad input), plus the limit
+ *     below.
  *   - All calls share the array and each clears it before use: calls that overlap on the GPU
  *     (other streams, other host threads) race and must be serialised by the caller.
  *   - Calls no cudaMalloc, cudaFree or allocating library routine. */

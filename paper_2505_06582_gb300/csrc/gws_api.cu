@@ -607,7 +607,9 @@ static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, in
     const size_t slice = (size_t)H * W * (dbl ? 16 : 8);
     CU(cudaMemsetAsync(at<char>(o, L.status), 0, 16, s));
     if (n_total == 0) {
-        for (int k = 0; k < n_scenes; ++k) CU(cudaMemsetAsync(out[k], 0, slice * nl, s));
+        // partial coherence writes pc_frames slabs of n_lambda x H x W (one per frame)
+        const size_t frames = o->blend == GWS_BLEND_PARTIAL_COHERENT ? (size_t)pc_frames(o) : 1;
+        for (int k = 0; k < n_scenes; ++k) CU(cudaMemsetAsync(out[k], 0, slice * nl * frames, s));
         return GWS_OK;
     }
     Front F;
@@ -710,6 +712,17 @@ static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, in
 
 }  // namespace gws
 
+namespace gws {
+// the argument checks of the encoding, shared by gws_encode and gws_encode_noalloc
+gws_status check_encode_args(const void *field, const gws_slm *slm, const gws_opts *opts, const float *phase_out,
+                             float amp_scale) {
+    GS(check_slm(slm));
+    GS(check_opts(opts));
+    if (!field || !phase_out || !std::isfinite(amp_scale)) return GWS_ERR_INVALID_ARG;
+    return GWS_OK;
+}
+}  // namespace gws
+
 using namespace gws;
 
 extern "C" {
@@ -800,9 +813,7 @@ gws_status gws_forward_batched(const gws_gaussians *scenes, const int64_t *n, in
 gws_status gws_encode(const void *field, const gws_slm *slm, const gws_opts *opts, float *phase_out,
                       float amp_scale) {
     t_launches = 0;
-    GS(check_slm(slm));
-    GS(check_opts(opts));
-    if (!field || !phase_out || !std::isfinite(amp_scale)) return GWS_ERR_INVALID_ARG;
+    GS(gws::check_encode_args(field, slm, opts, phase_out, amp_scale));
     Layout L;
     GS(plan_layout(0, 1, slm, opts, &L, false));
     if (amp_scale <= 0.f) {

@@ -22,19 +22,27 @@ std::mutex g_mu;
 void *g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of g_encode_scratch on the current device (host code cannot use the
-// symbol itself: on the host it names a stand-in, not device memory).  Looked up once per
-// device, with that device current.
-cudaError_t scratch_for_current_device(void **out) {
+// symbol itself: on the host it names a stand-in, not device memory).  Looked up with that
+// device current on every call made outside a stream capture (so a context rebuilt after
+// cudaDeviceReset gets its new address) and remembered per device; a call made while the
+// stream is being captured uses the remembered address, so the first call on a device must
+// come before any capture.
+cudaError_t scratch_for_current_device(cudaStream_t stream, void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_encode_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_ptr[dev] = p;
+    } else if (!g_scratch_ptr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;  // no address yet: the first call came under capture
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;
@@ -44,13 +52,12 @@ cudaError_t scratch_for_current_device(void **out) {
 
 extern "C" gws_status gws_encode_noalloc(const void *field, const gws_slm *slm, const gws_opts *opts,
                                          float *phase_out, float amp_scale) {
-    if (!slm || !opts || !field || !phase_out) return GWS_ERR_INVALID_ARG;
-    if (slm->n_lambda < 1 || slm->n_lambda > GWS_NOALLOC_MAX_LAMBDA) return GWS_ERR_INVALID_ARG;
-    if (slm->H < 1 || slm->W < 1 || (long long)slm->H * slm->W > (1ll << 31)) return GWS_ERR_INVALID_ARG;
-    if (opts->prec != GWS_PREC_FP64 && opts->prec != GWS_PREC_MIXED) return GWS_ERR_INVALID_ARG;
-    if (!(amp_scale == amp_scale) || amp_scale > 3.0e38f) return GWS_ERR_INVALID_ARG;
+    // the same checks as gws_encode, then the limit of the fixed scratch
+    const gws_status st = gws::check_encode_args(field, slm, opts, phase_out, amp_scale);
+    if (st != GWS_OK) return st;
+    if (slm->n_lambda > GWS_NOALLOC_MAX_LAMBDA) return GWS_ERR_INVALID_ARG;
     void *scratch = nullptr;
-    if (scratch_for_current_device(&scratch) != cudaSuccess) return GWS_ERR_CUDA;
+    if (scratch_for_current_device((cudaStream_t)opts->stream, &scratch) != cudaSuccess) return GWS_ERR_CUDA;
     // launch_encode clears the slots it uses before the max reduction (cudaMemsetAsync)
     cudaError_t e = gws::launch_encode(field, opts->prec == GWS_PREC_FP64, slm->n_lambda, slm->H, slm->W,
                                        static_cast<unsigned long long *>(scratch), (double)amp_scale, phase_out,

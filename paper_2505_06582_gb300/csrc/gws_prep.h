@@ -76,5 +76,9 @@ cudaError_t launch_exact_accum(const float2 *V, float2 *acc, const float2 *pixta
 
 cudaError_t launch_encode(const void *field, int prec64, int n_lambda, int H, int W, unsigned long long *amax2,
                           double amp_scale, float *out, cudaStream_t s);
+// argument checks of the encoding (grid, options, pointers, finite amp_scale), shared by
+// gws_encode and gws_encode_noalloc so that both return the same status for the same input
+gws_status check_encode_args(const void *field, const gws_slm *slm, const gws_opts *opts, const float *phase_out,
+                             float amp_scale);
 
 }  // namespace gws

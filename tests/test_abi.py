@@ -125,6 +125,27 @@ def test_null_arguments_rejected_before_any_launch():
     assert lib.gws_encode(None, C.byref(s), C.byref(o), C.c_void_p(256), C.c_float(0)) == 1
 
 
+@pytest.mark.parametrize("bad", [dict(amp=float("-inf")), dict(amp=float("nan")), dict(amp=float("inf")),
+                                 dict(pitch_x=0.0), dict(wl=-5e-7), dict(blend=7), dict(prec=3), dict(trunc_eps=0.0),
+                                 dict(field=None), dict(phase=None), dict(n_lambda=0), dict(H=0)])
+def test_encode_entry_points_return_the_same_status_for_bad_arguments(bad):
+    """gws_encode and gws_encode_noalloc share their argument checks (no GPU call is reached)."""
+    lib = gws.load()
+    wl = (C.c_double * 2)(*([bad.get("wl", 5e-7)] * 2))
+    s = gws._Slm(bad.get("H", 8), 8, bad.get("pitch_x", 8e-6), 8e-6, bad.get("n_lambda", 2), wl)
+    o = _opts()
+    for k in ("blend", "prec", "trunc_eps"):
+        if k in bad:
+            setattr(o, k, bad[k])
+    field = bad.get("field", 256)
+    phase = bad.get("phase", 256)
+    args = (C.c_void_p(field) if field else None, C.byref(s), C.byref(o), C.c_void_p(phase) if phase else None,
+            C.c_float(bad.get("amp", 1.0)))
+    a = lib.gws_encode(*args)
+    b = lib.gws_encode_noalloc(*args)
+    assert a == b == 1
+
+
 def test_triangle_entry_points_check_arguments_on_host():
     lib = gws.load()
     wl = (C.c_double * 2)(6.38e-7, 4.5e-7)

@@ -90,6 +90,12 @@ def test_partial_coherence_empty_and_arguments():
     slm = SLM(16, 16, 8e-6, 8e-6, (520e-9,))
     sc0 = uniform_scene(1, 0, slm)
     assert np.all(run(sc0, slm, 2, 1, 0, 0) == 0)
+    # several frames of an empty scene: every frame's slab is cleared (the output is [F, L, H, W])
+    g0 = gws.Gaussians.from_scene(sc0, "cuda")
+    dirty = torch.full((3, 1, 16, 16), complex(7.0, -3.0), dtype=torch.complex64, device="cuda")
+    got = gws.forward(g0, gws.Slm.of(slm), out=dirty, blend=gws.BLEND_PARTIAL_COHERENT, pc_l=1, pc_m=1,
+                      pc_frames=3).cpu().numpy()
+    assert got.shape == (3, 1, 16, 16) and np.all(got == 0)
     sc = uniform_scene(1, 3, slm)
     g = gws.Gaussians.from_scene(sc, "cuda")
     S = gws.Slm.of(slm)
