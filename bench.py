@@ -4,7 +4,9 @@ Workload: 1M Gaussians on random surfaces (seeded), 1920x1080 SLM, 8 um pitch, 3
 (638/520/450 nm).  One step = one pass of the whole hot path over the batch: validation and
 precompute, depth sort, footprint binning, the mixed-precision splat (Eq. 10 summed by
 Eq. 12), the centred inverse FFT, double-phase encoding and -- when the library provides it
--- the backward splat given a seeded cotangent of the field.
+-- the differentiable workload's loss (torch: the field refocused to z = 2, 5, 8 mm by the
+angular spectrum method against seeded intensity targets) and the backward splat given that
+loss's gradient with respect to the field.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -44,7 +46,29 @@ BWD_TRAFFIC_MB = 688.1     # 393.88 MB read + 294.21 MB written (wavelength-majo
 # products, 2 a'/b' products, 12 moments; G enters in polar form, the phase is reduced once per
 # (record, column)) -> 128 / 30 = 4.27 pairs/clk/SM, below its MUFU 6.4.
 FWD_PAIRS_PER_CLK = 6.4
+# A configuration that takes the cos of a fraction f of the pixels on the FP32 pipe (an 11 lane-op
+# polynomial with its reduction) needs 1/32 + 1/16 + (1 - f)/16 MUFU cycles and 14 + 11 f FP32
+# lane-ops per pair: its bound is the smaller of the two rates.
+def fwd_pairs_per_clk(cfg_desc) -> tuple[float, str]:
+    f = 0.0
+    if cfg_desc:
+        f = 2.0 * cfg_desc.get("cos_pairs_on_fp32", 0) / cfg_desc["px_per_thread"]
+    mufu = 1.0 / (1.0 / 32 + 1.0 / 16 + (1.0 - f) / 16)
+    fp32 = 128.0 / (14.0 + 11.0 * f)
+    if f == 0.0:
+        return FWD_PAIRS_PER_CLK, "MUFU bound (ex2 + sin + cos per pair)"
+    which = "MUFU" if mufu <= fp32 else "FP32"
+    return min(mufu, fp32), (f"{which} bound with the cos of {f:.2f} of the pixels on the FP32 pipe "
+                             f"(MUFU {mufu:.2f}, FP32 {fp32:.2f} pairs/clk/SM)")
+
+
 BWD_PAIRS_PER_CLK = 128.0 / 30.0
+# The generic per-pair counts of the hot-path survey (minimal formula, per-frequency terms amortised
+# over Gaussians): forward 23 FP32 issues + 3 MUFU -> min(128/23, 6.4) = 5.57 pairs/clk/SM; backward
+# the same 3 MUFU + 23 recompute + 2 x 14 accumulation lane-ops = 51 -> 128/51 = 2.51 pairs/clk/SM.
+FWD_PAIRS_PER_CLK_SURVEY = min(128.0 / 23.0, FWD_PAIRS_PER_CLK)
+BWD_PAIRS_PER_CLK_SURVEY = 128.0 / 51.0
+FOCAL_PLANES = (2e-3, 5e-3, 8e-3)  # refocus planes of the differentiable workload's loss (m)
 
 
 def parse():
@@ -72,6 +96,11 @@ def parse():
     p.add_argument("--batched", action="store_true",
                    help="the batched workload: 64 scenes of log-uniform size in [1k, 200k] Gaussians x 3 wavelengths "
                         "at 1920x1080, one CUDA-graph-captured gws_forward_batched call per step (forward only)")
+    p.add_argument("--seeded-cotangent", action="store_true",
+                   help="feed the backward a seeded complex cotangent instead of the refocus loss's gradient")
+    p.add_argument("--no-context", action="store_true",
+                   help="skip the context rows (plain FP64 path at 20k, the 100k differentiable step, the batched "
+                        "64-scene graph replay) timed after the main measurement")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
@@ -152,30 +181,36 @@ def aggregate_rate(world: int, ms_per_step: float) -> float:
     return world * 1000.0 / ms_per_step
 
 
-def cpu_baseline(scene, slm, seconds: float, seed=7):
-    """FP64 oracle on the host cores: sampled frequencies x all Gaussians, scaled to holograms/s."""
+def cpu_baseline(scene, slm, seconds: float, seed=7, keep_samples=False):
+    """FP64 oracle on the host cores: sampled frequencies x all Gaussians, scaled to holograms/s.
+    With keep_samples, also returns the sampled (wavelength, row, column, spectrum) arrays."""
     import oracle as O
     threads = O.num_threads()
     rng = np.random.default_rng(seed)
     k = 128
     total_pairs, t_used = 0, 0.0
+    samples = []
     while t_used < seconds * 0.5:
         lam = rng.integers(0, slm.n_lambda, k).astype(np.int32)
         r = rng.integers(0, slm.H, k).astype(np.int32)
         c = rng.integers(0, slm.W, k).astype(np.int32)
         t0 = time.perf_counter()
-        O.spectrum_at(scene, slm, lam, r, c)
+        vals = O.spectrum_at(scene, slm, lam, r, c)
         dt = time.perf_counter() - t0
         total_pairs += k * scene.n
         t_used += dt
         if dt < seconds * 0.1:
             k *= 2
+        samples.append((lam, r, c, vals))
     pairs_per_s = total_pairs / t_used
     holo = pairs_per_s / (scene.n * slm.H * slm.W * slm.n_lambda)
-    return {"value": holo, "unit": "holograms/s", "cores": threads, "kind": "oracle",
-            "sample": f"{total_pairs // scene.n} sampled (wavelength, frequency) spectrum values over all "
-                      f"{scene.n} Gaussians in {t_used:.1f} s ({pairs_per_s:.3g} Gaussian-frequency pairs/s); "
-                      f"scaled by N*H*W*L; the inverse DFT (O(HW(H+W)), < 0.1% of the pairs) is not timed"}
+    res = {"value": holo, "unit": "holograms/s", "cores": threads, "kind": "oracle",
+           "sample": f"{total_pairs // scene.n} sampled (wavelength, frequency) spectrum values over all "
+                     f"{scene.n} Gaussians in {t_used:.1f} s ({pairs_per_s:.3g} Gaussian-frequency pairs/s); "
+                     f"scaled by N*H*W*L; the inverse DFT (O(HW(H+W)), < 0.1% of the pairs) is not timed"}
+    if keep_samples:
+        return res, [np.concatenate([x[i] for x in samples]) for i in range(4)]
+    return res
 
 
 def run_reference(args):
@@ -206,6 +241,7 @@ def run_ours(args):
     import torch.distributed as dist
 
     from paper_2505_06582_gb300 import gws
+    from paper_2505_06582_gb300 import refocus
     from paper_2505_06582_gb300.scenes import config_scene, cotangent
 
     rank, world, local = dist_env()
@@ -252,12 +288,22 @@ def run_ours(args):
     # autotune the splat tile on a strided 10% sample of the scene (outside the timed region)
     sub = gws.Gaussians(*(getattr(g, k)[::10].contiguous() for k in ("mean", "quat", "scale", "opacity", "amp")))
     tile_cfg = gws.autotune(sub, S, workspace=ws) if not fp64 else 0
+    cfg_desc = gws.tile_configs().get(tile_cfg) if tile_cfg else None
+    fwd_per_clk, fwd_basis = fwd_pairs_per_clk(cfg_desc)
     field = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.complex128 if fp64 else torch.complex64, device=dev)
     phase = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.float32, device=dev)
     timers = dict(debug_flags=gws.DEBUG_TIME_KERNELS)
 
     fe0, fe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lo0, lo1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     cur = {"g": g}
+    # the differentiable workload's loss: refocus to z = 2, 5, 8 mm, seeded intensity targets (set up once)
+    use_loss = have_bwd and not args.seeded_cotangent
+    if use_loss:
+        Hz = refocus.transfer(slm, FOCAL_PLANES, dev)
+        gws.forward(g, S, out=field, workspace=ws, prec=prec, blend=blend, **pc_kw)
+        targets = refocus.seeded_targets(4, field, Hz)
+        loss_val = torch.zeros((), dtype=torch.float32, device=dev)
 
     def step(timed_kernels):
         kw = dict(timers) if timed_kernels else {}
@@ -285,15 +331,24 @@ def run_ours(args):
         gws.encode(field, S, out=phase, workspace=ws, **kw)
         launches += gws.last_launch_count()
         t_enc = gws.kernel_time_ms(gws.TIMER_ENCODE) if timed_kernels else None
-        t_bwd = None
+        t_bwd = t_loss = None
         if have_bwd:
-            gws.backward(g, S, cot, workspace=ws, **kw)
+            G = cot
+            if use_loss:
+                lo0.record(stream)
+                L, G = refocus.field_cotangent(field, Hz, targets)
+                loss_val.copy_(L)
+                lo1.record(stream)
+            gws.backward(g, S, G, workspace=ws, **kw)
             launches += gws.last_launch_count()
             t_bwd = gws.kernel_time_ms(gws.TIMER_SPLAT_BWD) if timed_kernels else None
+            if use_loss and timed_kernels:
+                lo1.synchronize()
+                t_loss = lo0.elapsed_time(lo1)
         if front is not None and timed_kernels:
             fe1.synchronize()
             t_front = fe0.elapsed_time(fe1)
-        return launches, t_splat, t_fft, t_enc, t_bwd, t_front, t_prep
+        return launches, t_splat, t_fft, t_enc, t_bwd, t_front, t_prep, t_loss
 
     step(False)
     torch.cuda.synchronize()
@@ -307,13 +362,15 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    times, splat_ms, fft_ms, enc_ms, bwd_ms, front_ms, prep_ms, launches = [], [], [], [], [], [], [], 0
+    times, splat_ms, fft_ms, enc_ms, bwd_ms, front_ms, prep_ms, loss_ms, launches = [], [], [], [], [], [], [], [], 0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
         flush.zero_()
         e0.record(stream)
-        n_l, ts, tf, te, tb, tfe, tp = step(True)
+        n_l, ts, tf, te, tb, tfe, tp, tl = step(True)
         prep_ms.append(tp)
+        if tl is not None:
+            loss_ms.append(tl)
         if tfe is not None:
             front_ms.append(tfe)
         e1.record(stream)
@@ -338,15 +395,19 @@ def run_ours(args):
         ("mean", "quat", "scale", "opacity", "amp")
     host = {k: getattr(src, k).cpu().pin_memory() for k in in_keys}
     cot_host = cot.cpu().pin_memory()
+    tgt_host = targets.cpu().pin_memory() if use_loss else None
+    tbuf = torch.empty_like(targets) if use_loss else None
+    loss_host = torch.empty((), dtype=torch.float32).pin_memory()
     phase_host = torch.empty(phase.shape, dtype=phase.dtype).pin_memory()
     dbuf = {k: torch.empty_like(getattr(src, k)) for k in host}
     cbuf = torch.empty_like(cot)
     grads_host = {k: torch.empty(getattr(g, k).shape, dtype=getattr(g, k).dtype).pin_memory()
                   for k in ("mean", "quat", "scale", "opacity", "amp")}
-    h2d = sum(v.numel() * v.element_size() for v in host.values()) + (cot_host.numel() * cot_host.element_size()
-                                                                       if have_bwd else 0)
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    if have_bwd:  # the step's other input: the loss's targets (or the seeded cotangent)
+        h2d += tgt_host.numel() * tgt_host.element_size() if use_loss else cot_host.numel() * cot_host.element_size()
     d2h = phase_host.numel() * phase_host.element_size() + (
-        sum(v.numel() * v.element_size() for v in grads_host.values()) if have_bwd else 0)
+        sum(v.numel() * v.element_size() for v in grads_host.values()) + (4 if use_loss else 0) if have_bwd else 0)
     e2e_times = []
     for _ in range(max(2, min(args.steps, 3))):
         flush.zero_()
@@ -364,8 +425,14 @@ def run_ours(args):
         gws.encode(field, S, out=phase, workspace=ws)
         phase_host.copy_(phase, non_blocking=True)
         if have_bwd:
-            cbuf.copy_(cot_host, non_blocking=True)
-            gr = gws.backward(gd, S, cbuf, workspace=ws, blend=blend)
+            if use_loss:
+                tbuf.copy_(tgt_host, non_blocking=True)
+                L, Gd = refocus.field_cotangent(field, Hz, tbuf)
+                loss_host.copy_(L, non_blocking=True)
+            else:
+                cbuf.copy_(cot_host, non_blocking=True)
+                Gd = cbuf
+            gr = gws.backward(gd, S, Gd, workspace=ws, blend=blend)
             for k in grads_host:
                 grads_host[k].copy_(gr[k], non_blocking=True)
         e1.record(stream)
@@ -384,14 +451,21 @@ def run_ours(args):
         dom_ms["prep"] = statistics.median(prep_ms)
     if bwd_ms:
         dom_ms["splat_bwd"] = statistics.median(bwd_ms)
+    if loss_ms:
+        dom_ms["refocus_loss"] = statistics.median(loss_ms)
     full_size = args.workload == WORKLOAD and not fp64 and args.n is None and args.blend == "oit"
 
-    def roof(kernel, kms, per_clk, basis, traffic_mb):
+    def roof(kernel, kms, per_clk, basis, traffic_mb, survey_per_clk=None, survey_basis=""):
         achieved = pairs / (kms * 1e-3)
         peak = n_sm * sm_mhz * 1e6 * per_clk
-        return {"kernel": kernel, "bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
-                "frac": achieved / peak, "traffic": None if traffic_mb is None else traffic_mb * 1e6,
-                "peak_basis": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median sampled) x {per_clk:.2f} pairs/clk/SM, " + basis}
+        r = {"kernel": kernel, "bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
+             "frac": achieved / peak, "traffic": None if traffic_mb is None else traffic_mb * 1e6,
+             "peak_basis": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median sampled) x {per_clk:.2f} pairs/clk/SM, " + basis}
+        if survey_per_clk is not None:
+            sp = n_sm * sm_mhz * 1e6 * survey_per_clk
+            r["survey_count"] = {"peak": sp / 1e9, "frac": achieved / sp, "per_clk": survey_per_clk,
+                                 "basis": survey_basis}
+        return r
 
     if args.blend in ("exact", "partial"):
         # the batch loop (one-Gaussian spectra, batched inverse FFT, mask or kernel product, batched
@@ -411,13 +485,17 @@ def run_ours(args):
                                    "note": "64 algorithmic bytes per (Gaussian, wavelength, pixel)"}}
     else:
         rooflines = {"splat_fwd": roof(
-            "k_splat_fp64" if fp64 else "k_splat_mixed", splat, FWD_PAIRS_PER_CLK,
-            "MUFU bound (ex2 + sin + cos per pair)" + (" (FP32/MUFU peak; the FP64 path runs on the FP64 pipe)" if fp64 else ""),
-            args.traffic_mb if args.traffic_mb is not None else (SPLAT_TRAFFIC_MB if full_size else None))}
+            "k_splat_fp64" if fp64 else "k_splat_mixed", splat, fwd_per_clk,
+            fwd_basis + (" (FP32/MUFU peak; the FP64 path runs on the FP64 pipe)" if fp64 else ""),
+            args.traffic_mb if args.traffic_mb is not None else (SPLAT_TRAFFIC_MB if full_size else None),
+            None if fp64 else FWD_PAIRS_PER_CLK_SURVEY,
+            "survey count: 23 FP32 issues + 3 MUFU per pair -> min(128/23, 6.4) pairs/clk/SM")}
     if bwd_ms:
         rooflines["splat_bwd"] = roof("k_splat_bwd", dom_ms["splat_bwd"], BWD_PAIRS_PER_CLK,
                                       "FP32 bound (30 lane-ops per pair at 128 lanes/clk/SM; MUFU bound 6.4)",
-                                      BWD_TRAFFIC_MB if full_size else None)
+                                      BWD_TRAFFIC_MB if full_size else None, BWD_PAIRS_PER_CLK_SURVEY,
+                                      "survey count: 3 MUFU + 23 recompute + 2 x 14 accumulation = 51 FP32 lane-ops "
+                                      "per pair -> 128/51 pairs/clk/SM")
     if front_ms:
         dom_ms["front_end"] = statistics.median(front_ms)
         # algorithmic bytes per Gaussian: mean 24 + quat 16 + scale 12 + 16 SH floats 64 read,
@@ -461,7 +539,8 @@ def run_ours(args):
                        "pitch_m": S.pitch_x, "blend": args.blend, "precision": args.prec,
                        "trunc_eps": None if fp64 else 1e-5,
                        "step": ("front_end+" if front is not None else "") + "forward+encode"
-                               + ("+backward" if have_bwd else ""), "tile_cfg": tile_cfg,
+                               + (("+refocus_loss(z=2,5,8mm)" if use_loss else "+seeded_cotangent") + "+backward"
+                                  if have_bwd else ""), "tile_cfg": tile_cfg, "tile_cfg_desc": cfg_desc,
                        "l2": "flushed before each timed step (512 MB write)", "parallelism": f"replicas x{world}"},
             "fwd_holograms_per_s": world * 1000.0 / fwd_ms if have_bwd else value,
             "pairs": {"dense_per_hologram": dense, "algorithmic_per_hologram": pairs,
@@ -476,24 +555,126 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(scene, slm, args.cpu_seconds)
+        line["cpu_baseline"], smp = cpu_baseline(scene, slm, args.cpu_seconds, keep_samples=True)
+        # parity of this workload's spectrum against the oracle values the baseline just computed (one
+        # more forward, outside the timed region): rel-L2 per wavelength over the sampled frequencies
+        spec = gws.forward(g, S, workspace=ws, prec=prec, blend=blend, domain=gws.DOMAIN_SPECTRUM, **pc_kw)
+        lam_i, r_i, c_i, ref = smp
+        got = spec[torch.as_tensor(lam_i.astype(np.int64), device=dev), torch.as_tensor(r_i.astype(np.int64), device=dev),
+                   torch.as_tensor(c_i.astype(np.int64), device=dev)].cpu().numpy().astype(np.complex128)
+        per = []
+        for l in range(S.n_lambda):
+            m = lam_i == l
+            per.append(float(np.linalg.norm(got[m] - ref[m]) / max(np.linalg.norm(ref[m]), 1e-300)) if m.any() else None)
+        line["parity"] = {"rel_l2_per_lambda": per, "wavelengths_nm": [round(w * 1e9, 1) for w in slm.wavelengths],
+                          "samples": int(lam_i.size), "against": "FP64 oracle (gwso_spectrum_at), same samples as "
+                          "cpu_baseline", "tolerance": 1e-6 if fp64 else 2e-4, "domain": "spectrum"}
+        del spec
+    if rank == 0 and world == 1 and not args.no_context and args.workload == WORKLOAD and args.n is None \
+            and not fp64 and args.blend == "oit" and front is None:
+        del ws
+        torch.cuda.empty_cache()
+        line["context"] = run_context(dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_batched(args):
-    """64 scenes x 3 wavelengths in one persistent splat launch, captured in a CUDA graph and replayed
-    once per step (forward: splat + inverse FFTs); holograms/s = 64 / step time."""
+def _event_ms(fn, stream, flush=None):
+    """CUDA-event time of fn() on the stream (L2 flushed first when a flush buffer is given)."""
+    import torch
+    if flush is not None:
+        flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_context(dev):
+    """One step each of the other workloads, timed in the same run (rank 0, after the headline):
+    the plain FP64 GPU path next to the mixed path at 20k Gaussians (1920x1080, 3 wavelengths), the
+    100k differentiable step (forward + encode + refocus loss + backward) and one CUDA-graph replay
+    of the batched 64-scene forward."""
+    import torch
+
+    from paper_2505_06582_gb300 import gws, refocus
+    from paper_2505_06582_gb300.scenes import config_scene
+
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    out = {}
+    # plain FP64 GPU path vs the mixed path at 20k Gaussians
+    sc, slm = config_scene("c1_slm_size")
+    S = gws.Slm.of(slm)
+    g = gws.Gaussians.from_scene(sc, dev)
+    ws = torch.empty(max(gws.workspace_size([g.n], S, gws.make_opts(prec=p)) for p in (gws.PREC_FP64, gws.PREC_MIXED)),
+                     dtype=torch.uint8, device=dev)
+    f64 = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.complex128, device=dev)
+    fmx = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.complex64, device=dev)
+    small = gws.Gaussians(*(getattr(g, k)[:64].contiguous() for k in ("mean", "quat", "scale", "opacity", "amp")))
+    gws.forward(small, S, out=f64, workspace=ws, prec=gws.PREC_FP64)  # module and plan warm-up
+    for _ in range(2):
+        gws.forward(g, S, out=fmx, workspace=ws, prec=gws.PREC_MIXED)
+    t_mx = _event_ms(lambda: gws.forward(g, S, out=fmx, workspace=ws, prec=gws.PREC_MIXED), stream, flush)
+    t_64 = _event_ms(lambda: gws.forward(g, S, out=f64, workspace=ws, prec=gws.PREC_FP64), stream, flush)
+    a, b = f64.cpu().numpy(), fmx.cpu().numpy().astype(np.complex128)
+    rel = [float(np.linalg.norm(b[l] - a[l]) / np.linalg.norm(a[l])) for l in range(S.n_lambda)]
+    dense = g.n * S.H * S.W * S.n_lambda
+    out["c1_20k_fp64_vs_mixed"] = {
+        "workload": "c1_slm_size: 20k Gaussians, 1920x1080, 3 wavelengths, forward (splat + inverse DFT)",
+        "fp64_ms": t_64, "mixed_ms": t_mx, "fp64_dense_pairs_per_s": dense / (t_64 * 1e-3),
+        "mixed_dense_pairs_per_s": dense / (t_mx * 1e-3), "speedup_mixed_over_fp64": t_64 / t_mx,
+        "mixed_vs_fp64_rel_l2_per_lambda": rel, "l2": "flushed before each call"}
+    del f64, fmx, ws, g
+    torch.cuda.empty_cache()
+    # the differentiable workload, one step
+    sc, slm = config_scene("c4_differentiable")
+    S = gws.Slm.of(slm)
+    g = gws.Gaussians.from_scene(sc, dev)
+    ws = torch.empty(gws.workspace_size([g.n], S, gws.make_opts()), dtype=torch.uint8, device=dev)
+    field = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.complex64, device=dev)
+    phase = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.float32, device=dev)
+    Hz = refocus.transfer(slm, FOCAL_PLANES, dev)
+    gws.forward(g, S, out=field, workspace=ws)
+    targets = refocus.seeded_targets(4, field, Hz)
+
+    def c4_step():
+        gws.forward(g, S, out=field, workspace=ws)
+        gws.encode(field, S, out=phase, workspace=ws)
+        _, G = refocus.field_cotangent(field, Hz, targets)
+        gws.backward(g, S, G, workspace=ws)
+
+    for _ in range(2):
+        c4_step()
+    t_c4 = statistics.median(_event_ms(c4_step, stream, flush) for _ in range(3))
+    out["c4_differentiable_step"] = {
+        "workload": "c4_differentiable: 100k Gaussians, 1920x1080, 3 wavelengths; forward + encode + refocus loss "
+                    "(z = 2, 5, 8 mm) + backward", "ms": t_c4, "holograms_per_s": 1000.0 / t_c4,
+        "l2": "flushed before each step"}
+    del field, phase, ws, g, Hz, targets
+    torch.cuda.empty_cache()
+    # the batched workload: one graph replay
+    t_b, pairs_b, n_scenes, n_tot, _ = batched_graph_ms(dev, warmup=1, steps=1, flush=flush)
+    out["c3_batched_graph"] = {
+        "workload": f"batched: {n_scenes} scenes of log-uniform [1k, 200k] Gaussians ({n_tot} in all) x 3 "
+                    "wavelengths, 1920x1080, one CUDA-graph replay of gws_forward_batched", "ms": t_b,
+        "holograms_per_s": n_scenes * 1000.0 / t_b, "algorithmic_pairs_per_s": pairs_b / (t_b * 1e-3),
+        "l2": "flushed before the replay"}
+    return out
+
+
+def batched_graph_ms(dev, warmup, steps, flush=None):
+    """Times graph replays of gws_forward_batched on the 64-scene workload: (median ms, footprint pairs,
+    scenes, Gaussians, kernel launches per replay)."""
     import torch
 
     from paper_2505_06582_gb300 import gws
     from paper_2505_06582_gb300.scenes import SLM, batched_scenes
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     slm = SLM(1080, 1920, 8e-6, 8e-6, (638e-9, 520e-9, 450e-9))
     scenes = batched_scenes(slm)
     gs = [gws.Gaussians.from_scene(sc, dev) for sc in scenes]
@@ -511,34 +692,40 @@ def run_batched(args):
     with torch.cuda.graph(graph):
         gws.forward_batched(gs, S, outs=outs, workspace=ws)
     launches = gws.last_launch_count()
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    if flush is None:
+        flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(warmup):
         graph.replay()
     torch.cuda.synchronize()
+    times = [_event_ms(graph.replay, stream, flush) for _ in range(steps)]
+    pairs = sum(gws.footprint_pairs(g, S, workspace=ws) for g in gs)
+    n_tot = sum(g.n for g in gs)
+    del graph, outs, ws
+    return statistics.median(times), pairs, len(gs), n_tot, launches
+
+
+def run_batched(args):
+    """64 scenes x 3 wavelengths in one persistent splat launch, captured in a CUDA graph and replayed
+    once per step (forward: splat + inverse FFTs); holograms/s = 64 / step time."""
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     clocks = ClockSampler(local)
     clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    times = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0.record(stream)
-        graph.replay()
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
+    ms, pairs, n_scenes, n_tot, launches = batched_graph_ms(dev, warmup=max(args.warmup, 3), steps=args.steps)
     clk = clocks.stop()
-    ms = statistics.median(times)
-    pairs = sum(gws.footprint_pairs(g, S, workspace=ws) for g in gs)
     sm_mhz = clk.get("sm_mhz") or 1440.0
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = n_sm * sm_mhz * 1e6 * FWD_PAIRS_PER_CLK
     ach = pairs / (ms * 1e-3)
-    line = {"metric": METRIC, "value": len(gs) * 1000.0 / ms, "unit": "holograms/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "batched_64_scenes_1k_200k_1080p_3l", "n_scenes": len(gs),
-                       "n_gaussians": sum(g.n for g in gs), "H": S.H, "W": S.W, "n_lambda": S.n_lambda,
+    line = {"metric": METRIC, "value": n_scenes * 1000.0 / ms, "unit": "holograms/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "batched_64_scenes_1k_200k_1080p_3l", "n_scenes": n_scenes,
+                       "n_gaussians": n_tot, "H": 1080, "W": 1920, "n_lambda": 3,
                        "step": "one graph replay of gws_forward_batched (splat + inverse FFTs)",
                        "l2": "flushed before each timed step (512 MB write)", "parallelism": "single GPU"},
             "roofline": {"kernel": "k_splat_mixed (whole graph timed)", "bound": "alu", "achieved": ach / 1e9,

@@ -73,7 +73,9 @@ typedef enum {
     GWS_ERR_CUDA = 3,        /* a CUDA / cuFFT call failed, or no device */
     GWS_ERR_NONFINITE = 4,   /* device status: NaN / Inf among the inputs */
     GWS_ERR_TIMEOUT = 5,     /* device status: a bounded wait gave up */
-    GWS_ERR_UNSUPPORTED = 6  /* combination not implemented (e.g. FP64 backward) */
+    GWS_ERR_UNSUPPORTED = 6, /* combination not implemented (e.g. FP64 backward) */
+    GWS_ERR_BOUNDS = 7       /* device status, bounds-checking build only: an index out of range
+                                (the access was skipped) or a workspace canary overwritten */
 } gws_status;
 
 typedef enum {
@@ -278,12 +280,19 @@ GWS_API gws_status gws_footprint_pairs(const gws_gaussians *g, int64_t n, const 
 /* Number of kernel launches the last forward / backward / encode issued (host counter). */
 GWS_API int gws_last_launch_count(void);
 
-/* Autotuner of the MIXED splat: runs each tile configuration (1: 64x32, 2: 32x32, 3: 128x16
- * frequencies per CTA tile; 4: 32x32 evaluating two records per iteration; 5: 32x32 at three
- * CTAs per SM) twice on this scene with field_scratch (complex64
- * [n_lambda][H][W]) as output, times the splat with CUDA events, and keeps the fastest for
- * this (H, W, n_lambda) in an in-process table used whenever opts.tile_cfg == 0.  Returns
- * its id in *best_cfg.  Synchronises the stream; not capturable. */
+/* Autotuner of the MIXED splat: runs each splat configuration (gws_tile_config lists them:
+ * frequency tile shape per CTA, pixels per thread, records per iteration, Gaussian records
+ * per bulk-copied chunk, ring depth, CTAs per SM) twice on this scene with field_scratch
+ * (complex64 [n_lambda][H][W]) as output, times the splat with CUDA events, and keeps the
+ * fastest for this (H, W, n_lambda) in an in-process table used whenever opts.tile_cfg == 0.
+ * Returns its id in *best_cfg.  Synchronises the stream; not capturable. */
+/* The splat configurations the autotuner searches (no counterpart in the paper; the benchmark spec's
+ * "tile shape and Gaussians per block").  Returns their number; for 1 <= id <= that number and
+ * desc != NULL writes desc[0..7] = tile width, tile height (frequencies), pixels per thread,
+ * records evaluated per iteration, Gaussian records per chunk, ring stages, CTAs per SM, pixel
+ * pairs per thread whose cos runs on the FP32 pipe.  Host only. */
+GWS_API int gws_tile_config(int id, int *desc);
+
 GWS_API gws_status gws_autotune(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
                         void *field_scratch, int *best_cfg);
 

@@ -106,7 +106,17 @@ static gws_status exec_fft(const Plan &p, void *data, void *work, int dbl, int d
 // workspace layout (one planner for the size query and for the calls)
 // ---------------------------------------------------------------------------------------
 
+#ifdef GWS_CHECK_BOUNDS
+// checking build: 64 bytes of canary words after every workspace sub-buffer
+constexpr size_t kCanaryBytes = 64;
+constexpr int kMaxCanaries = 64;
+#endif
+
 struct Layout {
+#ifdef GWS_CHECK_BOUNDS
+    size_t canary[kMaxCanaries];
+    int n_canary;
+#endif
     size_t status, queue, amax, gpre, ampc, dkey0, dkey1, dval0, dval1, skey0, skey1, hist, tsorted, tg, tdata;
     size_t rec64, w64, fkey0, fkey1, fval0, fval1, rec, Rr, ikey0, ikey1, ival0, ival1, icount, invrec, gspec, bacc;
     size_t pixtab, gtiles, dT, tq;
@@ -122,11 +132,24 @@ static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Planner {
     size_t cur = 0;
+#ifdef GWS_CHECK_BOUNDS
+    size_t canary[kMaxCanaries];
+    int n_canary = 0;
+    size_t take(size_t bytes) {
+        // the canary starts right after the buffer (16-byte granularity), then the usual alignment
+        const size_t o = cur;
+        const size_t end = o + ((std::max<size_t>(bytes, 16) + 15) & ~(size_t)15);
+        if (n_canary < kMaxCanaries) canary[n_canary++] = end;
+        cur = align_up(end + kCanaryBytes);
+        return o;
+    }
+#else
     size_t take(size_t bytes) {
         size_t o = cur;
         cur = align_up(cur + std::max<size_t>(bytes, 16));
         return o;
     }
+#endif
 };
 
 // tile configuration chosen by gws_autotune per grid class (H, W, n_lambda)
@@ -252,8 +275,54 @@ static gws_status plan_layout(long long n_total, int n_scenes, const gws_slm *sl
     }
     L->cufft = P.take(fft_work);
     L->total = P.cur;
+#ifdef GWS_CHECK_BOUNDS
+    L->n_canary = P.n_canary;
+    for (int i = 0; i < P.n_canary; ++i) L->canary[i] = P.canary[i];
+#endif
     return GWS_OK;
 }
+
+// Checking build: a call's workspace canaries are written when its guard is made (after the
+// workspace checks) and verified when the guard goes out of scope (every return path), on the
+// call's stream; an overwritten word sets ST_BOUNDS in the status word.  The product build's
+// guard does nothing.
+#ifdef GWS_CHECK_BOUNDS
+struct CanaryList {
+    int n;
+    unsigned long long off[kMaxCanaries];
+};
+__global__ void k_canary(unsigned char *ws, CanaryList c, int check, int *status) {
+    constexpr int words = (int)(kCanaryBytes / 4);
+    for (int i = threadIdx.x; i < c.n * words; i += blockDim.x) {
+        unsigned *w = reinterpret_cast<unsigned *>(ws + c.off[i / words]) + (i % words);
+        const unsigned pat = 0xC0DE5A5Au ^ ((unsigned)i * 2654435761u);
+        if (check) {
+            if (*w != pat) atomicOr(status, ST_BOUNDS);
+        } else {
+            *w = pat;
+        }
+    }
+}
+struct CanaryGuard {
+    const gws_opts *o;
+    CanaryList c;
+    size_t status;
+    cudaStream_t s;
+    CanaryGuard(const gws_opts *o_, const Layout &L, cudaStream_t s_) : o(o_), status(L.status), s(s_) {
+        c.n = L.n_canary;
+        for (int i = 0; i < L.n_canary; ++i) c.off[i] = L.canary[i];
+        k_canary<<<1, 256, 0, s>>>(static_cast<unsigned char *>(o->workspace), c, 0, nullptr);
+    }
+    ~CanaryGuard() {
+        k_canary<<<1, 256, 0, s>>>(static_cast<unsigned char *>(o->workspace), c, 1,
+                                   reinterpret_cast<int *>(static_cast<char *>(o->workspace) + status));
+    }
+};
+#else
+struct CanaryGuard {
+    CanaryGuard(const gws_opts *, const Layout &, cudaStream_t) {}
+};
+#endif
 
 // ---------------------------------------------------------------------------------------
 // argument checks
@@ -362,11 +431,11 @@ static gws_status run_front(const gws_gaussians *scenes, const int64_t *n, int n
     unsigned *dv0 = at<unsigned>(o, L.dval0), *dv1 = at<unsigned>(o, L.dval1);
     CU(launch_prep(T, nt, gp, at<float>(o, L.ampc), dk0, dv0, at<int>(o, L.status), s));
     unsigned *hist = at<unsigned>(o, L.hist);
-    CU(radix_sort<unsigned long long>(dk0, dk1, dv0, dv1, nt, 0, 64, hist, s));
+    CU(radix_sort<unsigned long long>(dk0, dk1, dv0, dv1, nt, 0, 64, hist, s, at<int>(o, L.status)));
     if (n_scenes > 1) {
         unsigned *sk0 = at<unsigned>(o, L.skey0), *sk1 = at<unsigned>(o, L.skey1);
         CU(launch_scene_key(gp, dv0, nt, sk0, s));
-        CU(radix_sort<unsigned>(sk0, sk1, dv0, dv1, nt, 0, 8, hist, s));
+        CU(radix_sort<unsigned>(sk0, sk1, dv0, dv1, nt, 0, 8, hist, s, at<int>(o, L.status)));
     }
     F->sorted = dv0;
     F->T_sorted = nullptr;
@@ -405,10 +474,11 @@ static gws_status run_records(const Front &F, const gws_slm *slm, const gws_opts
     const int drop = backward ? 0 : 1;
     CU(launch_foot_keys(gp, at<float>(o, L.ampc), F.sorted, F.T_sorted, F.S, n_rec, FP, drop, k0, v0, s));
     const int n_seg = F.S.n_scenes * F.S.n_lambda;
-    CU(radix_sort<unsigned long long>(k0, k1, v0, v1, n_rec, 0, 32 + seg_bits(n_seg), at<unsigned>(o, L.hist), s));
+    CU(radix_sort<unsigned long long>(k0, k1, v0, v1, n_rec, 0, 32 + seg_bits(n_seg), at<unsigned>(o, L.hist), s,
+                                      at<int>(o, L.status)));
     Rec *rec = at<Rec>(o, L.rec);
     CU(launch_gather(k0, v0, gp, at<float>(o, L.ampc), F.sorted, F.T_sorted, F.S, n_rec, FP, drop, backward, rec,
-                     at<float>(o, L.Rr), backward ? at<int>(o, L.invrec) : nullptr, s));
+                     at<float>(o, L.Rr), backward ? at<int>(o, L.invrec) : nullptr, at<int>(o, L.status), s));
     *rec_out = rec;
     return GWS_OK;
 }
@@ -600,6 +670,7 @@ static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, in
     GS(plan_layout(n_total, n_scenes, slm, o, &L, fft));
     GS(check_workspace(o, L));
     cudaStream_t s = (cudaStream_t)o->stream;
+    CanaryGuard guard(o, L, s);
     timers_reset(o);
     timer_mark(o, GWS_TIMER_TOTAL, 0, s);
     const int nl = slm->n_lambda, H = slm->H, W = slm->W;
@@ -637,6 +708,7 @@ static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, in
         for (int l = 0; l < nl; ++l) a.inv_lam[l] = 1.0 / slm->wavelengths[l];
         a.field_mode = fft ? 1 : 0;
         a.phase_match = o->phase_match ? 1 : 0;
+        a.status = at<int>(o, L.status);
         for (int k = 0; k < n_scenes; ++k) a.out[k] = out[k];
         timer_mark(o, GWS_TIMER_SPLAT_FWD, 0, s);
         CU(launch_splat_fp64(a, s));
@@ -653,7 +725,7 @@ static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, in
                         icount, s));
         const long long n_items = (long long)n_seg * L.n_tiles;
         CU(radix_sort<unsigned long long>(ik0, ik1, iv0, iv1, n_items, 0, 32 + seg_bits(n_seg), at<unsigned>(o, L.hist),
-                                          s));
+                                          s, at<int>(o, L.status)));
         CU(cudaMemsetAsync(at<int>(o, L.queue), 0, 16, s));
         // per-pixel (f_z - f0_z, log2(1/f_z)) of this configuration's tiles, once per call (FP64)
         InvLam il;
@@ -750,11 +822,22 @@ const char *gws_status_string(gws_status s) {
         case GWS_ERR_NONFINITE: return "GWS_ERR_NONFINITE";
         case GWS_ERR_TIMEOUT: return "GWS_ERR_TIMEOUT";
         case GWS_ERR_UNSUPPORTED: return "GWS_ERR_UNSUPPORTED";
+        case GWS_ERR_BOUNDS: return "GWS_ERR_BOUNDS";
     }
     return "GWS_ERR_UNKNOWN";
 }
 
 int gws_version(void) { return GWS_ABI_VERSION; }
+
+int gws_tile_config(int id, int *desc) {
+    const int n = n_tile_cfgs();
+    if (desc && id >= 1 && id <= n) {
+        const TileCfg c = tile_cfg(id);
+        const int v[8] = {c.tw, c.th, c.px, c.ru, c.chunk, c.stages, c.ctas, c.npoly};
+        for (int i = 0; i < 8; ++i) desc[i] = v[i];
+    }
+    return n;
+}
 
 int gws_last_launch_count(void) { return t_launches; }
 
@@ -837,6 +920,7 @@ gws_status gws_get_device_status(const gws_opts *opts) {
     CU(cudaMemcpyAsync(&h, opts->workspace, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     CU(cudaMemsetAsync(opts->workspace, 0, sizeof(int), s));
+    if (h & ST_BOUNDS) return GWS_ERR_BOUNDS;
     if (h & ST_NONFINITE) return GWS_ERR_NONFINITE;
     if (h & ST_TIMEOUT) return GWS_ERR_TIMEOUT;
     if (h & ST_BADVALUE) return GWS_ERR_INVALID_ARG;
@@ -853,6 +937,7 @@ gws_status gws_depth_order(const gws_gaussians *g, int64_t n, const gws_opts *op
     Layout L;
     GS(plan_layout(n, 1, &slm, opts, &L, false));
     GS(check_workspace(opts, L));
+    CanaryGuard guard(opts, L, (cudaStream_t)opts->stream);
     if (n == 0) return GWS_OK;
     cudaStream_t s = (cudaStream_t)opts->stream;
     CU(cudaMemsetAsync(at<char>(opts, L.status), 0, 16, s));
@@ -874,6 +959,7 @@ gws_status gws_transmittance(const gws_gaussians *g, int64_t n, const gws_opts *
     Layout L;
     GS(plan_layout(n, 1, &slm, opts, &L, false));
     GS(check_workspace(opts, L));
+    CanaryGuard guard(opts, L, (cudaStream_t)opts->stream);
     if (n == 0) return GWS_OK;
     cudaStream_t s = (cudaStream_t)opts->stream;
     CU(cudaMemsetAsync(at<char>(opts, L.status), 0, 16, s));
@@ -894,6 +980,7 @@ gws_status gws_footprints(const gws_gaussians *g, int64_t n, const gws_slm *slm,
     Layout L;
     GS(plan_layout(n, 1, slm, opts, &L, false));
     GS(check_workspace(opts, L));
+    CanaryGuard guard(opts, L, (cudaStream_t)opts->stream);
     if (n == 0) return GWS_OK;
     cudaStream_t s = (cudaStream_t)opts->stream;
     CU(cudaMemsetAsync(at<char>(opts, L.status), 0, 16, s));
@@ -934,6 +1021,7 @@ gws_status gws_footprint_pairs(const gws_gaussians *g, int64_t n, const gws_slm 
     Layout L;
     GS(plan_layout(n, 1, slm, opts, &L, false));
     GS(check_workspace(opts, L));
+    CanaryGuard guard(opts, L, (cudaStream_t)opts->stream);
     if (n == 0) return GWS_OK;
     cudaStream_t s = (cudaStream_t)opts->stream;
     CU(cudaMemsetAsync(at<char>(opts, L.status), 0, 16, s));
@@ -976,6 +1064,7 @@ gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, c
     Layout L;
     GS(plan_layout(n, 1, slm, opts, &L, fft));
     GS(check_workspace(opts, L));
+    CanaryGuard guard(opts, L, (cudaStream_t)opts->stream);
     cudaStream_t s = (cudaStream_t)opts->stream;
     timers_reset(opts);
     timer_mark(opts, GWS_TIMER_TOTAL, 0, s);
@@ -1041,6 +1130,7 @@ gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, c
     G.amp = out->amp;
     G.dT = sorted_t ? at<double>(opts, L.dT) : nullptr;
     G.phase_match = opts->phase_match ? 1 : 0;
+    G.status = at<int>(opts, L.status);
     for (int l = 0; l < nl; ++l) G.inv_lam[l] = il.v[l];
     CU(launch_grad_assemble(at<GPre>(opts, L.gpre), at<float>(opts, L.ampc), F.T_g, at<int>(opts, L.invrec),
                             at<double>(opts, L.bacc), g->quat, n, nl, G, s));

@@ -205,6 +205,10 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
         // wavelength-major: the CTAs in flight share one wavelength's tables in L2
         const int nblk = (int)((n + BB - 1) / BB);
         const int l = it / nblk, blk = it % nblk;
+        if (!in_bounds(l < A.segs.n_lambda, A.status)) {  // checking build only
+            __syncthreads();
+            continue;
+        }
         const long long seg_base = (long long)l * n;
         const long long k0 = (long long)blk * BB;
         const int nrec = (int)min((long long)BB, n - k0);
@@ -251,7 +255,10 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
         // overlaps its cull; the CTA's other resident CTA covers the rest of the wait
         for (int t = 0; t < n_t; ++t) {
             {
-                const size_t tile = (size_t)(S.ty0 + t / ntx) * A.tiles_x + (S.tx0 + t % ntx);
+                size_t tile = (size_t)(S.ty0 + t / ntx) * A.tiles_x + (S.tx0 + t % ntx);
+                if (!in_bounds(S.tx0 >= 0 && S.ty0 >= 0 && S.tx1 < A.tiles_x && S.ty1 < A.tiles_y && tile < ntiles,
+                               A.status))
+                    tile = 0;
 #pragma unroll
                 for (int i = 0; i < BQ / BNT; ++i) {
                     const int e = tid + BNT * i;
@@ -338,8 +345,10 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                 j = __shfl_sync(0xffffffffu, j, 0);
                 if (j >= n_surv) break;
                 const int k = S.list[j];
+                if (!in_bounds(k < nrec, A.status)) continue;
                 const int2 rr = S.rows[k];
                 const int row_lo = rr.x, row_hi = rr.y;
+                if (!in_bounds(row_lo >= 0 && row_hi < BTH, A.status)) continue;
                 const float4 Ar = S.sv[k][0], Br = S.sv[k][1], Gr = S.sv[k][2], Mr = S.sv[k][3];
                 const float2 ac = make_float2(fmaf(Ar.x, dx0, Ar.w), fmaf(Ar.x, dx1, Ar.w));
                 const float2 bc = make_float2(fmaf(Br.x, dx0, Br.w), fmaf(Br.x, dx1, Br.w));
@@ -442,7 +451,9 @@ __global__ void k_grad_assemble(const GPre *__restrict__ gp, const float *__rest
     double dmu[3] = {0, 0, 0}, G1[3] = {0, 0, 0}, G2[3] = {0, 0, 0}, G3[3] = {0, 0, 0};
     double dsu = 0, dsv = 0, dop = 0, dT = 0;
     for (int l = 0; l < L; ++l) {
-        const double *t = acc + (size_t)invrec[g * L + l] * NTOT;
+        const int ri = invrec[g * L + l];
+        if (!in_bounds(ri >= 0 && (long long)ri < n * L, G.status)) continue;
+        const double *t = acc + (size_t)ri * NTOT;
         const double c = ampc[g * L + l];
         const double Wl = kTwoPi * su * sv * c * o * T;
         double dr1p[3], dr2p[3], dW = 0;

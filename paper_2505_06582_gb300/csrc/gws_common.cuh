@@ -24,7 +24,20 @@ enum : int {
     ST_NONFINITE = 1,
     ST_BADVALUE = 2,
     ST_TIMEOUT = 4,
+    ST_BOUNDS = 8,  // bounds-checking build: an index out of range (access skipped) or a canary overwritten
 };
+
+// Bounds checks of the checking build (GWS_CHECK_BOUNDS): in_bounds(ok, status) records a failed
+// check in the status word and returns ok, so that the caller skips the access; the product
+// build compiles every check to `true`.
+#ifdef GWS_CHECK_BOUNDS
+__device__ __forceinline__ bool in_bounds(bool ok, int *status) {
+    if (!ok && status) atomicOr(status, ST_BOUNDS);
+    return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool in_bounds(bool, int *) { return true; }
+#endif
 
 // Per-Gaussian data after validation (concatenated over scenes, input order).
 struct alignas(16) GPre {

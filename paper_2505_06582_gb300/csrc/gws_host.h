@@ -16,7 +16,7 @@ size_t sort_hist_words(long long n);
 
 template <typename K>
 cudaError_t radix_sort(K *&keys, K *&keys_alt, unsigned *&vals, unsigned *&vals_alt, long long n, int begin_bit,
-                       int end_bit, unsigned *hist, cudaStream_t s);
+                       int end_bit, unsigned *hist, cudaStream_t s, int *status = nullptr);
 
 // ---- splat (forward) --------------------------------------------------------------------
 
@@ -38,7 +38,10 @@ __host__ __device__ inline long long seg_size(const Segs &S, int seg) {
 }
 
 struct TileCfg {
-    int id, tw, th;
+    int id, tw, th;   // configuration id, frequency tile width x height per CTA
+    int px, ru;       // pixels per thread, records evaluated per iteration
+    int chunk, stages, ctas;  // Gaussian records per bulk-copied chunk, ring depth, CTAs per SM
+    int npoly;        // pixel pairs per thread whose cos runs on the FP32 pipe (the rest on the MUFU)
 };
 int n_tile_cfgs();
 TileCfg tile_cfg(int id);  // id 1..n_tile_cfgs()
@@ -76,6 +79,7 @@ struct Splat64Args {
     double inv_lam[GWS_MAX_LAMBDA];
     int field_mode;
     int phase_match;
+    int *status;
     void *out[GWS_MAX_SCENES];
 };
 cudaError_t launch_splat_fp64(const Splat64Args &a, cudaStream_t s);
@@ -101,6 +105,7 @@ struct GradArgs {
     double *mean;
     float *quat, *scale, *opacity, *amp;
     double *dT;             // optional dL/dT_i (depth-sorted mode)
+    int *status;            // device status word (index checks of the checking build)
     int phase_match;
     double inv_lam[GWS_MAX_LAMBDA];
 };

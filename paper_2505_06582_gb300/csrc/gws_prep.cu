@@ -377,9 +377,18 @@ __device__ __forceinline__ Foot footprint(const float r1[3], const float r2[3], 
     return f;
 }
 
+// Rotation columns formed in FP64 and rounded once: in FP32, 1 - 2 (x^2 + y^2) loses the small
+// components (a near edge-on Gaussian's r3_z ~ 1e-5 came out ~5e-8 off, and the |r3.f| kink of
+// Eq. 10 makes the gradient through r3 jump when that moves pixels across r3.f = 0).
 __device__ __forceinline__ void cols_f32(const double qd[4], float r1[3], float r2[3], float r3[3]) {
-    float q[4] = {(float)qd[0], (float)qd[1], (float)qd[2], (float)qd[3]};
-    quat_cols<float>(q, r1, r2, r3);
+    double d1[3], d2[3], d3[3];
+    quat_cols<double>(qd, d1, d2, d3);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r1[k] = (float)d1[k];
+        r2[k] = (float)d2[k];
+        r3[k] = (float)d3[k];
+    }
 }
 
 // record slot k (segment-major, depth order inside a segment) -> (segment, sorted position)
@@ -431,13 +440,16 @@ __global__ void k_gather(const unsigned long long *__restrict__ key, const unsig
                          const GPre *__restrict__ gp, const float *__restrict__ ampc,
                          const unsigned *__restrict__ sorted, const double *__restrict__ T_sorted, Segs S,
                          long long n_rec, FootParams F, int drop_zero, int backward, Rec *__restrict__ rec,
-                         float *__restrict__ Rr, int *__restrict__ invrec) {
+                         float *__restrict__ Rr, int *__restrict__ invrec, int *status) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_rec) return;
     const int seg = (int)(key[k] >> 32);
+    const long long n_all = S.off[S.n_scenes];
+    if (!in_bounds(seg < S.n_scenes * S.n_lambda && (long long)val[k] < n_all, status)) return;
     const int l = seg % S.n_lambda;
     const long long p = val[k];
     const unsigned g = sorted[p];
+    if (!in_bounds((long long)g < n_all, status)) return;
     const GPre &G = gp[g];
     float r1[3], r2[3], r3[3];
     cols_f32(G.q, r1, r2, r3);
@@ -765,10 +777,10 @@ cudaError_t launch_foot_keys(const GPre *gp, const float *ampc, const unsigned *
 cudaError_t launch_gather(const unsigned long long *key, const unsigned *val, const GPre *gp, const float *ampc,
                           const unsigned *sorted, const double *T_sorted, const Segs &S, long long n_rec,
                           const FootParams &F, int drop_zero, int backward, Rec *rec, float *Rr, int *invrec,
-                          cudaStream_t s) {
+                          int *status, cudaStream_t s) {
     if (n_rec <= 0) return cudaSuccess;
     k_gather<<<nblk(n_rec, 256), 256, 0, s>>>(key, val, gp, ampc, sorted, T_sorted, S, n_rec, F, drop_zero, backward,
-                                               rec, Rr, invrec);
+                                               rec, Rr, invrec, status);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -26,7 +26,7 @@ cudaError_t launch_foot_keys(const GPre *gp, const float *ampc, const unsigned *
 cudaError_t launch_gather(const unsigned long long *key, const unsigned *val, const GPre *gp, const float *ampc,
                           const unsigned *sorted, const double *T_sorted, const Segs &S, long long n_rec,
                           const FootParams &F, int drop_zero, int backward, Rec *rec, float *Rr, int *invrec,
-                          cudaStream_t s);
+                          int *status, cudaStream_t s);
 cudaError_t launch_foot_inspect(const GPre *gp, long long n, float rho, float dzmax, float *out, cudaStream_t s);
 cudaError_t launch_items(const float *Rr, const Segs &S, int n_seg, int H, int W, int tw, int th, int tiles_x,
                          int n_tiles, double dfx, double dfy, unsigned long long *ikey, unsigned *ival, int *icount,

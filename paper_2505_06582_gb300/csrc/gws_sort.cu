@@ -77,7 +77,7 @@ template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
     k_sort_scatter(const K *__restrict__ keys_in, const unsigned *__restrict__ vals_in, K *__restrict__ keys_out,
                    unsigned *__restrict__ vals_out, long long n, int shift, const unsigned *__restrict__ offs,
-                   int nblocks) {
+                   int nblocks, int *status) {
     __shared__ unsigned s_off[256];
     __shared__ unsigned s_wc[kSortThreads / 32][257];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -99,8 +99,10 @@ __global__ void __launch_bounds__(kSortThreads)
         if (valid) {
             unsigned pos = s_off[d] + rank;
             for (int w = 0; w < warp; ++w) pos += s_wc[w][d];
-            keys_out[pos] = key;
-            vals_out[pos] = val;
+            if (in_bounds((long long)pos < n, status)) {
+                keys_out[pos] = key;
+                vals_out[pos] = val;
+            }
         }
         __syncthreads();
         {
@@ -125,13 +127,13 @@ size_t sort_hist_words(long long n) {
 
 template <typename K>
 cudaError_t radix_sort(K *&keys, K *&keys_alt, unsigned *&vals, unsigned *&vals_alt, long long n, int begin_bit,
-                       int end_bit, unsigned *hist, cudaStream_t s) {
+                       int end_bit, unsigned *hist, cudaStream_t s, int *status) {
     if (n <= 1) return cudaSuccess;
     const int nb = (int)((n + kSortTile - 1) / kSortTile);
     for (int shift = begin_bit; shift < end_bit; shift += 8) {
         k_sort_hist<K><<<nb, kSortThreads, 0, s>>>(keys, n, shift, hist, nb);
         k_sort_scan<<<1, 1024, 0, s>>>(hist, (long long)256 * nb);
-        k_sort_scatter<K><<<nb, kSortThreads, 0, s>>>(keys, vals, keys_alt, vals_alt, n, shift, hist, nb);
+        k_sort_scatter<K><<<nb, kSortThreads, 0, s>>>(keys, vals, keys_alt, vals_alt, n, shift, hist, nb, status);
         count_launches(3);
         K *tk = keys;
         keys = keys_alt;
@@ -144,8 +146,8 @@ cudaError_t radix_sort(K *&keys, K *&keys_alt, unsigned *&vals, unsigned *&vals_
 }
 
 template cudaError_t radix_sort<unsigned>(unsigned *&, unsigned *&, unsigned *&, unsigned *&, long long, int, int,
-                                          unsigned *, cudaStream_t);
+                                          unsigned *, cudaStream_t, int *);
 template cudaError_t radix_sort<unsigned long long>(unsigned long long *&, unsigned long long *&, unsigned *&,
-                                                    unsigned *&, long long, int, int, unsigned *, cudaStream_t);
+                                                    unsigned *&, long long, int, int, unsigned *, cudaStream_t, int *);
 
 }  // namespace gws

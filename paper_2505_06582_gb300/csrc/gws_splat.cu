@@ -50,13 +50,33 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
     s = t;
 }
 
+// cos of a phase within a few turns of zero on the FP32 pipe (both lanes of a pair): the nearest
+// whole turn is taken off with a two-part 2 pi (float(2 pi) and its remainder), then an even
+// degree-12 polynomial in r^2 gives cos(r), |r| <= pi.  The coefficients were fitted for this
+// kernel to cos on [-pi, pi] (least squares reweighted toward the minimax error; |error| of the
+// FP32 evaluation <= 4.4e-7, below sin/cos.approx's on the unreduced arguments).  It moves part of
+// the MUFU's load onto the FMA pipe.
+__device__ __forceinline__ float2 cos_poly2(float2 x) {
+    const float2 k = __fadd2_rn(__ffma2_rn(x, pair(0.15915494309189535f), pair(12582912.0f)), pair(-12582912.0f));
+    float2 r = __ffma2_rn(k, pair(-6.28318548202514648f), x);
+    r = __ffma2_rn(k, pair(1.74845553e-7f), r);
+    const float2 t = __fmul2_rn(r, r);
+    float2 p = __ffma2_rn(t, pair(1.7244632e-09f), pair(-2.7078977e-07f));
+    p = __ffma2_rn(p, t, pair(2.4769886e-05f));
+    p = __ffma2_rn(p, t, pair(-1.3887804e-03f));
+    p = __ffma2_rn(p, t, pair(4.1666489e-02f));
+    p = __ffma2_rn(p, t, pair(-4.9999988e-01f));
+    return __ffma2_rn(p, t, pair(1.0f));
+}
+
 // One listed record over this thread's PH pixel pairs (packed f32x2): the Gaussian factor and
 // the phase of Eq. 10 from the per-(record, tile) scalars sv[0..3], accumulated into acc.  The
 // linear forms are anchored at the thread's middle column (offset dxm from the tile's reference
 // frequency; the pixels sit at ddx from it), and the phase there is reduced to [-pi, pi] once per
 // record, so the per-pixel phase stays within |t_x ddx| + |t_z dz| + pi of zero and goes to
-// sin/cos unreduced (the argument error of sin.approx grows like 1.2e-7 |t|).
-template <int PH>
+// sin/cos unreduced (the argument error of sin.approx grows like 1.2e-7 |t|).  The cos of the
+// first NPOLY pairs runs on the FP32 pipe (cos_poly2) instead of the MUFU.
+template <int PH, int NPOLY>
 __device__ __forceinline__ void splat_record(const float4 *__restrict__ sv, float dy, float dxm, const float2 *ddx,
                                              const float2 *dz, const float2 *lfz, float2 *acc_re, float2 *acc_im) {
     const float4 Ar = sv[0], Br = sv[1], Gr = sv[2], Mr = sv[3];
@@ -78,19 +98,22 @@ __device__ __forceinline__ void splat_record(const float4 *__restrict__ sv, floa
         const float2 u = __ffma2_rn(a, a, __ffma2_rn(b, b, lfz[h]));
         const float2 amp = __fmul2_rn(g, make_float2(with_sign_of(ex2_approx(-u.x), g.x),
                                                      with_sign_of(ex2_approx(-u.y), g.y)));
-        acc_re[h] = __ffma2_rn(amp, make_float2(cos_approx(ang.x), cos_approx(ang.y)), acc_re[h]);
+        const float2 cs = h < NPOLY ? cos_poly2(ang) : make_float2(cos_approx(ang.x), cos_approx(ang.y));
+        acc_re[h] = __ffma2_rn(amp, cs, acc_re[h]);
         acc_im[h] = __ffma2_rn(amp, make_float2(sin_approx(ang.x), sin_approx(ang.y)), acc_im[h]);
     }
 }
 
 // RU: listed records evaluated per iteration (2: two independent accumulator sets for more
 // instruction-level parallelism; needs the register room of the 4-pixel configuration)
-template <int TW, int TH, int PX, int CHUNK, int STAGES, int RU, int MINB>
+template <int TW, int TH, int PX, int CHUNK, int STAGES, int RU, int MINB, int NPOLY>
 __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __grid_constant__ SplatArgs A) {
     constexpr int NT = (TW / PX) * TH;
     constexpr int NW = NT / 32;          // warps = row bands of the tile
     constexpr int RPW = 32 / (TW / PX);  // tile rows per warp
-    static_assert(CHUNK == NT && CHUNK % 32 == 0 && (TW / PX) <= 32 && 32 % (TW / PX) == 0, "chunk / tile shape");
+    // a chunk holds up to one record per thread (threads past the chunk cull nothing)
+    static_assert(CHUNK <= NT && CHUNK <= 256 && CHUNK % 32 == 0 && (TW / PX) <= 32 && 32 % (TW / PX) == 0,
+                  "chunk / tile shape");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Rec *s_rec = reinterpret_cast<Rec *>(smem_raw);
     float4 *s_sv = reinterpret_cast<float4 *>(smem_raw + sizeof(Rec) * STAGES * CHUNK);
@@ -120,8 +143,13 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
         if (it >= A.n_items) break;
         const unsigned item = A.items[it];
         const int seg = (int)(item / (unsigned)A.n_tiles), tile = (int)(item % (unsigned)A.n_tiles);
+        if (!in_bounds(seg < A.segs.n_scenes * A.segs.n_lambda, A.status)) {  // checking build only
+            __syncthreads();
+            continue;
+        }
         const int scene = seg / A.segs.n_lambda, l = seg % A.segs.n_lambda;
-        const int count = A.item_count[item];
+        int count = A.item_count[item];
+        if (!in_bounds(count >= 0 && count <= seg_size(A.segs, seg), A.status)) count = 0;
         const Rec *rbase = A.rec + seg_start(A.segs, seg);
         const int tx = tile % A.tiles_x, ty = tile / A.tiles_x;
         const int c_lo = tx * TW, r_lo = ty * TH;
@@ -262,17 +290,22 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
 
             // ---- the hot loop: every surviving record x this thread's PX pixels ----
             for (int v = 0; v < NW; ++v) {
-                const int cnt = s_cnt[warp][v];
+                int cnt = s_cnt[warp][v];
                 const unsigned char *lst = s_list + (warp * NW + v) * 32;
+#ifdef GWS_CHECK_BOUNDS
+                // every listed slot must hold a record of this chunk
+                for (int i = 0; i < cnt; ++i)
+                    if (!in_bounds(lst[i] < nrec, A.status)) cnt = 0;
+#endif
                 int i = 0;
                 if (RU == 2) {
                     for (; i + 1 < cnt; i += 2) {
-                        splat_record<PH>(s_sv + lst[i] * 4, dy, dxm, dx, dz, lfz, acc_re, acc_im);
-                        splat_record<PH>(s_sv + lst[i + 1] * 4, dy, dxm, dx, dz, lfz, acc2_re, acc2_im);
+                        splat_record<PH, NPOLY>(s_sv + lst[i] * 4, dy, dxm, dx, dz, lfz, acc_re, acc_im);
+                        splat_record<PH, NPOLY>(s_sv + lst[i + 1] * 4, dy, dxm, dx, dz, lfz, acc2_re, acc2_im);
                     }
                 }
 #pragma unroll 2
-                for (; i < cnt; ++i) splat_record<PH>(s_sv + lst[i] * 4, dy, dxm, dx, dz, lfz, acc_re, acc_im);
+                for (; i < cnt; ++i) splat_record<PH, NPOLY>(s_sv + lst[i] * 4, dy, dxm, dx, dz, lfz, acc_re, acc_im);
             }
             if (RU == 2) {
 #pragma unroll
@@ -340,11 +373,12 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
 
 // ---- tile configurations (autotuned) ----------------------------------------------------
 
-// MINB: CTAs per SM the launch bounds aim at (3 needs <= 85 registers and the 2-stage ring)
-template <int TW, int TH, int PX, int RU = 1, int STAGES = 3, int MINB = 2>
+// MINB: CTAs per SM the launch bounds aim at (3 needs <= 85 registers and the 2-stage ring);
+// CHUNK: Gaussian records per bulk-copied chunk (<= threads; 0 = one per thread); STAGES: ring depth
+template <int TW, int TH, int PX, int RU = 1, int STAGES = 3, int MINB = 2, int CHUNK_ = 0, int NPOLY = 0>
 struct SplatCfg {
     static constexpr int NT = (TW / PX) * TH;
-    static constexpr int CHUNK = NT;
+    static constexpr int CHUNK = CHUNK_ > 0 ? CHUNK_ : NT;
     static constexpr size_t smem = sizeof(Rec) * STAGES * CHUNK + sizeof(float4) * 4 * CHUNK + (size_t)(NT / 32) * NT;
     // the opt-in shared-memory size is a per-device function attribute: set it once per
     // device (gws_prepare or the first call), not while a stream is being captured
@@ -354,7 +388,7 @@ struct SplatCfg {
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-        e = cudaFuncSetAttribute(k_splat_mixed<TW, TH, PX, CHUNK, STAGES, RU, MINB>,
+        e = cudaFuncSetAttribute(k_splat_mixed<TW, TH, PX, CHUNK, STAGES, RU, MINB, NPOLY>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
         return e;
@@ -362,39 +396,68 @@ struct SplatCfg {
     static cudaError_t launch(const SplatArgs &a, int grid, cudaStream_t s) {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
-        k_splat_mixed<TW, TH, PX, CHUNK, STAGES, RU, MINB><<<grid, NT, smem, s>>>(a);
+        k_splat_mixed<TW, TH, PX, CHUNK, STAGES, RU, MINB, NPOLY><<<grid, NT, smem, s>>>(a);
         count_launches(1);
         return cudaGetLastError();
     }
 };
 
+// The autotuner's search space: tile shape (frequencies per CTA), pixels per thread, records per
+// iteration, Gaussian records per chunk, ring depth and CTAs per SM.
+using Cfg1 = SplatCfg<64, 32, 8>;                 // 64x32, 8 px/thread, 256 records/chunk, 3 stages
+using Cfg2 = SplatCfg<32, 32, 4>;                 // 32x32, 4 px/thread
+using Cfg3 = SplatCfg<128, 16, 8>;                // 128x16
+using Cfg4 = SplatCfg<32, 32, 4, 2>;              // 32x32, two records per iteration
+using Cfg5 = SplatCfg<32, 32, 4, 1, 2, 3>;        // 32x32 at three CTAs per SM, 2 stages
+using Cfg6 = SplatCfg<64, 32, 8, 1, 4, 2, 128>;   // 64x32, 128 records/chunk, 4 stages
+using Cfg7 = SplatCfg<64, 32, 8, 1, 2, 2, 256>;   // 64x32, 256 records/chunk, 2 stages
+using Cfg8 = SplatCfg<64, 32, 8, 1, 6, 2, 64>;    // 64x32, 64 records/chunk, 6 stages
+using Cfg9 = SplatCfg<64, 32, 8, 1, 3, 2, 0, 1>;  // 64x32, the cos of 1 of the 4 pixel pairs on the FP32 pipe
+using Cfg10 = SplatCfg<128, 16, 8, 1, 3, 2, 0, 1>;  // 128x16, likewise
+
 cudaError_t prepare_splat_kernels() {
-    cudaError_t e = SplatCfg<64, 32, 8>::prepare();
-    if (e == cudaSuccess) e = SplatCfg<32, 32, 4>::prepare();
-    if (e == cudaSuccess) e = SplatCfg<128, 16, 8>::prepare();
-    if (e == cudaSuccess) e = SplatCfg<32, 32, 4, 2>::prepare();
-    if (e == cudaSuccess) e = SplatCfg<32, 32, 4, 1, 2, 3>::prepare();
+    cudaError_t e = Cfg1::prepare();
+    if (e == cudaSuccess) e = Cfg2::prepare();
+    if (e == cudaSuccess) e = Cfg3::prepare();
+    if (e == cudaSuccess) e = Cfg4::prepare();
+    if (e == cudaSuccess) e = Cfg5::prepare();
+    if (e == cudaSuccess) e = Cfg6::prepare();
+    if (e == cudaSuccess) e = Cfg7::prepare();
+    if (e == cudaSuccess) e = Cfg8::prepare();
+    if (e == cudaSuccess) e = Cfg9::prepare();
+    if (e == cudaSuccess) e = Cfg10::prepare();
     return e;
 }
 
-// id, tile width, tile height (4: the 32x32 tile with two records per iteration; 5: the 32x32
-// tile at three CTAs per SM with a 2-stage ring)
-static const TileCfg kCfgs[] = {{1, 64, 32}, {2, 32, 32}, {3, 128, 16}, {4, 32, 32}, {5, 32, 32}};
+template <typename C>
+constexpr TileCfg describe(int id, int tw, int th, int px, int ru, int stages, int ctas, int npoly = 0) {
+    return TileCfg{id, tw, th, px, ru, C::CHUNK, stages, ctas, npoly};
+}
+static const TileCfg kCfgs[] = {
+    describe<Cfg1>(1, 64, 32, 8, 1, 3, 2), describe<Cfg2>(2, 32, 32, 4, 1, 3, 2), describe<Cfg3>(3, 128, 16, 8, 1, 3, 2),
+    describe<Cfg4>(4, 32, 32, 4, 2, 3, 2), describe<Cfg5>(5, 32, 32, 4, 1, 2, 3), describe<Cfg6>(6, 64, 32, 8, 1, 4, 2),
+    describe<Cfg7>(7, 64, 32, 8, 1, 2, 2), describe<Cfg8>(8, 64, 32, 8, 1, 6, 2), describe<Cfg9>(9, 64, 32, 8, 1, 3, 2, 1),
+    describe<Cfg10>(10, 128, 16, 8, 1, 3, 2, 1)};
 
 int n_tile_cfgs() { return (int)(sizeof(kCfgs) / sizeof(kCfgs[0])); }
 TileCfg tile_cfg(int id) {
     if (id < 1 || id > n_tile_cfgs()) id = 1;
     return kCfgs[id - 1];
 }
-int splat_mixed_ctas_per_sm(int cfg) { return cfg == 5 ? 3 : 2; }
+int splat_mixed_ctas_per_sm(int cfg) { return tile_cfg(cfg).ctas; }
 
 cudaError_t launch_splat_mixed(int cfg, const SplatArgs &a, int grid, cudaStream_t s) {
     switch (cfg) {
-        case 2: return SplatCfg<32, 32, 4>::launch(a, grid, s);
-        case 3: return SplatCfg<128, 16, 8>::launch(a, grid, s);
-        case 4: return SplatCfg<32, 32, 4, 2>::launch(a, grid, s);
-        case 5: return SplatCfg<32, 32, 4, 1, 2, 3>::launch(a, grid, s);
-        default: return SplatCfg<64, 32, 8>::launch(a, grid, s);
+        case 2: return Cfg2::launch(a, grid, s);
+        case 3: return Cfg3::launch(a, grid, s);
+        case 4: return Cfg4::launch(a, grid, s);
+        case 5: return Cfg5::launch(a, grid, s);
+        case 6: return Cfg6::launch(a, grid, s);
+        case 7: return Cfg7::launch(a, grid, s);
+        case 8: return Cfg8::launch(a, grid, s);
+        case 9: return Cfg9::launch(a, grid, s);
+        case 10: return Cfg10::launch(a, grid, s);
+        default: return Cfg1::launch(a, grid, s);
     }
 }
 
@@ -415,6 +478,7 @@ __global__ void __launch_bounds__(256) k_splat_fp64(const __grid_constant__ Spla
         const double dz = fz - inv_lam;
         const long long p0 = A.segs.off[scene], p1 = A.segs.off[scene + 1];
         const int L = A.segs.n_lambda;
+        if (!in_bounds(scene < A.segs.n_scenes && p0 >= 0 && p1 >= p0, A.status)) return;
         for (long long p = p0; p < p1; ++p) {
             const Rec64 &g = A.rec[p];
             const double w = A.w[p * L + l];

@@ -7,6 +7,7 @@ There is no fallback: if ``libgws.so`` is missing or fails to load, every call r
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import math
 import os
@@ -28,7 +29,7 @@ TIMER_SPLAT_FWD, TIMER_SPLAT_BWD, TIMER_FFT, TIMER_ENCODE, TIMER_TOTAL = 0, 1, 2
 MAX_LAMBDA, MAX_SCENES = 16, 128
 
 STATUS = {0: "GWS_OK", 1: "GWS_ERR_INVALID_ARG", 2: "GWS_ERR_WORKSPACE", 3: "GWS_ERR_CUDA",
-          4: "GWS_ERR_NONFINITE", 5: "GWS_ERR_TIMEOUT", 6: "GWS_ERR_UNSUPPORTED"}
+          4: "GWS_ERR_NONFINITE", 5: "GWS_ERR_TIMEOUT", 6: "GWS_ERR_UNSUPPORTED", 7: "GWS_ERR_BOUNDS"}
 
 
 class GwsError(RuntimeError):
@@ -75,43 +76,61 @@ class _Camera(C.Structure):
                 ("cy", C.c_double), ("projection", C.c_int), ("z_near", C.c_double)]
 
 
-_lib = None
+_libs = {}
+_variant = ""  # "" = libgws.so; "check" = libgws_check.so (bounds-checking build, tests only)
 _lib_lock = threading.Lock()
 
 EXPORTS = ["gws_opts_default", "gws_status_string", "gws_version", "gws_workspace_size", "gws_prepare",
            "gws_forward", "gws_forward_batched", "gws_backward", "gws_encode", "gws_get_device_status",
            "gws_depth_order", "gws_transmittance", "gws_footprints", "gws_last_launch_count", "gws_autotune",
            "gws_kernel_time_ms", "gws_footprint_pairs", "gws_encode_noalloc", "gws_holographics",
-           "gws_triangles_workspace_size", "gws_forward_triangles"]
+           "gws_triangles_workspace_size", "gws_forward_triangles", "gws_tile_config"]
 
 
-def lib_path() -> str:
-    return _build.LIB
+def lib_path(variant: str | None = None) -> str:
+    return _build.VARIANTS[_variant if variant is None else variant][0]
 
 
 def load(build_if_needed: bool = True):
-    """Loads libgws.so (building it in-tree first if sources are newer)."""
-    global _lib
+    """Loads libgws.so (building it in-tree first if sources are newer); inside ``checking_build()``
+    the bounds-checking variant libgws_check.so instead."""
     with _lib_lock:
-        if _lib is not None:
-            return _lib
-        if build_if_needed and _build.stale():
-            _build.build()
-        if not os.path.exists(_build.LIB):
-            raise RuntimeError("libgws.so is not built; run __graft_entry__.build()")
-        lib = C.CDLL(_build.LIB)
+        lib = _libs.get(_variant)
+        if lib is not None:
+            return lib
+        path = lib_path()
+        if build_if_needed and _build.stale(_variant):
+            _build.build(variants=(_variant,))
+        if not os.path.exists(path):
+            raise RuntimeError(f"{os.path.basename(path)} is not built; run __graft_entry__.build()")
+        lib = C.CDLL(path)
         for name in EXPORTS:
             getattr(lib, name)  # raises AttributeError if an export is missing
         lib.gws_status_string.restype = C.c_char_p
         lib.gws_version.restype = C.c_int
         lib.gws_last_launch_count.restype = C.c_int
         lib.gws_kernel_time_ms.restype = C.c_float
+        lib.gws_tile_config.restype = C.c_int
         for name in EXPORTS:
             if name not in ("gws_status_string", "gws_version", "gws_last_launch_count", "gws_opts_default",
-                            "gws_kernel_time_ms"):
+                            "gws_kernel_time_ms", "gws_tile_config"):
                 getattr(lib, name).restype = C.c_int
-        _lib = lib
+        _libs[_variant] = lib
         return lib
+
+
+@contextlib.contextmanager
+def checking_build():
+    """Routes every call of this module to libgws_check.so (built with GWS_CHECK_BOUNDS: index checks
+    in the kernels, canary words after the workspace's sub-buffers; a violation reads back as
+    GWS_ERR_BOUNDS from gws_get_device_status).  For tests; not thread-safe."""
+    global _variant
+    old = _variant
+    _variant = "check"
+    try:
+        yield load()
+    finally:
+        _variant = old
 
 
 def _check(code: int, where: str):
@@ -397,6 +416,19 @@ def autotune(g: Gaussians, slm: Slm, workspace=None, **kw) -> int:
     _check(lib.gws_autotune(C.byref(g._c()), C.c_int64(g.n), C.byref(slm._c()), C.byref(opts),
                             C.c_void_p(scratch.data_ptr()), C.byref(best)), "gws_autotune")
     return int(best.value)
+
+
+def tile_configs() -> dict:
+    """The splat configurations the autotuner searches: id -> description."""
+    lib = load()
+    n = int(lib.gws_tile_config(0, None))
+    out = {}
+    for i in range(1, n + 1):
+        d = (C.c_int * 8)()
+        lib.gws_tile_config(i, d)
+        out[i] = dict(zip(("tile_w", "tile_h", "px_per_thread", "records_per_iteration", "records_per_chunk",
+                           "ring_stages", "ctas_per_sm", "cos_pairs_on_fp32"), list(d)))
+    return out
 
 
 def forward_triangles(vertices: torch.Tensor, opacity: torch.Tensor, amp: torch.Tensor, slm: Slm,

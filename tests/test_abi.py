@@ -32,6 +32,43 @@ def test_library_is_built_for_sm_103a_only():
     assert os.path.exists(_build.LIB)
 
 
+def test_checking_build_exports_the_same_symbols_and_reserves_canaries():
+    """libgws_check.so (GWS_CHECK_BOUNDS) is the same ABI; its workspace has canary words after every
+    sub-buffer, so it asks for more bytes."""
+    assert os.path.exists(_build.LIB_CHECK)
+    chk = C.CDLL(_build.LIB_CHECK)
+    for n in declared_functions():
+        assert hasattr(chk, n), n
+    wl = (C.c_double * 3)(6.38e-7, 5.2e-7, 4.5e-7)
+    s = gws._Slm(45, 70, 8e-6, 6e-6, 3, wl)
+    sizes = []
+    for lib in (gws.load(), chk):
+        o = gws._Opts()
+        lib.gws_opts_default(C.byref(o))
+        o.domain = 1  # spectrum: no FFT plan (no GPU call) in the size query
+        arr = (C.c_int64 * 1)(64)
+        out = C.c_size_t(0)
+        assert lib.gws_workspace_size(arr, 1, C.byref(s), C.byref(o), C.byref(out)) == 0
+        sizes.append(out.value)
+    assert sizes[1] > sizes[0] + 40 * 64
+    chk.gws_status_string.restype = C.c_char_p
+    assert chk.gws_status_string(7).decode() == "GWS_ERR_BOUNDS"
+
+
+def test_tile_configurations_are_described():
+    """The autotuner's search space (tile shape, pixels per thread, records per iteration, records
+    per chunk, ring depth, CTAs per SM): more than tile shapes alone, chunks within the CTA's threads."""
+    cfgs = gws.tile_configs()
+    assert len(cfgs) >= 8
+    assert len({c["records_per_chunk"] for c in cfgs.values()}) >= 3
+    assert len({c["ring_stages"] for c in cfgs.values()}) >= 3
+    for c in cfgs.values():
+        threads = c["tile_w"] // c["px_per_thread"] * c["tile_h"]
+        assert 32 <= c["records_per_chunk"] <= min(threads, 256) and c["records_per_chunk"] % 32 == 0
+    lib = gws.load()
+    assert lib.gws_tile_config(0, None) == len(cfgs) and lib.gws_tile_config(99, None) == len(cfgs)
+
+
 def test_status_strings_and_version():
     lib = gws.load()
     assert lib.gws_version() == 1

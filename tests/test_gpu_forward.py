@@ -60,7 +60,7 @@ def test_forward_field_matches_oracle(name, slm, kind, seed, n, blend):
     assert max(per_lambda_rel(fmx, ref)) < TOLMX
 
 
-@pytest.mark.parametrize("tile_cfg", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("tile_cfg", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 def test_spectrum_domain_and_every_tile_config(tile_cfg):
     slm = SLM(96, 160, 8e-6, 8e-6, (638e-9, 520e-9, 450e-9))
     sc = surface_scene(7, 120, slm, n_surfaces=3)
@@ -233,6 +233,51 @@ def test_full_size_sampled_spectrum(cfg, n, k):
     for l in range(slm.n_lambda):
         e = (torch.linalg.norm(f[l].to(torch.complex128) - ref_f[l]) / torch.linalg.norm(ref_f[l])).item()
         assert e < 1e-5, e
+
+
+def _band_samples(slm, band, k, seed):
+    """k frequencies of one band: 'dc' (within 2 pixels of f = 0), 'mid' (normalised radius in
+    [0.3, 0.6] of the grid's half extent per axis), 'outer' ([0.8, 1.0]: where few footprints reach
+    and the truncation acts) or 'corner' (corners of the forward's 64 x 32 frequency tiles, where the
+    in-tile phase deltas from the tile's reference frequency are largest)."""
+    rng = np.random.default_rng(seed)
+    H, W = slm.H, slm.W
+    if band == "dc":
+        r = H // 2 + rng.integers(-2, 3, k)
+        c = W // 2 + rng.integers(-2, 3, k)
+    elif band == "corner":
+        r = rng.integers(0, (H + 31) // 32, k) * 32 + rng.choice([0, 31], k)
+        c = rng.integers(0, (W + 63) // 64, k) * 64 + rng.choice([0, 63], k)
+        r, c = np.minimum(r, H - 1), np.minimum(c, W - 1)
+    else:
+        lo, hi = (0.3, 0.6) if band == "mid" else (0.8, 1.0)
+        rad = rng.uniform(lo, hi, k)
+        ang = rng.uniform(0, 2 * math.pi, k)
+        r = np.clip(np.round(H // 2 + rad * np.sin(ang) * (H // 2)), 0, H - 1)
+        c = np.clip(np.round(W // 2 + rad * np.cos(ang) * (W // 2)), 0, W - 1)
+    return r.astype(np.int32), c.astype(np.int32)
+
+
+@pytest.mark.parametrize("cfg", ["headline_1m_1080p_3l", "c2_precision_at_scale"])
+def test_full_size_band_stratified_spectrum(cfg):
+    """Full-size parity per frequency band and wavelength, each band against its own norm: the
+    sampled mixed spectrum (the bench's launch configuration) vs the oracle, which sums every
+    Gaussian at each sample without truncation."""
+    sc, slm = config_scene(cfg)
+    u = gws.forward(dev(sc), slm, prec=gws.PREC_MIXED, domain=gws.DOMAIN_SPECTRUM)
+    report = {}
+    for bi, band in enumerate(("dc", "mid", "outer", "corner")):
+        for l in range(slm.n_lambda):
+            r, c = _band_samples(slm, band, 40, 1000 + 10 * bi + l)
+            lam = np.full(r.shape, l, np.int32)
+            got = u[l, torch.as_tensor(r, dtype=torch.long), torch.as_tensor(c, dtype=torch.long)].cpu().numpy()
+            ref = O.spectrum_at(sc, slm, lam, r, c)
+            e = rel_l2(got, ref)
+            peak = np.abs(ref).max()
+            report[(band, l)] = (e, float(np.abs(got - ref).max() / peak), float(peak))
+            assert e < TOLMX, (band, l, e)
+    print(cfg, {f"{b}/{l}": f"rel-L2 {v[0]:.2e}, max|err|/peak {v[1]:.2e}, peak {v[2]:.3g}"
+                for (b, l), v in report.items()})
 
 
 def test_fp64_path_at_slm_size_sampled():
