@@ -101,6 +101,9 @@ def parse():
     p.add_argument("--no-context", action="store_true",
                    help="skip the context rows (plain FP64 path at 20k, the 100k differentiable step, the batched "
                         "64-scene graph replay) timed after the main measurement")
+    p.add_argument("--tile-sweep", action="store_true",
+                   help="time the forward splat of every autotuner configuration on the workload (3 calls each) and "
+                        "print them as one JSON line")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
@@ -735,9 +738,43 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_tile_sweep(args):
+    """Forward splat time of every configuration of the autotuner's search space on the workload."""
+    import torch
+
+    from paper_2505_06582_gb300 import gws
+    from paper_2505_06582_gb300.scenes import config_scene
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scene, slm = config_scene(args.workload, n=args.n)
+    S = gws.Slm.of(slm)
+    g = gws.Gaussians.from_scene(scene, dev)
+    ws = torch.empty(gws.workspace_size([g.n], S, gws.make_opts()), dtype=torch.uint8, device=dev)
+    out = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.complex64, device=dev)
+    gws.prepare(S)
+    clocks = ClockSampler(local)
+    clocks.start()
+    rows = []
+    for c, d in gws.tile_configs().items():
+        ts = []
+        for _ in range(3):
+            gws.forward(g, S, out=out, workspace=ws, tile_cfg=c, domain=gws.DOMAIN_SPECTRUM,
+                        debug_flags=gws.DEBUG_TIME_KERNELS)
+            ts.append(gws.kernel_time_ms(gws.TIMER_SPLAT_FWD))
+        rows.append(dict(d, id=c, splat_ms=statistics.median(ts)))
+    clk = clocks.stop()
+    if rank == 0:
+        print(json.dumps({"mode": "tile_sweep", "workload": args.workload, "n_gaussians": g.n,
+                          "configs": rows, "clocks": clk}), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.tile_sweep:
+        run_tile_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.batched:
         run_batched(args)
