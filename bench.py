@@ -600,8 +600,8 @@ def _event_ms(fn, stream, flush=None):
 def run_context(dev):
     """One step each of the other workloads, timed in the same run (rank 0, after the headline):
     the plain FP64 GPU path next to the mixed path at 20k Gaussians (1920x1080, 3 wavelengths), the
-    100k differentiable step (forward + encode + refocus loss + backward) and one CUDA-graph replay
-    of the batched 64-scene forward."""
+    100k differentiable step (forward + encode + refocus loss + backward), the 1M-Gaussian forward at
+    3840x2160 and one CUDA-graph replay of the batched 64-scene forward."""
     import torch
 
     from paper_2505_06582_gb300 import gws, refocus
@@ -659,6 +659,24 @@ def run_context(dev):
                     "(z = 2, 5, 8 mm) + backward", "ms": t_c4, "holograms_per_s": 1000.0 / t_c4,
         "l2": "flushed before each step"}
     del field, phase, ws, g, Hz, targets
+    torch.cuda.empty_cache()
+    # precision at scale: 1M Gaussians at 3840x2160, 3.74 um pitch, the mixed forward (its parity per
+    # frequency band against the oracle is a GPU test, not part of this timing)
+    sc, slm = config_scene("c2_precision_at_scale")
+    S = gws.Slm.of(slm)
+    g = gws.Gaussians.from_scene(sc, dev)
+    ws = torch.empty(gws.workspace_size([g.n], S, gws.make_opts()), dtype=torch.uint8, device=dev)
+    field = torch.empty((S.n_lambda, S.H, S.W), dtype=torch.complex64, device=dev)
+    gws.forward(g, S, out=field, workspace=ws)
+    t_c2 = _event_ms(lambda: gws.forward(g, S, out=field, workspace=ws), stream, flush)
+    pairs_c2 = gws.footprint_pairs(g, S, workspace=ws)
+    out["c2_precision_at_scale"] = {
+        "workload": "c2_precision_at_scale: 1M Gaussians, 3840x2160, 3.74 um pitch, 3 wavelengths; mixed forward "
+                    "(splat + inverse DFT)", "ms": t_c2, "holograms_per_s": 1000.0 / t_c2,
+        "algorithmic_pairs_per_s": pairs_c2 / (t_c2 * 1e-3),
+        "parity": "tests/test_gpu_forward.py::test_full_size_band_stratified_spectrum[c2_precision_at_scale]",
+        "l2": "flushed before the call"}
+    del field, ws, g
     torch.cuda.empty_cache()
     # the batched workload: one graph replay
     t_b, pairs_b, n_scenes, n_tot, _ = batched_graph_ms(dev, warmup=1, steps=1, flush=flush)
