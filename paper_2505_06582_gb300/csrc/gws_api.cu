@@ -308,7 +308,8 @@ struct CanaryGuard {
     CanaryList c;
     size_t status;
     cudaStream_t s;
-    CanaryGuard(const gws_opts *o_, const Layout &L, cudaStream_t s_) : o(o_), status(L.status), s(s_) {
+    template <class LayoutT>
+    CanaryGuard(const gws_opts *o_, const LayoutT &L, cudaStream_t s_) : o(o_), status(L.status), s(s_) {
         c.n = L.n_canary;
         for (int i = 0; i < L.n_canary; ++i) c.off[i] = L.canary[i];
         k_canary<<<1, 256, 0, s>>>(static_cast<unsigned char *>(o->workspace), c, 0, nullptr);
@@ -320,7 +321,8 @@ struct CanaryGuard {
 };
 #else
 struct CanaryGuard {
-    CanaryGuard(const gws_opts *, const Layout &, cudaStream_t) {}
+    template <class LayoutT>
+    CanaryGuard(const gws_opts *, const LayoutT &, cudaStream_t) {}
 };
 #endif
 
@@ -529,6 +531,8 @@ static gws_status exact_forward(const gws_gaussians *scene, long long n, const g
     E.ok = E.co + (size_t)B * nl;
     E.rr = E.ok + B;
     E.mu = nullptr;
+    E.status = at<int>(o, L.status);
+    E.n = n;
     InvLam il;
     std::memset(&il, 0, sizeof il);
     for (int l = 0; l < nl; ++l) il.v[l] = 1.0 / slm->wavelengths[l];
@@ -595,6 +599,8 @@ static gws_status pc_forward(const gws_gaussians *scene, long long n, const gws_
     E.co = E.amp + (size_t)B * nl;
     E.ok = E.co + (size_t)B * nl;
     E.rr = E.ok + B;
+    E.status = at<int>(o, L.status);
+    E.n = n;
     InvLam il;
     std::memset(&il, 0, sizeof il);
     for (int l = 0; l < nl; ++l) il.v[l] = 1.0 / slm->wavelengths[l];
@@ -1184,6 +1190,10 @@ gws_status gws_autotune(const gws_gaussians *g, int64_t n, const gws_slm *slm, c
 // ---- triangle primitive ----------------------------------------------------------------------
 
 struct TriLayout {
+#ifdef GWS_CHECK_BOUNDS
+    size_t canary[kMaxCanaries];
+    int n_canary;
+#endif
     size_t status, rec, w, cufft, total;
 };
 
@@ -1200,6 +1210,10 @@ static gws_status tri_layout(int64_t n, const gws_slm *slm, bool fft, TriLayout 
     }
     L->cufft = P.take(std::max<size_t>(work, 16));
     L->total = P.cur;
+#ifdef GWS_CHECK_BOUNDS
+    L->n_canary = P.n_canary;
+    for (int i = 0; i < P.n_canary; ++i) L->canary[i] = P.canary[i];
+#endif
     return GWS_OK;
 }
 
@@ -1228,6 +1242,7 @@ gws_status gws_forward_triangles(const gws_triangles *t, int64_t n, const gws_sl
     if (!opts->workspace || opts->workspace_bytes < L.total) return GWS_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(opts->workspace) % 256 != 0) return GWS_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)opts->stream;
+    CanaryGuard guard(opts, L, s);
     const int nl = slm->n_lambda, H = slm->H, W = slm->W;
     const double dfx = 1.0 / (W * slm->pitch_x), dfy = 1.0 / (H * slm->pitch_y);
     timers_reset(opts);

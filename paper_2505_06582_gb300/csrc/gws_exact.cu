@@ -19,6 +19,7 @@ __global__ void k_exact_gather(const unsigned *__restrict__ sorted, long long b0
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nb) return;
     const long long i = sorted[b0 + k];
+    if (!in_bounds(b0 + k < E.n && i < E.n, E.status)) return;  // checking build only
     // the field on the Gaussian's own plane; partial coherence: at the origin (translated after the kernel)
     E.mean[3 * k] = pc ? 0.0 : mean[3 * i];
     E.mean[3 * k + 1] = pc ? 0.0 : mean[3 * i + 1];

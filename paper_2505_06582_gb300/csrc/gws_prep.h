@@ -46,6 +46,8 @@ struct ExactBatch {  // one batch of exact blending (Gaussians in depth order)
     float *ok;       // [B] o
     double *mu;      // [B][3] the means (partial coherence: the inner fields sit at the origin)
     float *rr;       // [B][9] kappa s_u r1, kappa s_v r2, 2 pi s_u s_v r3 (the one-Gaussian record)
+    int *status;     // device status word (index checks of the checking build)
+    long long n;     // Gaussians of the scene (bound of the depth-order indices)
 };
 // pc = 0: exact blending (the means keep x, y; depth zeroed); pc = 1: partial coherence (means zeroed)
 cudaError_t launch_exact_gather(const unsigned *sorted, long long b0, int nb, const gws_gaussians *g, int L,
