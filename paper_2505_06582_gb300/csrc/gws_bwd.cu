@@ -12,7 +12,9 @@
 // tile is one contiguous block per table, and a lane's two columns c and c + 32 of a row sit
 // side by side for the packed f32x2 arithmetic): G enters in polar form, as a factor of the
 // exponential and a shift of the phase, so conj(G) P0 costs no complex product.  It culls
-// each record exactly and hands the survivors to its warps through a shared counter; a warp
+// each record exactly (and where g = r3.f keeps one sign over the tile, folds that sign into
+// the record's r3, so that its pixels skip their own) and hands the survivors to its warps
+// through a shared counter; a warp
 // takes one record over the tile (lane = column pair, rows in a loop, the phase re-anchored
 // per 32-row segment), accumulating 16 FP32 partial sums per column; these are reduced across
 // the warp and merged per tile into 13 FP64 totals per record in shared memory:
@@ -20,6 +22,7 @@
 // with P0 = conj(G) f_z^-1 2^-(a'^2+b'^2) e^{j phi},  R = |g| Re(P0),  I = |g| Im(P0),
 // g = r3.f, d = f - f_r.  A record's totals are only touched by the warp holding it in the
 // current tile, and tiles are visited in a fixed order, so the result is deterministic.
+#include <type_traits>
 #include <float.h>
 
 #include "gws_prep.h"
@@ -38,8 +41,20 @@ int bwd_block_size() { return BB; }
 struct TileConst {  // geometry of the current tile, computed once by thread 0
     double f0x, f0y, f0z, dz0;
     float x0, x1, y0, y1;
+    float fzlo, fzhi;  // range of f_z over the tile's valid pixels (0 where evanescent)
     int c_lo, r_lo, c_ref, r_ref;
 };
+
+// The sign of g = r3.f over a tile when it is the same at every pixel (+1 / -1), else 0: g is
+// linear in (f_x, f_y, f_z), so its bounds over the box [x0, x1] x [y0, y1] x [fzlo, fzhi] are
+// sums of per-axis extremes; a margin covers the FP32 evaluation of g per pixel.
+__device__ __forceinline__ int tile_sign(float r3x, float r3y, float r3z, const TileConst &T) {
+    const float lo = fminf(r3x * T.x0, r3x * T.x1) + fminf(r3y * T.y0, r3y * T.y1) + fminf(r3z * T.fzlo, r3z * T.fzhi);
+    const float hi = fmaxf(r3x * T.x0, r3x * T.x1) + fmaxf(r3y * T.y0, r3y * T.y1) + fmaxf(r3z * T.fzlo, r3z * T.fzhi);
+    const float tol = 1e-5f * (fabsf(r3x) * fmaxf(fabsf(T.x0), fabsf(T.x1)) + fabsf(r3y) * fmaxf(fabsf(T.y0), fabsf(T.y1)) +
+                               fabsf(r3z) * T.fzhi);
+    return lo > tol ? 1 : (hi < -tol ? -1 : 0);
+}
 
 struct BwdShared {
     float4 t[BQ];   // [row][lane]: (dz(c), dz(c + 32), lw(c), lw(c + 32)), c = c_lo + lane, lw = log2(f_z / |G|)
@@ -50,6 +65,7 @@ struct BwdShared {
     double tot[BB][NTOT];
     float red[BNT / 32][16];
     unsigned mask[BB / 32];
+    signed char sgn[BB];     // per surviving record: the sign of g over the tile (0: it changes)
     unsigned char list[BB];  // the surviving records of the current tile, in record order
     int n_surv, next;        // their count; the next list entry a warp takes
     TileConst tc;
@@ -286,6 +302,14 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                 T.x1 = (float)((double)(c_hi - A.W / 2) * A.dfx);
                 T.y0 = (float)((double)(T.r_lo - A.H / 2) * A.dfy);
                 T.y1 = (float)((double)(r_hi - A.H / 2) * A.dfy);
+                {  // |f| over the rectangle: nearest and farthest point from f = 0
+                    const double x0 = (double)(T.c_lo - A.W / 2) * A.dfx, x1 = (double)(c_hi - A.W / 2) * A.dfx;
+                    const double y0 = (double)(T.r_lo - A.H / 2) * A.dfy, y1 = (double)(r_hi - A.H / 2) * A.dfy;
+                    const double nx = x0 > 0.0 ? x0 : (x1 < 0.0 ? x1 : 0.0), ny = y0 > 0.0 ? y0 : (y1 < 0.0 ? y1 : 0.0);
+                    const double fx = fmax(fabs(x0), fabs(x1)), fy = fmax(fabs(y0), fabs(y1));
+                    T.fzhi = (float)sqrt(fmax(k2 - (nx * nx + ny * ny), 0.0));
+                    T.fzlo = (float)sqrt(fmax(k2 - (fx * fx + fy * fy), 0.0));
+                }
             }
             __syncthreads();
             const int c_lo = S.tc.c_lo, r_lo = S.tc.r_lo, c_ref = S.tc.c_ref, r_ref = S.tc.r_ref;
@@ -314,7 +338,13 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                         const float fxf = (float)f0x, fyf = (float)f0y, fzf = (float)f0z, dzf = (float)dz0;
                         S.sv[tid][0] = make_float4(r.r1x, r.r1y, r.r1z, fmaf(r.r1z, dzf, fmaf(r.r1y, fyf, r.r1x * fxf)));
                         S.sv[tid][1] = make_float4(r.r2x, r.r2y, r.r2z, fmaf(r.r2z, dzf, fmaf(r.r2y, fyf, r.r2x * fxf)));
-                        S.sv[tid][2] = make_float4(r.r3x, r.r3y, r.r3z, fmaf(r.r3z, fzf, fmaf(r.r3y, fyf, r.r3x * fxf)));
+                        // where g keeps one sign over the tile it is folded into r3 (g' = |g|), so that the
+                        // pixels need no sign of their own; the Rg moments are multiplied back by it
+                        const int sg = tile_sign(r.r3x, r.r3y, r.r3z, S.tc);
+                        const float sf = sg < 0 ? -1.f : 1.f;
+                        S.sgn[tid] = (signed char)sg;
+                        S.sv[tid][2] = make_float4(sf * r.r3x, sf * r.r3y, sf * r.r3z,
+                                                   sf * fmaf(r.r3z, fzf, fmaf(r.r3y, fyf, r.r3x * fxf)));
                         S.sv[tid][3] = make_float4(r.mx, r.my, r.mz, (float)cyc);
                     }
                 }
@@ -364,41 +394,57 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                 float2 sp[4], sz[4], sy[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) sp[u] = sz[u] = sy[u] = pair(0.f);
-                for (int seg = row_lo / BSEG; seg <= row_hi / BSEG; ++seg) {
-                    const int s_lo = max(row_lo, seg * BSEG), s_hi = min(row_hi, seg * BSEG + BSEG - 1);
-                    const float dys = fmaf((float)(seg * BSEG + BSEG / 2), dfyf, dyb);  // dy of the middle row
-                    const float dyrb = dyb - dys;
-                    float2 ts = __ffma2_rn(ty, pair(dys), tc);
-                    {
-                        const float2 kt = __fadd2_rn(__ffma2_rn(ts, pair(0.15915494309189535f), pair(12582912.0f)),
-                                                     pair(-12582912.0f));
-                        ts = __ffma2_rn(kt, pair(-6.28318530717958647692f), ts);
-                    }
-                    // one row = the lane's two columns as one f32x2 pair; up to eight rows in flight
-#pragma unroll 8
-                    for (int row = s_lo; row <= s_hi; ++row) {
-                        const float2 dy = pair(fmaf((float)row, dfyf, dyb));
-                        const float2 dyr = pair(fmaf((float)row, dfyf, dyrb));
-                        const float4 T4 = S.t[32 * row + lane];
-                        const float2 ps = S.ps[32 * row + lane];
-                        const float2 dz = make_float2(T4.x, T4.y), lw = make_float2(T4.z, T4.w);
-                        const float2 a = __ffma2_rn(az, dz, __ffma2_rn(ay, dy, ac));
-                        const float2 b = __ffma2_rn(bz, dz, __ffma2_rn(by, dy, bc));
-                        const float2 g = __ffma2_rn(gz, dz, __ffma2_rn(gy, dy, gc));
-                        const float2 ang = __ffma2_rn(tz, dz, __fadd2_rn(__ffma2_rn(ty, dyr, ts), ps));  // phi - arg G
-                        const float2 uq = __ffma2_rn(a, a, __ffma2_rn(b, b, lw));  // a'^2 + b'^2 + log2(f_z / |G|)
-                        const float2 es = make_float2(with_sign_of(ex2_approx(-uq.x), g.x), with_sign_of(ex2_approx(-uq.y), g.y));
-                        // sign(g) P0 = sign(g) conj(G) f_z^-1 2^-(a'^2+b'^2) e^{j phi} = Rg + j Pi
-                        const float2 Rg = __fmul2_rn(es, make_float2(cos_approx(ang.x), cos_approx(ang.y)));
-                        const float2 Pi = __fmul2_rn(es, make_float2(sin_approx(ang.x), sin_approx(ang.y)));
-                        const float2 R = __fmul2_rn(g, Rg), I = __fmul2_rn(g, Pi);  // |g| Re P0, |g| Im P0
-                        const float2 X[4] = {__fmul2_rn(R, a), __fmul2_rn(R, b), Rg, I};
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            sp[u] = __fadd2_rn(sp[u], X[u]);
-                            sy[u] = __ffma2_rn(X[u], dy, sy[u]);
-                            sz[u] = __ffma2_rn(X[u], dz, sz[u]);
+                const int sgn = S.sgn[k];
+                // SIGNED: g changes sign inside the tile and each pixel takes its own
+                auto rows = [&](auto signed_tag) {
+                    constexpr bool SIGNED = decltype(signed_tag)::value;
+                    for (int seg = row_lo / BSEG; seg <= row_hi / BSEG; ++seg) {
+                        const int s_lo = max(row_lo, seg * BSEG), s_hi = min(row_hi, seg * BSEG + BSEG - 1);
+                        const float dys = fmaf((float)(seg * BSEG + BSEG / 2), dfyf, dyb);  // dy of the middle row
+                        const float dyrb = dyb - dys;
+                        float2 ts = __ffma2_rn(ty, pair(dys), tc);
+                        {
+                            const float2 kt = __fadd2_rn(__ffma2_rn(ts, pair(0.15915494309189535f), pair(12582912.0f)),
+                                                         pair(-12582912.0f));
+                            ts = __ffma2_rn(kt, pair(-6.28318530717958647692f), ts);
                         }
+                        // one row = the lane's two columns as one f32x2 pair; up to eight rows in flight
+#pragma unroll 8
+                        for (int row = s_lo; row <= s_hi; ++row) {
+                            const float2 dy = pair(fmaf((float)row, dfyf, dyb));
+                            const float2 dyr = pair(fmaf((float)row, dfyf, dyrb));
+                            const float4 T4 = S.t[32 * row + lane];
+                            const float2 ps = S.ps[32 * row + lane];
+                            const float2 dz = make_float2(T4.x, T4.y), lw = make_float2(T4.z, T4.w);
+                            const float2 a = __ffma2_rn(az, dz, __ffma2_rn(ay, dy, ac));
+                            const float2 b = __ffma2_rn(bz, dz, __ffma2_rn(by, dy, bc));
+                            const float2 g = __ffma2_rn(gz, dz, __ffma2_rn(gy, dy, gc));
+                            const float2 ang = __ffma2_rn(tz, dz, __fadd2_rn(__ffma2_rn(ty, dyr, ts), ps));  // phi - arg G
+                            const float2 uq = __ffma2_rn(a, a, __ffma2_rn(b, b, lw));  // a'^2 + b'^2 + log2(f_z / |G|)
+                            float2 es = make_float2(ex2_approx(-uq.x), ex2_approx(-uq.y));
+                            if constexpr (SIGNED) es = make_float2(with_sign_of(es.x, g.x), with_sign_of(es.y, g.y));
+                            // sign(g) P0 = sign(g) conj(G) f_z^-1 2^-(a'^2+b'^2) e^{j phi} = Rg + j Pi
+                            const float2 Rg = __fmul2_rn(es, make_float2(cos_approx(ang.x), cos_approx(ang.y)));
+                            const float2 Pi = __fmul2_rn(es, make_float2(sin_approx(ang.x), sin_approx(ang.y)));
+                            const float2 R = __fmul2_rn(g, Rg), I = __fmul2_rn(g, Pi);  // |g| Re P0, |g| Im P0
+                            const float2 X[4] = {__fmul2_rn(R, a), __fmul2_rn(R, b), Rg, I};
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                sp[u] = __fadd2_rn(sp[u], X[u]);
+                                sy[u] = __ffma2_rn(X[u], dy, sy[u]);
+                                sz[u] = __ffma2_rn(X[u], dz, sz[u]);
+                            }
+                        }
+                    }
+                };
+                if (sgn == 0) {
+                    rows(std::true_type{});
+                } else {
+                    rows(std::false_type{});
+                    if (sgn < 0) {  // back to sign(g) P0 for the Rg moments
+                        sp[2] = __fmul2_rn(sp[2], pair(-1.f));
+                        sy[2] = __fmul2_rn(sy[2], pair(-1.f));
+                        sz[2] = __fmul2_rn(sz[2], pair(-1.f));
                     }
                 }
                 float v[16];
