@@ -62,6 +62,47 @@ def test_backward_phase_match():
     _cmp(got, ref)
 
 
+def test_backward_where_g_changes_sign_inside_tiles():
+    """Nearly edge-on Gaussians (|r3_z| <= 0.02): the zero line of g = r3.f crosses the grid, so some
+    (Gaussian, 64 x 64 tile) pairs see both signs of g and take the per-pixel sign, the rest keep one sign
+    (positive and negative) and take it once per tile; the gradients must match the oracle's."""
+    from paper_2505_06582_gb300.scenes import _quat_from_frame, _tangent_frame
+    slm = SLM(128, 160, 8e-6, 8e-6, (520e-9, 638e-9))
+    rng = np.random.default_rng(41)
+    n = 12
+    r3z = np.array([0.002, -0.002, 0.006, -0.006, 0.01, -0.01, 0.014, -0.014, 0.018, -0.018, 0.02, -0.02])
+    psi = rng.uniform(0, 2 * np.pi, n)  # direction of the in-plane part of the normal
+    rxy = np.sqrt(1 - r3z ** 2)
+    normal = np.stack([rxy * np.cos(psi), rxy * np.sin(psi), r3z], 1)
+    r1, r2, r3 = _tangent_frame(normal, rng.uniform(0, np.pi, n))
+    quat = _quat_from_frame(r1, r2, r3).astype(np.float32)
+    ax, ay = slm.W * slm.pitch_x, slm.H * slm.pitch_y
+    mean = np.stack([rng.uniform(-ax / 3, ax / 3, n), rng.uniform(-ay / 3, ay / 3, n), rng.uniform(1e-3, 4e-3, n)], 1)
+    sc = make_scene(mean, quat, rng.uniform(2, 5, (n, 2)) * 8e-6, rng.uniform(0.3, 1.0, n),
+                    rng.uniform(0.2, 1.0, (n, 2)))
+    sc.quat = sc.quat.astype(np.float32)
+    sc.scale, sc.opacity, sc.amp = sc.scale.astype(np.float32), sc.opacity.astype(np.float32), sc.amp.astype(np.float32)
+    # the scene does what it is for: per wavelength, tiles where g keeps each sign and tiles where it changes
+    q = sc.quat.astype(np.float64) / np.linalg.norm(sc.quat.astype(np.float64), axis=1, keepdims=True)
+    w, x, y, z = q.T
+    n3 = np.stack([2 * (x * z + w * y), 2 * (y * z - w * x), 1 - 2 * (x * x + y * y)], 1)
+    kinds = set()
+    for lam in slm.wavelengths:
+        FX, FY, FZ = grid_freqs(slm, lam)
+        for i in range(n):
+            gi = n3[i, 0] * FX + n3[i, 1] * FY + n3[i, 2] * FZ
+            for r0 in range(0, slm.H, 64):
+                for c0 in range(0, slm.W, 64):
+                    t = gi[r0:r0 + 64, c0:c0 + 64]
+                    kinds.add("mixed" if t.min() < 0 < t.max() else ("pos" if t.min() > 0 else "neg"))
+    assert kinds == {"mixed", "pos", "neg"}, kinds
+    G = cotangent(43, slm)
+    got = gws.backward(dev(sc), slm, torch.as_tensor(G, device="cuda"))
+    _cmp(got, O.backward_field(sc, slm, G.astype(np.complex128)))
+    u = gws.forward(dev(sc), slm, domain=gws.DOMAIN_SPECTRUM).cpu().numpy()
+    assert rel_l2(u, O.spectrum(sc, slm)) < TOL
+
+
 def test_backward_is_deterministic():
     slm = SLM(96, 128, 8e-6, 8e-6, (638e-9, 520e-9))
     sc = surface_scene(8, 400, slm, n_surfaces=4)
