@@ -401,25 +401,25 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                     for (int seg = row_lo / BSEG; seg <= row_hi / BSEG; ++seg) {
                         const int s_lo = max(row_lo, seg * BSEG), s_hi = min(row_hi, seg * BSEG + BSEG - 1);
                         const float dys = fmaf((float)(seg * BSEG + BSEG / 2), dfyf, dyb);  // dy of the middle row
-                        const float dyrb = dyb - dys;
                         float2 ts = __ffma2_rn(ty, pair(dys), tc);
                         {
                             const float2 kt = __fadd2_rn(__ffma2_rn(ts, pair(0.15915494309189535f), pair(12582912.0f)),
                                                          pair(-12582912.0f));
                             ts = __ffma2_rn(kt, pair(-6.28318530717958647692f), ts);
                         }
+                        // t_y dy + ts is the reduced phase plus t_y (dy - dy_s): one rounding of t_y dy_s here
+                        ts = __ffma2_rn(ty, pair(-dys), ts);
                         // one row = the lane's two columns as one f32x2 pair; up to eight rows in flight
 #pragma unroll 8
                         for (int row = s_lo; row <= s_hi; ++row) {
                             const float2 dy = pair(fmaf((float)row, dfyf, dyb));
-                            const float2 dyr = pair(fmaf((float)row, dfyf, dyrb));
                             const float4 T4 = S.t[32 * row + lane];
                             const float2 ps = S.ps[32 * row + lane];
                             const float2 dz = make_float2(T4.x, T4.y), lw = make_float2(T4.z, T4.w);
                             const float2 a = __ffma2_rn(az, dz, __ffma2_rn(ay, dy, ac));
                             const float2 b = __ffma2_rn(bz, dz, __ffma2_rn(by, dy, bc));
                             const float2 g = __ffma2_rn(gz, dz, __ffma2_rn(gy, dy, gc));
-                            const float2 ang = __ffma2_rn(tz, dz, __fadd2_rn(__ffma2_rn(ty, dyr, ts), ps));  // phi - arg G
+                            const float2 ang = __ffma2_rn(tz, dz, __fadd2_rn(__ffma2_rn(ty, dy, ts), ps));  // phi - arg G
                             const float2 uq = __ffma2_rn(a, a, __ffma2_rn(b, b, lw));  // a'^2 + b'^2 + log2(f_z / |G|)
                             float2 es = make_float2(ex2_approx(-uq.x), ex2_approx(-uq.y));
                             if constexpr (SIGNED) es = make_float2(with_sign_of(es.x, g.x), with_sign_of(es.y, g.y));
