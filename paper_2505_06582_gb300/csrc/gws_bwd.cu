@@ -409,8 +409,8 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                         }
                         // t_y dy + ts is the reduced phase plus t_y (dy - dy_s): one rounding of t_y dy_s here
                         ts = __ffma2_rn(ty, pair(-dys), ts);
-                        // one row = the lane's two columns as one f32x2 pair; up to eight rows in flight
-#pragma unroll 8
+                        // one row = the lane's two columns as one f32x2 pair; up to sixteen rows in flight
+#pragma unroll 16
                         for (int row = s_lo; row <= s_hi; ++row) {
                             const float2 dy = pair(fmaf((float)row, dfyf, dyb));
                             const float4 T4 = S.t[32 * row + lane];
