@@ -111,6 +111,8 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
     constexpr int NT = (TW / PX) * TH;
     constexpr int NW = NT / 32;          // warps = row bands of the tile
     constexpr int RPW = 32 / (TW / PX);  // tile rows per warp
+    // records unrolled in the hot loop (four measured best; two where three CTAs share an SM's registers)
+    constexpr int UNR = MINB >= 3 ? 2 : 4;
     // a chunk holds up to one record per thread (threads past the chunk cull nothing)
     static_assert(CHUNK <= NT && CHUNK <= 256 && CHUNK % 32 == 0 && (TW / PX) <= 32 && 32 % (TW / PX) == 0,
                   "chunk / tile shape");
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
                         splat_record<PH, NPOLY>(s_sv + lst[i + 1] * 4, dy, dxm, dx, dz, lfz, acc2_re, acc2_im);
                     }
                 }
-#pragma unroll 2
+#pragma unroll(UNR)
                 for (; i < cnt; ++i) splat_record<PH, NPOLY>(s_sv + lst[i] * 4, dy, dxm, dx, dz, lfz, acc_re, acc_im);
             }
             if (RU == 2) {
