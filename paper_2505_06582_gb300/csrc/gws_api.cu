@@ -1123,7 +1123,7 @@ gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, c
     a.phase_match = opts->phase_match ? 1 : 0;
     const int B = bwd_block_size();
     a.n_items = (int)(nl * ((n + B - 1) / B));
-    const int grid = (int)std::min<long long>(a.n_items, (long long)num_sms() * 2);
+    const int grid = (int)std::min<long long>(a.n_items, (long long)num_sms() * bwd_ctas_per_sm());
     timer_mark(opts, GWS_TIMER_SPLAT_BWD, 0, s);
     CU(launch_splat_bwd(a, grid, s));
     timer_mark(opts, GWS_TIMER_SPLAT_BWD, 1, s);

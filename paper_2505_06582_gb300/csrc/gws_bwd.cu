@@ -6,7 +6,7 @@
 //
 // The spectra are recomputed, never stored.  A work item is a block of BB consecutive
 // records of one wavelength (footprint order, so a block's footprints are alike).  The CTA
-// walks the 64 x 64 frequency tiles of the block's footprint union; per tile it stages two
+// walks the 64 x 48 frequency tiles of the block's footprint union; per tile it stages two
 // per-pixel tables in shared memory with cp.async from copies laid out tile by tile
 // (k_bwd_tables: (f_z - f0_z, log2 f_z - log2 |G|) and -arg G, padded past the grid so that a
 // tile is one contiguous block per table, and a lane's two columns c and c + 32 of a row sit
@@ -16,7 +16,7 @@
 // the record's r3, so that its pixels skip their own) and hands the survivors to its warps
 // through a shared counter; a warp
 // takes one record over the tile (lane = column pair, rows in a loop, the phase re-anchored
-// per 32-row segment), accumulating 16 FP32 partial sums per column; these are reduced across
+// once per tile), accumulating 16 FP32 partial sums per column; these are reduced across
 // the warp and merged per tile into 13 FP64 totals per record in shared memory:
 //   TA = sum R a' d,  TB = sum R b' d,  TG = sum sign(g) Re(P0) f,  TI = sum I f,  SI = sum I,
 // with P0 = conj(G) f_z^-1 2^-(a'^2+b'^2) e^{j phi},  R = |g| Re(P0),  I = |g| Im(P0),
@@ -29,14 +29,19 @@
 
 namespace gws {
 
-constexpr int BTW = 64, BTH = 64, BPX = BTW * BTH;
-constexpr int BSEG = 32;     // rows per phase segment (the phase is re-anchored at each segment's middle row)
+constexpr int BTW = 64, BTH = 48, BPX = BTW * BTH;
+constexpr int BSEG = 48;     // rows per phase segment (one per tile: the phase is re-anchored at its middle row,
+                             // so the rows' |t_y (dy - dy_s)| stays within 24 rows' worth)
 constexpr int BQ = BPX / 2;  // column pairs per tile (entries of each table)
 constexpr int BB = 128;   // records per work item
 constexpr int BNT = 256;  // threads per CTA
+constexpr int BCTA = 3;   // resident CTAs per SM (registers per thread: 65536 / (BCTA BNT))
 constexpr int NTOT = 13;
 
+static_assert(BTH % 2 == 0 && BQ % (2 * BNT) == 0, "tile tables are copied in whole 16-byte pieces per thread");
+
 int bwd_block_size() { return BB; }
+int bwd_ctas_per_sm() { return BCTA; }
 
 struct TileConst {  // geometry of the current tile, computed once by thread 0
     double f0x, f0y, f0z, dz0;
@@ -72,6 +77,7 @@ struct BwdShared {
     int tx0, tx1, ty0, ty1;
     int item;
 };
+static_assert(BCTA * (sizeof(BwdShared) + 1024) <= 228 * 1024, "BCTA CTAs must fit an SM's shared memory");
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
@@ -207,7 +213,7 @@ __global__ void k_bwd_tables(const float2 *__restrict__ G, int n_lambda, int H, 
     ps[idx] = make_float2(ph[0], ph[1]);
 }
 
-__global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ BwdArgs A) {
+__global__ void __launch_bounds__(BNT, BCTA) k_splat_bwd(const __grid_constant__ BwdArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BwdShared &S = *reinterpret_cast<BwdShared *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -267,8 +273,9 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
         const float4 *tsl = A.tab + (size_t)l * ntiles * BQ;
         const float2 *psl = A.ps + (size_t)l * ntiles * BQ;
 
-        // one buffer per table (the tables of a 64 x 64 tile take 48 KB): the copy of tile t
-        // overlaps its cull; the CTA's other resident CTA covers the rest of the wait
+        // one buffer per table (the tables of a 64 x 48 tile take 36 KB, so that three CTAs of 80
+        // registers a thread fit an SM): the copy of tile t overlaps its cull; the other resident
+        // CTAs cover the rest of the wait
         for (int t = 0; t < n_t; ++t) {
             {
                 size_t tile = (size_t)(S.ty0 + t / ntx) * A.tiles_x + (S.tx0 + t % ntx);
@@ -409,8 +416,8 @@ __global__ void __launch_bounds__(BNT, 2) k_splat_bwd(const __grid_constant__ Bw
                         }
                         // t_y dy + ts is the reduced phase plus t_y (dy - dy_s): one rounding of t_y dy_s here
                         ts = __ffma2_rn(ty, pair(-dys), ts);
-                        // one row = the lane's two columns as one f32x2 pair; up to sixteen rows in flight
-#pragma unroll 16
+                        // one row = the lane's two columns as one f32x2 pair; up to 24 rows in flight
+#pragma unroll 24
                         for (int row = s_lo; row <= s_hi; ++row) {
                             const float2 dy = pair(fmaf((float)row, dfyf, dyb));
                             const float4 T4 = S.t[32 * row + lane];
@@ -577,6 +584,10 @@ cudaError_t prepare_bwd_kernels() {
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
     e = cudaFuncSetAttribute(k_splat_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BwdShared));
+    // BCTA CTAs' shared memory per SM needs the largest shared-memory carveout
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_splat_bwd, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
     return e;
 }

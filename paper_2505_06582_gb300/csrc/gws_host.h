@@ -135,6 +135,7 @@ cudaError_t launch_grad_assemble(const GPre *gp, const float *ampc, const double
                                  const double *acc, const float *quat_in, long long n, int L, const GradArgs &G,
                                  cudaStream_t s);
 int bwd_block_size();
+int bwd_ctas_per_sm();
 int bwd_tiles_x(int W);
 int bwd_tiles_y(int H);
 size_t bwd_table_bytes(int n_lambda, int H, int W);  // one float4 tile-major table (the float2 one takes half)
