@@ -50,17 +50,6 @@ struct TileConst {  // geometry of the current tile, computed once by thread 0
     int c_lo, r_lo, c_ref, r_ref;
 };
 
-// The sign of g = r3.f over a tile when it is the same at every pixel (+1 / -1), else 0: g is
-// linear in (f_x, f_y, f_z), so its bounds over the box [x0, x1] x [y0, y1] x [fzlo, fzhi] are
-// sums of per-axis extremes; a margin covers the FP32 evaluation of g per pixel.
-__device__ __forceinline__ int tile_sign(float r3x, float r3y, float r3z, const TileConst &T) {
-    const float lo = fminf(r3x * T.x0, r3x * T.x1) + fminf(r3y * T.y0, r3y * T.y1) + fminf(r3z * T.fzlo, r3z * T.fzhi);
-    const float hi = fmaxf(r3x * T.x0, r3x * T.x1) + fmaxf(r3y * T.y0, r3y * T.y1) + fmaxf(r3z * T.fzlo, r3z * T.fzhi);
-    const float tol = 1e-5f * (fabsf(r3x) * fmaxf(fabsf(T.x0), fabsf(T.x1)) + fabsf(r3y) * fmaxf(fabsf(T.y0), fabsf(T.y1)) +
-                               fabsf(r3z) * T.fzhi);
-    return lo > tol ? 1 : (hi < -tol ? -1 : 0);
-}
-
 struct BwdShared {
     float4 t[BQ];   // [row][lane]: (dz(c), dz(c + 32), lw(c), lw(c + 32)), c = c_lo + lane, lw = log2(f_z / |G|)
     float2 ps[BQ];  // [row][lane]: (-arg G(c), -arg G(c + 32))
@@ -309,14 +298,8 @@ __global__ void __launch_bounds__(BNT, BCTA) k_splat_bwd(const __grid_constant__
                 T.x1 = (float)((double)(c_hi - A.W / 2) * A.dfx);
                 T.y0 = (float)((double)(T.r_lo - A.H / 2) * A.dfy);
                 T.y1 = (float)((double)(r_hi - A.H / 2) * A.dfy);
-                {  // |f| over the rectangle: nearest and farthest point from f = 0
-                    const double x0 = (double)(T.c_lo - A.W / 2) * A.dfx, x1 = (double)(c_hi - A.W / 2) * A.dfx;
-                    const double y0 = (double)(T.r_lo - A.H / 2) * A.dfy, y1 = (double)(r_hi - A.H / 2) * A.dfy;
-                    const double nx = x0 > 0.0 ? x0 : (x1 < 0.0 ? x1 : 0.0), ny = y0 > 0.0 ? y0 : (y1 < 0.0 ? y1 : 0.0);
-                    const double fx = fmax(fabs(x0), fabs(x1)), fy = fmax(fabs(y0), fabs(y1));
-                    T.fzhi = (float)sqrt(fmax(k2 - (nx * nx + ny * ny), 0.0));
-                    T.fzlo = (float)sqrt(fmax(k2 - (fx * fx + fy * fy), 0.0));
-                }
+                fz_range((double)(T.c_lo - A.W / 2) * A.dfx, (double)(c_hi - A.W / 2) * A.dfx,
+                         (double)(T.r_lo - A.H / 2) * A.dfy, (double)(r_hi - A.H / 2) * A.dfy, k2, T.fzlo, T.fzhi);
             }
             __syncthreads();
             const int c_lo = S.tc.c_lo, r_lo = S.tc.r_lo, c_ref = S.tc.c_ref, r_ref = S.tc.r_ref;
@@ -347,7 +330,8 @@ __global__ void __launch_bounds__(BNT, BCTA) k_splat_bwd(const __grid_constant__
                         S.sv[tid][1] = make_float4(r.r2x, r.r2y, r.r2z, fmaf(r.r2z, dzf, fmaf(r.r2y, fyf, r.r2x * fxf)));
                         // where g keeps one sign over the tile it is folded into r3 (g' = |g|), so that the
                         // pixels need no sign of their own; the Rg moments are multiplied back by it
-                        const int sg = tile_sign(r.r3x, r.r3y, r.r3z, S.tc);
+                        const int sg =
+                            sign_over_box(r.r3x, r.r3y, r.r3z, S.tc.x0, S.tc.x1, S.tc.y0, S.tc.y1, S.tc.fzlo, S.tc.fzhi);
                         const float sf = sg < 0 ? -1.f : 1.f;
                         S.sgn[tid] = (signed char)sg;
                         S.sv[tid][2] = make_float4(sf * r.r3x, sf * r.r3y, sf * r.r3z,

@@ -219,6 +219,28 @@ __host__ __device__ __forceinline__ void tile_ref(int c_lo, int c_hi, int r_lo, 
     }
 }
 
+// Range [fzlo, fzhi] of f_z = sqrt(1/lambda^2 - f_x^2 - f_y^2) over the frequency rectangle
+// [x0, x1] x [y0, y1] (FP64): its points nearest to and farthest from f = 0 (0 where evanescent).
+__host__ __device__ __forceinline__ void fz_range(double x0, double x1, double y0, double y1, double k2, float &fzlo,
+                                                  float &fzhi) {
+    const double nx = x0 > 0.0 ? x0 : (x1 < 0.0 ? x1 : 0.0), ny = y0 > 0.0 ? y0 : (y1 < 0.0 ? y1 : 0.0);
+    const double fx = fmax(fabs(x0), fabs(x1)), fy = fmax(fabs(y0), fabs(y1));
+    fzhi = (float)sqrt(fmax(k2 - (nx * nx + ny * ny), 0.0));
+    fzlo = (float)sqrt(fmax(k2 - (fx * fx + fy * fy), 0.0));
+}
+
+// The sign of g = r3.f over the box [x0, x1] x [y0, y1] x [fzlo, fzhi] when it is the same at
+// every point (+1 / -1), else 0: g is linear in f, so its bounds are sums of per-axis extremes;
+// a margin of 1e-5 of its terms covers the FP32 evaluation of g at a pixel.
+__device__ __forceinline__ int sign_over_box(float r3x, float r3y, float r3z, float x0, float x1, float y0, float y1,
+                                             float fzlo, float fzhi) {
+    const float lo = fminf(r3x * x0, r3x * x1) + fminf(r3y * y0, r3y * y1) + fminf(r3z * fzlo, r3z * fzhi);
+    const float hi = fmaxf(r3x * x0, r3x * x1) + fmaxf(r3y * y0, r3y * y1) + fmaxf(r3z * fzlo, r3z * fzhi);
+    const float tol = 1e-5f * (fabsf(r3x) * fmaxf(fabsf(x0), fabsf(x1)) + fabsf(r3y) * fmaxf(fabsf(y0), fabsf(y1)) +
+                               fabsf(r3z) * fzhi);
+    return lo > tol ? 1 : (hi < -tol ? -1 : 0);
+}
+
 // Centred-DFT modulation angle, in cycles: ((a * b) mod n) / n, exact integer reduction.
 __device__ __forceinline__ double mod_frac(long long a, long long b, long long n) {
     long long m = (a * b) % n;
