@@ -14,14 +14,16 @@
 // exponential and a shift of the phase, so conj(G) P0 costs no complex product.  It culls
 // each record exactly (and where g = r3.f keeps one sign over the tile, folds that sign into
 // the record's r3, so that its pixels skip their own) and hands the survivors to its warps
-// through a shared counter; a warp
-// takes one record over the tile (lane = column pair, rows in a loop, the phase re-anchored
-// once per tile), accumulating 16 FP32 partial sums per column; these are reduced across
-// the warp and merged per tile into 13 FP64 totals per record in shared memory:
+// through a shared counter; a warp takes one record over the tile (lane = column pair, rows
+// in a loop, the phase re-anchored once per tile), accumulating 16 FP32 partial sums per
+// column; these are reduced across the warp and merged per tile into 13 FP64 totals per
+// record in shared memory:
 //   TA = sum R a' d,  TB = sum R b' d,  TG = sum sign(g) Re(P0) f,  TI = sum I f,  SI = sum I,
 // with P0 = conj(G) f_z^-1 2^-(a'^2+b'^2) e^{j phi},  R = |g| Re(P0),  I = |g| Im(P0),
 // g = r3.f, d = f - f_r.  A record's totals are only touched by the warp holding it in the
 // current tile, and tiles are visited in a fixed order, so the result is deterministic.
+// Three CTAs share an SM (80 registers a thread): the kernel is bound by its FP32 work, and
+// with 24 resident warps the FMA pipe stays busier than with 16 warps at more registers.
 #include <type_traits>
 #include <float.h>
 
