@@ -37,6 +37,8 @@ CASES = [
     ("rgb_ragged", SLM(72, 100, 8e-6, 6e-6, (638e-9, 520e-9, 450e-9)), "surface", 1, 50),
     ("odd", SLM(37, 45, 8e-6, 8e-6, (520e-9,)), "uniform", 2, 12),
     ("single", SLM(40, 48, 8e-6, 8e-6, (638e-9, 450e-9)), "uniform", 3, 1),
+    # 97 rows = two 48-row tiles and a last tile of one row
+    ("one_row_tail", SLM(97, 70, 8e-6, 6e-6, (520e-9,)), "surface", 4, 40),
 ]
 
 
