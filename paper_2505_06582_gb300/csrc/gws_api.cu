@@ -756,6 +756,10 @@ static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, in
         a.dfx = dfx;
         a.dfy = dfy;
         for (int l = 0; l < nl; ++l) a.inv_lam[l] = 1.0 / slm->wavelengths[l];
+        {
+            const FootParams FPa = foot_params(slm, o);
+            for (int l = 0; l < nl; ++l) a.dzmax[l] = FPa.dzmax[l];
+        }
         a.field_mode = fft ? 1 : 0;
         a.phase_match = o->phase_match ? 1 : 0;
         a.timeout = o->timeout_cycles;
@@ -1120,6 +1124,10 @@ gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, c
     a.dfx = dfx;
     a.dfy = dfy;
     for (int l = 0; l < nl; ++l) a.inv_lam[l] = il.v[l];
+    {
+        const FootParams FPa = foot_params(slm, opts);
+        for (int l = 0; l < nl; ++l) a.dzmax[l] = FPa.dzmax[l];
+    }
     a.phase_match = opts->phase_match ? 1 : 0;
     const int B = bwd_block_size();
     a.n_items = (int)(nl * ((n + B - 1) / B));

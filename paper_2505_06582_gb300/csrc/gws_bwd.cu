@@ -49,6 +49,7 @@ struct TileConst {  // geometry of the current tile, computed once by thread 0
     double f0x, f0y, f0z, dz0;
     float x0, x1, y0, y1;
     float fzlo, fzhi;  // range of f_z over the tile's valid pixels (0 where evanescent)
+    float dzt;         // bound on |f_z - 1/lambda| over them
     int c_lo, r_lo, c_ref, r_ref;
 };
 
@@ -302,6 +303,8 @@ __global__ void __launch_bounds__(BNT, BCTA) k_splat_bwd(const __grid_constant__
                 T.y1 = (float)((double)(r_hi - A.H / 2) * A.dfy);
                 fz_range((double)(T.c_lo - A.W / 2) * A.dfx, (double)(c_hi - A.W / 2) * A.dfx,
                          (double)(T.r_lo - A.H / 2) * A.dfy, (double)(r_hi - A.H / 2) * A.dfy, k2, T.fzlo, T.fzhi);
+                T.dzt = (float)dz_far((double)(T.c_lo - A.W / 2) * A.dfx, (double)(c_hi - A.W / 2) * A.dfx,
+                                      (double)(T.r_lo - A.H / 2) * A.dfy, (double)(r_hi - A.H / 2) * A.dfy, inv_lam);
             }
             __syncthreads();
             const int c_lo = S.tc.c_lo, r_lo = S.tc.r_lo, c_ref = S.tc.c_ref, r_ref = S.tc.r_ref;
@@ -311,13 +314,16 @@ __global__ void __launch_bounds__(BNT, BCTA) k_splat_bwd(const __grid_constant__
                 if (tid < nrec) {
                     const Rec &r = S.rec[tid];
                     const double f0x = S.tc.f0x, f0y = S.tc.f0y, f0z = S.tc.f0z, dz0 = S.tc.dz0;
-                    pass = ellipse_hits_rect_b(r.e00, r.e01, r.e11, S.tc.x0, S.tc.x1, S.tc.y0, S.tc.y1);
+                    // the footprint for this tile's bound on |d_z| (within the grid-wide one)
+                    const float sc = footprint_scale(A.dzmax[l], S.tc.dzt, r.wz);
+                    const float e00 = r.e00 * sc, e01 = r.e01 * sc, e11 = r.e11 * sc;
+                    pass = ellipse_hits_rect_b(e00, e01, e11, S.tc.x0, S.tc.x1, S.tc.y0, S.tc.y1);
                     if (pass) {
                         // rows of the tile inside the footprint's bounding box
-                        const float det = r.e00 * r.e11 - r.e01 * r.e01;
+                        const float det = e00 * e11 - e01 * e01;
                         int rlo = 0, rhi = BTH - 1;
                         if (det > 0.f) {
-                            const float hy = sqrtf(r.e00 / det) * 1.001f + 1e-3f * (float)A.dfy;
+                            const float hy = sqrtf(e00 / det) * 1.001f + 1e-3f * (float)A.dfy;
                             const float dfyf = (float)A.dfy;
                             rlo = max(0, (int)ceilf((-hy - S.tc.y0) / dfyf));
                             rhi = min(BTH - 1, (int)floorf((hy - S.tc.y0) / dfyf));

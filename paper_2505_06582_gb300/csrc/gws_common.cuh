@@ -61,8 +61,8 @@ struct alignas(16) Rec {
     float e00, e01, e11, W;
     double mux, muy;
     double muz;
-    int g;  // global (concatenated) Gaussian index
-    int pad;
+    int g;     // global (concatenated) Gaussian index
+    float wz;  // |(s_u r1z, s_v r2z)| / rho': how fast the footprint shrinks with the tile's bound on |d_z|
 };
 static_assert(sizeof(Rec) == 96, "record must stay 96 bytes");
 
@@ -239,6 +239,21 @@ __device__ __forceinline__ int sign_over_box(float r3x, float r3y, float r3z, fl
     const float tol = 1e-5f * (fabsf(r3x) * fmaxf(fabsf(x0), fabsf(x1)) + fabsf(r3y) * fmaxf(fabsf(y0), fabsf(y1)) +
                                fabsf(r3z) * fzhi);
     return lo > tol ? 1 : (hi < -tol ? -1 : 0);
+}
+
+// The largest |f_z - 1/lambda| over the frequency rectangle [x0, x1] x [y0, y1]: at its point
+// farthest from f = 0 (1/lambda where that point is evanescent).
+__host__ __device__ __forceinline__ double dz_far(double x0, double x1, double y0, double y1, double inv_lam) {
+    const double fx = fmax(fabs(x0), fabs(x1)), fy = fmax(fabs(y0), fabs(y1));
+    return inv_lam - sqrt(fmax(inv_lam * inv_lam - (fx * fx + fy * fy), 0.0));
+}
+
+// The footprint ellipse of a record over a tile whose |d_z| stays within dzt, from the grid-wide
+// one (built for |d_z| <= dzmax): rho' shrinks to rho + dzt |(s_u r1z, s_v r2z)|, i.e. by the factor
+// rt = 1 - (dzmax - dzt) wz, and the ellipse's matrix grows by 1 / rt^2.
+__device__ __forceinline__ float footprint_scale(float dzmax, float dzt, float wz) {
+    const float rt = 1.f - fmaxf(dzmax - dzt, 0.f) * wz;
+    return 1.f / (rt * rt);
 }
 
 // Centred-DFT modulation angle, in cycles: ((a * b) mod n) / n, exact integer reduction.

@@ -57,6 +57,7 @@ struct SplatArgs {
     int H, W, tiles_x, n_tiles;
     double dfx, dfy;
     double inv_lam[GWS_MAX_LAMBDA];
+    float dzmax[GWS_MAX_LAMBDA];  // the grid-wide |d_z| bound the records' footprints were built for
     int field_mode;  // 1: multiply by the centred-DFT pre-modulation
     int phase_match;
     unsigned long long timeout;
@@ -97,6 +98,7 @@ struct BwdArgs {
     int H, W, tiles_x, tiles_y;
     double dfx, dfy;
     double inv_lam[GWS_MAX_LAMBDA];
+    float dzmax[GWS_MAX_LAMBDA];  // the grid-wide |d_z| bound the records' footprints were built for
     int phase_match;
     int n_items;            // (wavelength, block of records) work items
 };

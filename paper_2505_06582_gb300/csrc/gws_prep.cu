@@ -348,6 +348,7 @@ __global__ void k_rec64(const GPre *__restrict__ gp, const float *__restrict__ a
 
 struct Foot {
     float e00, e01, e11, R;
+    float wz;  // |(s_u r1z, s_v r2z)| / rho' (rho' before the 1.0005 margin)
 };
 
 // Frequencies with |M^T f| > rho' have E = 2 pi^2 (s_u^2 a^2 + s_v^2 b^2) > ln(1/eps): with
@@ -360,7 +361,9 @@ __device__ __forceinline__ Foot footprint(const float r1[3], const float r2[3], 
                                           float dzmax) {
     const float m00 = su * r1[0], m01 = sv * r2[0], m10 = su * r1[1], m11 = sv * r2[1];
     const float a00 = m00 * m00 + m01 * m01, a01 = m00 * m10 + m01 * m11, a11 = m10 * m10 + m11 * m11;
-    float rp = rho + dzmax * sqrtf(su * su * r1[2] * r1[2] + sv * sv * r2[2] * r2[2]);
+    const float cz = sqrtf(su * su * r1[2] * r1[2] + sv * sv * r2[2] * r2[2]);
+    float rp = rho + dzmax * cz;
+    const float wz = cz / rp;
     rp *= 1.0005f;
     const float inv = 1.f / (rp * rp);
     Foot f;
@@ -374,6 +377,7 @@ __device__ __forceinline__ Foot footprint(const float r1[3], const float r2[3], 
     const float lmax = half + disc;
     const float lmin = lmax > 0.f ? det2 / lmax : 0.f;
     f.R = (lmin > 1e-30f * lmax && lmin > 0.f) ? 1.002f * rp / sqrtf(lmin) : FLT_MAX;
+    f.wz = wz;
     return f;
 }
 
@@ -478,7 +482,7 @@ __global__ void k_gather(const unsigned long long *__restrict__ key, const unsig
     r.muy = G.mu[1];
     r.muz = G.mu[2];
     r.g = (int)g;
-    r.pad = 0;
+    r.wz = f.wz;
     rec[k] = r;
     Rr[k] = (drop_zero && W == 0.f) ? -1.f : f.R;
     if (invrec) invrec[(size_t)g * S.n_lambda + l] = (int)k;

@@ -126,6 +126,7 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
     __shared__ uint64_t s_full[STAGES];
     __shared__ uint64_t s_never;
     __shared__ unsigned char s_cnt[NW][NW];
+    __shared__ float s_dzt;  // the current tile's bound on |f_z - 1/lambda|
     __shared__ int s_item;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -198,6 +199,9 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
         // tile rectangle (pixel-centre frequencies of the valid pixels) for the cull
         const float x0 = (float)((double)(c_lo - A.W / 2) * A.dfx), x1 = (float)((double)(c_hi - A.W / 2) * A.dfx);
         const float y0 = (float)((double)(r_lo - A.H / 2) * A.dfy), y1 = (float)((double)(r_hi - A.H / 2) * A.dfy);
+        if (tid == 0)  // read by the cull, after the barrier that opens each chunk
+            s_dzt = (float)dz_far((double)(c_lo - A.W / 2) * A.dfx, (double)(c_hi - A.W / 2) * A.dfx,
+                                  (double)(r_lo - A.H / 2) * A.dfy, (double)(r_hi - A.H / 2) * A.dfy, inv_lam);
 
         const int n_chunks = (count + CHUNK - 1) / CHUNK;
         int issued = 0, consumed = 0;
@@ -244,12 +248,15 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
                 unsigned bands = 0;
                 if (tid < nrec) {
                     const Rec &r = s_rec[st * CHUNK + tid];
-                    if (ellipse_hits_rect(r.e00, r.e01, r.e11, x0, x1, y0, y1)) {
+                    // the footprint for this tile's bound on |d_z| (within the grid-wide one)
+                    const float sc = footprint_scale(A.dzmax[l], s_dzt, r.wz);
+                    const float e00 = r.e00 * sc, e01 = r.e01 * sc, e11 = r.e11 * sc;
+                    if (ellipse_hits_rect(e00, e01, e11, x0, x1, y0, y1)) {
 #pragma unroll
                         for (int w = 0; w < NW; ++w) {
                             const float yb0 = fmaf((float)(w * RPW), dfyf, y0);
                             const float yb1 = fminf(fmaf((float)(RPW - 1), dfyf, yb0), y1);
-                            if (yb0 <= y1 && ellipse_hits_rect(r.e00, r.e01, r.e11, x0, x1, yb0, yb1)) bands |= 1u << w;
+                            if (yb0 <= y1 && ellipse_hits_rect(e00, e01, e11, x0, x1, yb0, yb1)) bands |= 1u << w;
                         }
                     }
                     if (bands) {
