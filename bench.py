@@ -36,8 +36,8 @@ METRIC = "holograms/s (1M Gaussians, 1920x1080, 3 λ) fwd & fwd+bwd; Gaussian·f
 WORKLOAD = "headline_1m_1080p_3l"
 # DRAM bytes (read + write) of one launch of each splat on the headline workload, from
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` of the kernels as they stand
-SPLAT_TRAFFIC_MB = None    # to be re-taken for the per-tile footprint cull
-BWD_TRAFFIC_MB = None      # to be re-taken for the per-tile footprint cull
+SPLAT_TRAFFIC_MB = 1626.4  # 1559.54 MB read + 66.82 MB written (per-tile footprint cull, configuration 1)
+BWD_TRAFFIC_MB = 686.4     # 397.12 MB read + 289.25 MB written (per-tile footprint cull)
 # Per (Gaussian, frequency) pair: the forward needs ex2, sin and cos on the MUFU (32, 16, 16 per
 # SM per clock): 1 / (1/32 + 2/16) = 6.4 pairs/clk/SM; its 14 FP32 lane-ops (8 affine, 2 exponent,
 # 1 |g| e, 1 sin/cos prescale, 2 accumulations; the phase is reduced once per (record, thread))
