@@ -36,8 +36,9 @@ METRIC = "holograms/s (1M Gaussians, 1920x1080, 3 λ) fwd & fwd+bwd; Gaussian·f
 WORKLOAD = "headline_1m_1080p_3l"
 # DRAM bytes (read + write) of one launch of each splat on the headline workload, from
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` of the kernels as they stand
-SPLAT_TRAFFIC_MB = 1626.4  # 1559.54 MB read + 66.82 MB written (per-tile footprint cull, configuration 1)
-BWD_TRAFFIC_MB = 686.4     # 397.12 MB read + 289.25 MB written (per-tile footprint cull)
+# (forward: per autotuner configuration, the one the bench's tuner picks)
+SPLAT_TRAFFIC_MB = {1: 1592.8}  # configuration 1: 1527.00 MB read + 65.79 MB written (per-tile footprint cull)
+BWD_TRAFFIC_MB = 685.8     # 396.52 MB read + 289.29 MB written (per-tile footprint cull)
 # Per (Gaussian, frequency) pair: the forward needs ex2, sin and cos on the MUFU (32, 16, 16 per
 # SM per clock): 1 / (1/32 + 2/16) = 6.4 pairs/clk/SM; its 14 FP32 lane-ops (8 affine, 2 exponent,
 # 1 |g| e, 1 sin/cos prescale, 2 accumulations; the phase is reduced once per (record, thread))
@@ -49,8 +50,18 @@ FWD_PAIRS_PER_CLK = 6.4
 # A configuration that takes the cos of a fraction f of the pixels on the FP32 pipe (an 11 lane-op
 # polynomial with its reduction) needs 1/32 + 1/16 + (1 - f)/16 MUFU cycles and 14 + 11 f FP32
 # lane-ops per pair: its bound is the smaller of the two rates.
+# A column-step configuration evaluates every second pixel pair as its left neighbour's phase
+# factor times one per-record rotation (2 sin/cos per record and thread of 8 pixels) and a
+# first-order residual: per pair 1/32 + 1.25/16 MUFU cycles (9.14 pairs/clk/SM) and
+# (14 + 18) / 2 = 16 FP32 lane-ops (8.0 pairs/clk/SM, the bound).
+FWD_STEP_PAIRS_PER_CLK = min(1.0 / (1.0 / 32 + 1.25 / 16), 128.0 / 16.0)
+
+
 def fwd_pairs_per_clk(cfg_desc) -> tuple[float, str]:
     f = 0.0
+    if cfg_desc and cfg_desc.get("column_step"):
+        return FWD_STEP_PAIRS_PER_CLK, ("FP32 bound of the column step (16 FP32 lane-ops per pair; MUFU "
+                                        "1/32 + 1.25/16 cycles -> 9.14 pairs/clk/SM)")
     if cfg_desc:
         f = 2.0 * cfg_desc.get("cos_pairs_on_fp32", 0) / cfg_desc["px_per_thread"]
     mufu = 1.0 / (1.0 / 32 + 1.0 / 16 + (1.0 - f) / 16)
@@ -104,6 +115,8 @@ def parse():
     p.add_argument("--tile-sweep", action="store_true",
                    help="time the forward splat of every autotuner configuration on the workload (3 calls each) and "
                         "print them as one JSON line")
+    p.add_argument("--tile-cfgs", default=None,
+                   help="--tile-sweep: comma-separated configuration ids to time (default: all)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
@@ -490,7 +503,7 @@ def run_ours(args):
         rooflines = {"splat_fwd": roof(
             "k_splat_fp64" if fp64 else "k_splat_mixed", splat, fwd_per_clk,
             fwd_basis + (" (FP32/MUFU peak; the FP64 path runs on the FP64 pipe)" if fp64 else ""),
-            args.traffic_mb if args.traffic_mb is not None else (SPLAT_TRAFFIC_MB if full_size else None),
+            args.traffic_mb if args.traffic_mb is not None else (SPLAT_TRAFFIC_MB.get(tile_cfg) if full_size else None),
             None if fp64 else FWD_PAIRS_PER_CLK_SURVEY,
             "survey count: 23 FP32 issues + 3 MUFU per pair -> min(128/23, 6.4) pairs/clk/SM")}
     if bwd_ms:
@@ -775,7 +788,10 @@ def run_tile_sweep(args):
     clocks = ClockSampler(local)
     clocks.start()
     rows = []
+    only = {int(x) for x in args.tile_cfgs.split(",")} if args.tile_cfgs else None
     for c, d in gws.tile_configs().items():
+        if only is not None and c not in only:
+            continue
         ts = []
         for _ in range(3):
             gws.forward(g, S, out=out, workspace=ws, tile_cfg=c, domain=gws.DOMAIN_SPECTRUM,

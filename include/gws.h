@@ -293,6 +293,13 @@ GWS_API int gws_last_launch_count(void);
  * pairs per thread whose cos runs on the FP32 pipe.  Host only. */
 GWS_API int gws_tile_config(int id, int *desc);
 
+/* gws_tile_config with the whole description: writes desc[0 .. min(n_desc, 9) - 1], the eight
+ * values above followed by desc[8] = 1 where the configuration evaluates every second pixel
+ * pair by the column step (its phase factor as the left neighbour's times one per-record
+ * rotation and a first-order residual; chunks whose residual would exceed 2e-3 rad fall back
+ * to the direct evaluation), else 0.  Host only. */
+GWS_API int gws_tile_config_ext(int id, int *desc, int n_desc);
+
 GWS_API gws_status gws_autotune(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
                         void *field_scratch, int *best_cfg);
 

@@ -839,15 +839,17 @@ const char *gws_status_string(gws_status s) {
 
 int gws_version(void) { return GWS_ABI_VERSION; }
 
-int gws_tile_config(int id, int *desc) {
+int gws_tile_config_ext(int id, int *desc, int n_desc) {
     const int n = n_tile_cfgs();
     if (desc && id >= 1 && id <= n) {
         const TileCfg c = tile_cfg(id);
-        const int v[8] = {c.tw, c.th, c.px, c.ru, c.chunk, c.stages, c.ctas, c.npoly};
-        for (int i = 0; i < 8; ++i) desc[i] = v[i];
+        const int v[9] = {c.tw, c.th, c.px, c.ru, c.chunk, c.stages, c.ctas, c.npoly, c.step};
+        for (int i = 0; i < 9 && i < n_desc; ++i) desc[i] = v[i];
     }
     return n;
 }
+
+int gws_tile_config(int id, int *desc) { return gws_tile_config_ext(id, desc, 8); }
 
 int gws_last_launch_count(void) { return t_launches; }
 

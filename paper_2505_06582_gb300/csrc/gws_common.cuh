@@ -140,6 +140,7 @@ __device__ __forceinline__ void quat_cols(const T q[4], T r1[3], T r2[3], T r3[3
 
 // packed f32x2 helpers: both lanes of a pair equal; sign(g) e for e >= 0 (g's sign bit on e)
 __device__ __forceinline__ float2 pair(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 neg2(float2 x) { return make_float2(-x.x, -x.y); }
 __device__ __forceinline__ float with_sign_of(float e, float g) {
     return __int_as_float(__float_as_int(e) ^ (__float_as_int(g) & 0x80000000));
 }

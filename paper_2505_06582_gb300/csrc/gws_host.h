@@ -42,6 +42,7 @@ struct TileCfg {
     int px, ru;       // pixels per thread, records evaluated per iteration
     int chunk, stages, ctas;  // Gaussian records per bulk-copied chunk, ring depth, CTAs per SM
     int npoly;        // pixel pairs per thread whose cos runs on the FP32 pipe (the rest on the MUFU)
+    int step;         // 1: the odd pixel pairs by the column step (sin/cos of the even pairs rotated)
 };
 int n_tile_cfgs();
 TileCfg tile_cfg(int id);  // id 1..n_tile_cfgs()

@@ -104,11 +104,87 @@ __device__ __forceinline__ void splat_record(const float4 *__restrict__ sv, floa
     }
 }
 
+// Pixel p of a thread's PX in the packed layout: pack and lane.  Layout 0 pairs neighbours
+// (p = 2h, 2h + 1).  Layout 1 (the column-step configurations) pairs p = 4k + {0, 2} in pack 2k and
+// p = 4k + {1, 3} in pack 2k + 1, so that each lane of an odd pack sits one column right of the
+// same lane of the even pack before it.
+// Largest |t_z| max|dl| of a record the column step takes: (1 + j e) errs from e^{j e} by
+// e^2 / 2 <= 2e-6 of the term.  On the 8 um and 3.74 um grids of 1920 and 3840 columns,
+// max|dl| <= 0.0095 / m, so every record with |mu_z| <= 33 mm qualifies.
+constexpr float kStepEps = 2e-3f;
+
+template <int LAYOUT>
+__host__ __device__ constexpr int pix_of(int h, int lane) {
+    return LAYOUT == 0 ? 2 * h + lane : (h & 1) + 4 * (h >> 1) + 2 * lane;
+}
+
+// Column-step variant of splat_record (layout 1): the even packs as in splat_record; each odd
+// pack, one column right, takes its linear forms a', b', g as the even pack's plus the record's
+// per-column steps (x-slope dfx + z-slope sbar, the thread's mean step of f_z, plus the z-slope
+// times the pixel's residual step dl: exact up to rounding) and its phase factor e^{j phi} as the even pack's
+// times e^{j beta} (beta = t_x dfx + t_z sbar, one sin/cos per record and thread) times
+// (1 + j t_z dl) for the residual.  The first-order residual errs by (t_z dl)^2 / 2: the cull
+// sends a chunk to splat_record instead whenever a record's |t_z| max|dl| over the tile exceeds
+// kStepEps.  The odd packs need no sin/cos of their own: per record and thread, 2 sin/cos in
+// place of 8, for 12 more FP32 lane-ops per odd pack.
+template <int PH>
+__device__ __forceinline__ void splat_record_step(const float4 *__restrict__ sv, float dy, float dxm,
+                                                  const float2 *ddx, const float2 *dz, const float2 *lfz,
+                                                  const float2 *dl, float sbar, float2 *acc_re, float2 *acc_im) {
+    const float4 Ar = sv[0], Br = sv[1], Gr = sv[2], Mr = sv[3], Xr = sv[4];
+    const float2 ar = pair(fmaf(Ar.x, dxm, fmaf(Ar.y, dy, Ar.w))), br = pair(fmaf(Br.x, dxm, fmaf(Br.y, dy, Br.w)));
+    const float2 gr = pair(fmaf(Gr.x, dxm, fmaf(Gr.y, dy, Gr.w)));
+    const float t0 = fmaf(Mr.x, dxm, fmaf(Mr.y, dy, Mr.w));
+    const float k0 = __fadd_rn(fmaf(t0, 0.15915494309189535f, 12582912.0f), -12582912.0f);
+    const float2 tr = pair(fmaf(k0, -6.28318530717958647692f, t0));
+    const float2 ax = pair(Ar.x), az = pair(Ar.z), bx = pair(Br.x), bz = pair(Br.z);
+    const float2 gx = pair(Gr.x), gz = pair(Gr.z), tx2 = pair(Mr.x), tz = pair(Mr.z);
+    // one column to the right: Xr = dfx (a'_x, b'_x, g_x, t_x); beta reduced to [-pi, pi]
+    const float beta0 = fmaf(Mr.z, sbar, Xr.w);
+    const float kb = __fadd_rn(fmaf(beta0, 0.15915494309189535f, 12582912.0f), -12582912.0f);
+    const float beta = fmaf(kb, -6.28318530717958647692f, beta0);
+    const float sb = sin_approx(beta);
+    const float2 qc = pair(cos_approx(beta)), qs = pair(sb), nqs = pair(-sb);
+    const float2 ca = pair(fmaf(Ar.z, sbar, Xr.x)), cb = pair(fmaf(Br.z, sbar, Xr.y));
+    const float2 cg = pair(fmaf(Gr.z, sbar, Xr.z));
+#pragma unroll
+    for (int h = 0; h + 1 < PH; h += 2) {
+        const float2 a = __ffma2_rn(az, dz[h], __ffma2_rn(ax, ddx[h], ar));
+        const float2 b = __ffma2_rn(bz, dz[h], __ffma2_rn(bx, ddx[h], br));
+        const float2 g = __ffma2_rn(gz, dz[h], __ffma2_rn(gx, ddx[h], gr));
+        const float2 ang = __ffma2_rn(tz, dz[h], __ffma2_rn(tx2, ddx[h], tr));
+        const float2 u = __ffma2_rn(a, a, __ffma2_rn(b, b, lfz[h]));
+        const float2 amp = __fmul2_rn(g, make_float2(with_sign_of(ex2_approx(-u.x), g.x),
+                                                     with_sign_of(ex2_approx(-u.y), g.y)));
+        const float2 cs = make_float2(cos_approx(ang.x), cos_approx(ang.y));
+        const float2 sn = make_float2(sin_approx(ang.x), sin_approx(ang.y));
+        acc_re[h] = __ffma2_rn(amp, cs, acc_re[h]);
+        acc_im[h] = __ffma2_rn(amp, sn, acc_im[h]);
+        // the odd pack h + 1, one column right of pack h
+        const float2 d = dl[h / 2];
+        const float2 a1 = __ffma2_rn(az, d, __fadd2_rn(a, ca));
+        const float2 b1 = __ffma2_rn(bz, d, __fadd2_rn(b, cb));
+        const float2 g1 = __ffma2_rn(gz, d, __fadd2_rn(g, cg));
+        const float2 u1 = __ffma2_rn(a1, a1, __ffma2_rn(b1, b1, lfz[h + 1]));
+        const float2 amp1 = __fmul2_rn(g1, make_float2(with_sign_of(ex2_approx(-u1.x), g1.x),
+                                                       with_sign_of(ex2_approx(-u1.y), g1.y)));
+        const float2 e = __fmul2_rn(tz, d);              // residual phase step t_z dl
+        const float2 pr = __ffma2_rn(e, nqs, qc);        // Re e^{j beta} (1 + j e)
+        const float2 pi = __ffma2_rn(e, qc, qs);         // Im
+        const float2 c1 = __ffma2_rn(neg2(sn), pi, __fmul2_rn(cs, pr));
+        const float2 s1 = __ffma2_rn(sn, pr, __fmul2_rn(cs, pi));
+        acc_re[h + 1] = __ffma2_rn(amp1, c1, acc_re[h + 1]);
+        acc_im[h + 1] = __ffma2_rn(amp1, s1, acc_im[h + 1]);
+    }
+}
+
 // RU: listed records evaluated per iteration (2: two independent accumulator sets for more
 // instruction-level parallelism; needs the register room of the 4-pixel configuration)
-template <int TW, int TH, int PX, int CHUNK, int STAGES, int RU, int MINB, int NPOLY>
+// STEP: the column-step evaluation of the odd packs (splat_record_step, pixel layout 1).
+template <int TW, int TH, int PX, int CHUNK, int STAGES, int RU, int MINB, int NPOLY, int STEP>
 __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __grid_constant__ SplatArgs A) {
     constexpr int NT = (TW / PX) * TH;
+    constexpr int SVN = STEP ? 5 : 4;  // float4 per record of the per-(record, tile) scalars
     constexpr int NW = NT / 32;          // warps = row bands of the tile
     constexpr int RPW = 32 / (TW / PX);  // tile rows per warp
     // records unrolled in the hot loop (four measured best; two where three CTAs share an SM's registers)
@@ -122,11 +198,12 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
     // per consumer warp w and source warp v: the chunk slots culled in by warp v that warp w
     // evaluates (records whose footprint meets w's band of rows)
     unsigned char *s_list =
-        reinterpret_cast<unsigned char *>(smem_raw + sizeof(Rec) * STAGES * CHUNK + sizeof(float4) * 4 * CHUNK);
+        reinterpret_cast<unsigned char *>(smem_raw + sizeof(Rec) * STAGES * CHUNK + sizeof(float4) * SVN * CHUNK);
     __shared__ uint64_t s_full[STAGES];
     __shared__ uint64_t s_never;
     __shared__ unsigned char s_cnt[NW][NW];
     __shared__ float s_dzt;  // the current tile's bound on |f_z - 1/lambda|
+    __shared__ unsigned s_dlmax;  // STEP: largest |dl| of the tile's threads (float bits, >= 0)
     __shared__ int s_item;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -140,7 +217,10 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
     uint32_t parity = 0;
 
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(A.queue, 1);
+        if (tid == 0) {
+            s_item = atomicAdd(A.queue, 1);
+            s_dlmax = 0u;
+        }
         __syncthreads();
         const int it = s_item;
         if (it >= A.n_items) break;
@@ -174,27 +254,71 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
         const float dfxf = (float)A.dfx, dfyf = (float)A.dfy;
         const float dy = (float)((double)(prow - r_ref) * A.dfy);
         const float2 *prow_tab = A.pixtab + ((size_t)l * A.H + (prow < A.H ? prow : 0)) * A.W;
-        // pixels p = 2 h + {0, 1} form the f32x2 pair h of the packed arithmetic
+        // pixel pix_of(h, lane) is lane `lane` of the f32x2 pair h of the packed arithmetic
         constexpr int PH = PX / 2;
         float2 dx[PH], dz[PH], lfz[PH];  // dx: offsets from the thread's middle column
         const float dxm = (float)(pcol0 + PX / 2 - c_ref) * dfxf;
 #pragma unroll
-        for (int p = 0; p < PX; ++p) {
-            const int col = pcol0 + p;
-            const float2 pt = (prow < A.H && col < A.W) ? prow_tab[col] : make_float2(0.f, -INFINITY);
-            const bool ok = pt.y > -INFINITY;  // (0, -inf): evanescent or outside the grid
-            const float vx = (float)(p - PX / 2) * dfxf;
-            const float vl = ok ? -pt.y : INFINITY;  // log2 f_z: 2^-(a^2 + b^2 + log2 f_z) = f_z^-1 2^-(a^2 + b^2)
-            const float vz = ok ? pt.x : 0.f;
-            if (p & 1) {
-                dx[p / 2].y = vx;
-                lfz[p / 2].y = vl;
-                dz[p / 2].y = vz;
-            } else {
-                dx[p / 2].x = vx;
-                lfz[p / 2].x = vl;
-                dz[p / 2].x = vz;
+        for (int h = 0; h < PH; ++h) {
+#pragma unroll
+            for (int ln = 0; ln < 2; ++ln) {
+                const int p = pix_of<STEP>(h, ln);
+                const int col = pcol0 + p;
+                const float2 pt = (prow < A.H && col < A.W) ? prow_tab[col] : make_float2(0.f, -INFINITY);
+                const bool ok = pt.y > -INFINITY;  // (0, -inf): evanescent or outside the grid
+                const float vx = (float)(p - PX / 2) * dfxf;
+                const float vl = ok ? -pt.y : INFINITY;  // log2 f_z: 2^-(a^2 + b^2 + log2 f_z) = f_z^-1 2^-(a^2 + b^2)
+                const float vz = ok ? pt.x : 0.f;
+                if (ln) {
+                    dx[h].y = vx;
+                    lfz[h].y = vl;
+                    dz[h].y = vz;
+                } else {
+                    dx[h].x = vx;
+                    lfz[h].x = vl;
+                    dz[h].x = vz;
+                }
             }
+        }
+        // STEP: the thread's mean step of f_z from an even pack's pixel to the odd pack's one
+        // column right (sbar), each pixel's residual from it (dl), and the tile's largest |dl|.
+        // A pixel without amplitude (lfz = inf) needs no phase; an even one whose right
+        // neighbour has amplitude takes f_z - f0_z = the neighbour's minus sbar, so that its
+        // residual is 0 (only its phase is carried to the neighbour).
+        float sbar = 0.f;
+        float2 dl[PH / 2 > 0 ? PH / 2 : 1];
+        if constexpr (STEP) {
+            float ssum = 0.f;
+            int ns = 0;
+#pragma unroll
+            for (int h = 0; h + 1 < PH; h += 2) {
+                if (lfz[h].x < INFINITY && lfz[h + 1].x < INFINITY) {
+                    ssum += dz[h + 1].x - dz[h].x;
+                    ++ns;
+                }
+                if (lfz[h].y < INFINITY && lfz[h + 1].y < INFINITY) {
+                    ssum += dz[h + 1].y - dz[h].y;
+                    ++ns;
+                }
+            }
+            sbar = ns ? ssum / (float)ns : 0.f;
+            float dmax = 0.f;
+#pragma unroll
+            for (int h = 0; h + 1 < PH; h += 2) {
+                float d0 = 0.f, d1 = 0.f;
+                if (lfz[h + 1].x < INFINITY) {
+                    if (lfz[h].x < INFINITY) d0 = (dz[h + 1].x - dz[h].x) - sbar;
+                    else dz[h].x = dz[h + 1].x - sbar;
+                }
+                if (lfz[h + 1].y < INFINITY) {
+                    if (lfz[h].y < INFINITY) d1 = (dz[h + 1].y - dz[h].y) - sbar;
+                    else dz[h].y = dz[h + 1].y - sbar;
+                }
+                dl[h / 2] = make_float2(d0, d1);
+                dmax = fmaxf(dmax, fmaxf(fabsf(d0), fabsf(d1)));
+            }
+            const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
+            if (lane == 0) atomicMax(&s_dlmax, m);  // read by the cull, after the barrier that opens each chunk
         }
         // tile rectangle (pixel-centre frequencies of the valid pixels) for the cull
         const float x0 = (float)((double)(c_lo - A.W / 2) * A.dfx), x1 = (float)((double)(c_hi - A.W / 2) * A.dfx);
@@ -244,6 +368,7 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
             // against each warp's band of RPW rows (FP32, from the tile's edges), and only the
             // warps whose band it meets evaluate it.
             const int nrec = min(CHUNK, count - ch * CHUNK);
+            bool need_direct = false;  // STEP: this record's residual phase step is too large for it
             {
                 unsigned bands = 0;
                 if (tid < nrec) {
@@ -267,11 +392,15 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
                         const float a0 = fmaf(r.r1z, dz0f, fmaf(r.r1y, f0yf, r.r1x * f0xf));
                         const float b0 = fmaf(r.r2z, dz0f, fmaf(r.r2y, f0yf, r.r2x * f0xf));
                         const float g0 = fmaf(r.r3z, f0zf, fmaf(r.r3y, f0yf, r.r3x * f0xf));
-                        float4 *sv = s_sv + tid * 4;
+                        float4 *sv = s_sv + tid * SVN;
                         sv[0] = make_float4(r.r1x, r.r1y, r.r1z, a0);
                         sv[1] = make_float4(r.r2x, r.r2y, r.r2z, b0);
                         sv[2] = make_float4(r.r3x, r.r3y, r.r3z, g0);
                         sv[3] = make_float4(r.mx, r.my, r.mz, (float)cyc);
+                        if constexpr (STEP) {
+                            sv[4] = make_float4(r.r1x * dfxf, r.r2x * dfxf, r.r3x * dfxf, r.mx * dfxf);
+                            need_direct = fabsf(r.mz) * __uint_as_float(s_dlmax) > kStepEps;
+                        }
                     }
                 }
                 const unsigned lt = (1u << lane) - 1u;
@@ -283,7 +412,10 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
                     if (lane == 0) s_cnt[w][warp] = (unsigned char)__popc(bal);
                 }
             }
-            __syncthreads();
+            // STEP: the whole chunk goes through splat_record if any of its records needs it
+            bool direct = true;
+            if constexpr (STEP) direct = __syncthreads_or(need_direct) != 0;
+            else __syncthreads();
             // the stage is free again: refill it with the chunk STAGES ahead
             if (issued < n_chunks) {
                 if (tid == 0) {
@@ -307,14 +439,23 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
                     if (!in_bounds(lst[i] < nrec, A.status)) cnt = 0;
 #endif
                 int i = 0;
+                if constexpr (STEP) {
+                    if (!direct) {
+#pragma unroll(UNR)
+                        for (; i < cnt; ++i)
+                            splat_record_step<PH>(s_sv + lst[i] * SVN, dy, dxm, dx, dz, lfz, dl, sbar, acc_re, acc_im);
+                        continue;
+                    }
+                }
                 if (RU == 2) {
                     for (; i + 1 < cnt; i += 2) {
-                        splat_record<PH, NPOLY>(s_sv + lst[i] * 4, dy, dxm, dx, dz, lfz, acc_re, acc_im);
-                        splat_record<PH, NPOLY>(s_sv + lst[i + 1] * 4, dy, dxm, dx, dz, lfz, acc2_re, acc2_im);
+                        splat_record<PH, NPOLY>(s_sv + lst[i] * SVN, dy, dxm, dx, dz, lfz, acc_re, acc_im);
+                        splat_record<PH, NPOLY>(s_sv + lst[i + 1] * SVN, dy, dxm, dx, dz, lfz, acc2_re, acc2_im);
                     }
                 }
 #pragma unroll(UNR)
-                for (; i < cnt; ++i) splat_record<PH, NPOLY>(s_sv + lst[i] * 4, dy, dxm, dx, dz, lfz, acc_re, acc_im);
+                for (; i < cnt; ++i)
+                    splat_record<PH, NPOLY>(s_sv + lst[i] * SVN, dy, dxm, dx, dz, lfz, acc_re, acc_im);
             }
             if (RU == 2) {
 #pragma unroll
@@ -326,10 +467,11 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
             }
 #pragma unroll
             for (int h = 0; h < PH; ++h) {
-                two_sum_acc(sum_re[2 * h], cmp_re[2 * h], acc_re[h].x);
-                two_sum_acc(sum_re[2 * h + 1], cmp_re[2 * h + 1], acc_re[h].y);
-                two_sum_acc(sum_im[2 * h], cmp_im[2 * h], acc_im[h].x);
-                two_sum_acc(sum_im[2 * h + 1], cmp_im[2 * h + 1], acc_im[h].y);
+                const int p0 = pix_of<STEP>(h, 0), p1 = pix_of<STEP>(h, 1);
+                two_sum_acc(sum_re[p0], cmp_re[p0], acc_re[h].x);
+                two_sum_acc(sum_re[p1], cmp_re[p1], acc_re[h].y);
+                two_sum_acc(sum_im[p0], cmp_im[p0], acc_im[h].x);
+                two_sum_acc(sum_im[p1], cmp_im[p1], acc_im[h].y);
                 acc_re[h] = acc_im[h] = make_float2(0.f, 0.f);
             }
             __syncthreads();
@@ -384,11 +526,12 @@ __global__ void __launch_bounds__((TW / PX) * TH, MINB) k_splat_mixed(const __gr
 
 // MINB: CTAs per SM the launch bounds aim at (3 needs <= 85 registers and the 2-stage ring);
 // CHUNK: Gaussian records per bulk-copied chunk (<= threads; 0 = one per thread); STAGES: ring depth
-template <int TW, int TH, int PX, int RU = 1, int STAGES = 3, int MINB = 2, int CHUNK_ = 0, int NPOLY = 0>
+template <int TW, int TH, int PX, int RU = 1, int STAGES = 3, int MINB = 2, int CHUNK_ = 0, int NPOLY = 0, int STEP = 0>
 struct SplatCfg {
     static constexpr int NT = (TW / PX) * TH;
     static constexpr int CHUNK = CHUNK_ > 0 ? CHUNK_ : NT;
-    static constexpr size_t smem = sizeof(Rec) * STAGES * CHUNK + sizeof(float4) * 4 * CHUNK + (size_t)(NT / 32) * NT;
+    static constexpr size_t smem =
+        sizeof(Rec) * STAGES * CHUNK + sizeof(float4) * (STEP ? 5 : 4) * CHUNK + (size_t)(NT / 32) * NT;
     // the opt-in shared-memory size is a per-device function attribute: set it once per
     // device (gws_prepare or the first call), not while a stream is being captured
     static cudaError_t prepare() {
@@ -397,7 +540,7 @@ struct SplatCfg {
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-        e = cudaFuncSetAttribute(k_splat_mixed<TW, TH, PX, CHUNK, STAGES, RU, MINB, NPOLY>,
+        e = cudaFuncSetAttribute(k_splat_mixed<TW, TH, PX, CHUNK, STAGES, RU, MINB, NPOLY, STEP>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
         return e;
@@ -405,7 +548,7 @@ struct SplatCfg {
     static cudaError_t launch(const SplatArgs &a, int grid, cudaStream_t s) {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
-        k_splat_mixed<TW, TH, PX, CHUNK, STAGES, RU, MINB, NPOLY><<<grid, NT, smem, s>>>(a);
+        k_splat_mixed<TW, TH, PX, CHUNK, STAGES, RU, MINB, NPOLY, STEP><<<grid, NT, smem, s>>>(a);
         count_launches(1);
         return cudaGetLastError();
     }
@@ -423,6 +566,8 @@ using Cfg7 = SplatCfg<64, 32, 8, 1, 2, 2, 256>;   // 64x32, 256 records/chunk, 2
 using Cfg8 = SplatCfg<64, 32, 8, 1, 6, 2, 64>;    // 64x32, 64 records/chunk, 6 stages
 using Cfg9 = SplatCfg<64, 32, 8, 1, 3, 2, 0, 1>;  // 64x32, the cos of 1 of the 4 pixel pairs on the FP32 pipe
 using Cfg10 = SplatCfg<128, 16, 8, 1, 3, 2, 0, 1>;  // 128x16, likewise
+using Cfg11 = SplatCfg<64, 32, 8, 1, 3, 2, 0, 0, 1>;  // 64x32, the odd packs by the column step
+using Cfg12 = SplatCfg<128, 16, 8, 1, 3, 2, 0, 0, 1>; // 128x16, likewise
 
 cudaError_t prepare_splat_kernels() {
     cudaError_t e = Cfg1::prepare();
@@ -435,18 +580,21 @@ cudaError_t prepare_splat_kernels() {
     if (e == cudaSuccess) e = Cfg8::prepare();
     if (e == cudaSuccess) e = Cfg9::prepare();
     if (e == cudaSuccess) e = Cfg10::prepare();
+    if (e == cudaSuccess) e = Cfg11::prepare();
+    if (e == cudaSuccess) e = Cfg12::prepare();
     return e;
 }
 
 template <typename C>
-constexpr TileCfg describe(int id, int tw, int th, int px, int ru, int stages, int ctas, int npoly = 0) {
-    return TileCfg{id, tw, th, px, ru, C::CHUNK, stages, ctas, npoly};
+constexpr TileCfg describe(int id, int tw, int th, int px, int ru, int stages, int ctas, int npoly = 0, int step = 0) {
+    return TileCfg{id, tw, th, px, ru, C::CHUNK, stages, ctas, npoly, step};
 }
 static const TileCfg kCfgs[] = {
     describe<Cfg1>(1, 64, 32, 8, 1, 3, 2), describe<Cfg2>(2, 32, 32, 4, 1, 3, 2), describe<Cfg3>(3, 128, 16, 8, 1, 3, 2),
     describe<Cfg4>(4, 32, 32, 4, 2, 3, 2), describe<Cfg5>(5, 32, 32, 4, 1, 2, 3), describe<Cfg6>(6, 64, 32, 8, 1, 4, 2),
     describe<Cfg7>(7, 64, 32, 8, 1, 2, 2), describe<Cfg8>(8, 64, 32, 8, 1, 6, 2), describe<Cfg9>(9, 64, 32, 8, 1, 3, 2, 1),
-    describe<Cfg10>(10, 128, 16, 8, 1, 3, 2, 1)};
+    describe<Cfg10>(10, 128, 16, 8, 1, 3, 2, 1), describe<Cfg11>(11, 64, 32, 8, 1, 3, 2, 0, 1),
+    describe<Cfg12>(12, 128, 16, 8, 1, 3, 2, 0, 1)};
 
 int n_tile_cfgs() { return (int)(sizeof(kCfgs) / sizeof(kCfgs[0])); }
 TileCfg tile_cfg(int id) {
@@ -466,6 +614,8 @@ cudaError_t launch_splat_mixed(int cfg, const SplatArgs &a, int grid, cudaStream
         case 8: return Cfg8::launch(a, grid, s);
         case 9: return Cfg9::launch(a, grid, s);
         case 10: return Cfg10::launch(a, grid, s);
+        case 11: return Cfg11::launch(a, grid, s);
+        case 12: return Cfg12::launch(a, grid, s);
         default: return Cfg1::launch(a, grid, s);
     }
 }

@@ -84,7 +84,7 @@ EXPORTS = ["gws_opts_default", "gws_status_string", "gws_version", "gws_workspac
            "gws_forward", "gws_forward_batched", "gws_backward", "gws_encode", "gws_get_device_status",
            "gws_depth_order", "gws_transmittance", "gws_footprints", "gws_last_launch_count", "gws_autotune",
            "gws_kernel_time_ms", "gws_footprint_pairs", "gws_encode_noalloc", "gws_holographics",
-           "gws_triangles_workspace_size", "gws_forward_triangles", "gws_tile_config"]
+           "gws_triangles_workspace_size", "gws_forward_triangles", "gws_tile_config", "gws_tile_config_ext"]
 
 
 def lib_path(variant: str | None = None) -> str:
@@ -111,9 +111,10 @@ def load(build_if_needed: bool = True):
         lib.gws_last_launch_count.restype = C.c_int
         lib.gws_kernel_time_ms.restype = C.c_float
         lib.gws_tile_config.restype = C.c_int
+        lib.gws_tile_config_ext.restype = C.c_int
         for name in EXPORTS:
             if name not in ("gws_status_string", "gws_version", "gws_last_launch_count", "gws_opts_default",
-                            "gws_kernel_time_ms", "gws_tile_config"):
+                            "gws_kernel_time_ms", "gws_tile_config", "gws_tile_config_ext"):
                 getattr(lib, name).restype = C.c_int
         _libs[_variant] = lib
         return lib
@@ -424,10 +425,10 @@ def tile_configs() -> dict:
     n = int(lib.gws_tile_config(0, None))
     out = {}
     for i in range(1, n + 1):
-        d = (C.c_int * 8)()
-        lib.gws_tile_config(i, d)
+        d = (C.c_int * 9)()
+        lib.gws_tile_config_ext(i, d, 9)
         out[i] = dict(zip(("tile_w", "tile_h", "px_per_thread", "records_per_iteration", "records_per_chunk",
-                           "ring_stages", "ctas_per_sm", "cos_pairs_on_fp32"), list(d)))
+                           "ring_stages", "ctas_per_sm", "cos_pairs_on_fp32", "column_step"), list(d)))
     return out
 
 

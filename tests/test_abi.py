@@ -67,6 +67,11 @@ def test_tile_configurations_are_described():
         assert 32 <= c["records_per_chunk"] <= min(threads, 256) and c["records_per_chunk"] % 32 == 0
     lib = gws.load()
     assert lib.gws_tile_config(0, None) == len(cfgs) and lib.gws_tile_config(99, None) == len(cfgs)
+    # the extended description writes no more than it is given room for
+    d = (C.c_int * 10)(*([-7] * 10))
+    assert lib.gws_tile_config_ext(1, d, 3) == len(cfgs) and list(d)[3:] == [-7] * 7
+    assert lib.gws_tile_config_ext(1, d, 10) == len(cfgs) and d[9] == -7 and d[8] in (0, 1)
+    assert {c["column_step"] for c in cfgs.values()} == {0, 1}
 
 
 def test_status_strings_and_version():

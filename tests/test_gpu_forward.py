@@ -60,7 +60,7 @@ def test_forward_field_matches_oracle(name, slm, kind, seed, n, blend):
     assert max(per_lambda_rel(fmx, ref)) < TOLMX
 
 
-@pytest.mark.parametrize("tile_cfg", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("tile_cfg", list(range(1, 13)))
 def test_spectrum_domain_and_every_tile_config(tile_cfg):
     slm = SLM(96, 160, 8e-6, 8e-6, (638e-9, 520e-9, 450e-9))
     sc = surface_scene(7, 120, slm, n_surfaces=3)
@@ -70,6 +70,63 @@ def test_spectrum_domain_and_every_tile_config(tile_cfg):
     assert max(per_lambda_rel(u, ref)) < TOLMX
     u64 = gws.forward(g, slm, prec=gws.PREC_FP64, domain=gws.DOMAIN_SPECTRUM).cpu().numpy()
     assert max(per_lambda_rel(u64, ref)) < TOL64
+
+
+def _near_slm(sc, lo, hi, seed):
+    """The scene with its depths redrawn in [lo, hi] (m)."""
+    sc.mean[:, 2] = np.random.default_rng(seed).uniform(lo, hi, sc.n)
+    return sc
+
+
+# grids where the column step's residual |t_z dl| stays below its 2e-3 rad bound for depths
+# up to 0.15 mm (ragged widths, an odd grid, a pitch with evanescent corners), and the phase match
+STEP_CASES = [
+    ("96x160", SLM(96, 160, 8e-6, 8e-6, (638e-9, 520e-9, 450e-9)), 0.15e-3, False),
+    ("ragged", SLM(100, 150, 8e-6, 6e-6, (638e-9, 450e-9)), 0.1e-3, False),
+    ("odd", SLM(77, 99, 8e-6, 8e-6, (520e-9,)), 0.15e-3, True),
+    ("evanescent", SLM(64, 72, 0.3e-6, 0.3e-6, (520e-9,)), 0.4e-6, False),
+]
+
+
+@pytest.mark.parametrize("name,slm,zmax,pm", STEP_CASES, ids=[c[0] for c in STEP_CASES])
+@pytest.mark.parametrize("tile_cfg", [11, 12])
+def test_column_step_configs_match_oracle(name, slm, zmax, pm, tile_cfg):
+    """The column-step configurations on grids where their step path runs (the records' residual
+    phase steps within bounds; at the evanescent boundary, where f_z bends sharply, those tiles
+    take the direct path): element-wise against the oracle, bar 2e-4 per wavelength."""
+    if name == "evanescent":
+        sc = uniform_scene(12, 30, slm)
+        sc.scale[:] = np.float32(0.6e-6)
+    else:
+        sc = surface_scene(11, 150, slm, n_surfaces=3)
+    sc = _near_slm(sc, 0.2 * zmax, zmax, 13)
+    ref = O.spectrum(sc, slm, phase_match=pm)
+    u = gws.forward(dev(sc), slm, prec=gws.PREC_MIXED, domain=gws.DOMAIN_SPECTRUM, tile_cfg=tile_cfg,
+                    phase_match=pm).cpu().numpy()
+    assert max(per_lambda_rel(u, ref)) < TOLMX, per_lambda_rel(u, ref)
+
+
+def test_column_step_mixed_chunks_at_512x768():
+    """A 512 x 768 grid with 1200 Gaussians at 2-10 mm: some records' residual phase step is
+    within the column step's bound and some not, so chunks of both kinds run in one launch.
+    Sampled spectrum against the oracle (2e-4 per wavelength) and the whole spectrum against the
+    direct configuration of the same tile shape."""
+    slm = SLM(512, 768, 8e-6, 8e-6, (638e-9, 520e-9, 450e-9))
+    sc = surface_scene(14, 1200, slm, n_surfaces=6)
+    g = dev(sc)
+    lam, r, c = _samples(slm, 1500, 15)
+    ref = O.spectrum_at(sc, slm, lam, r, c)
+    u1 = gws.forward(g, slm, prec=gws.PREC_MIXED, domain=gws.DOMAIN_SPECTRUM, tile_cfg=1)
+    for cfg in (11, 12):
+        u = gws.forward(g, slm, prec=gws.PREC_MIXED, domain=gws.DOMAIN_SPECTRUM, tile_cfg=cfg)
+        got = u[torch.as_tensor(lam, dtype=torch.long), torch.as_tensor(r, dtype=torch.long),
+                torch.as_tensor(c, dtype=torch.long)].cpu().numpy()
+        for l in range(slm.n_lambda):
+            m = lam == l
+            assert rel_l2(got[m], ref[m]) < TOLMX, (cfg, l, rel_l2(got[m], ref[m]))
+        for l in range(slm.n_lambda):
+            e = (torch.linalg.norm(u[l] - u1[l]) / torch.linalg.norm(u1[l])).item()
+            assert e < 2e-5, (cfg, l, e)
 
 
 def test_phase_match_option():
@@ -261,23 +318,26 @@ def _band_samples(slm, band, k, seed):
 @pytest.mark.parametrize("cfg", ["headline_1m_1080p_3l", "c2_precision_at_scale"])
 def test_full_size_band_stratified_spectrum(cfg):
     """Full-size parity per frequency band and wavelength, each band against its own norm: the
-    sampled mixed spectrum (the bench's launch configuration) vs the oracle, which sums every
-    Gaussian at each sample without truncation."""
+    sampled mixed spectrum vs the oracle, which sums every Gaussian at each sample without
+    truncation; for the direct configuration 1 and the column-step configuration 11 (the
+    autotuner's candidates for the bench's launch)."""
     sc, slm = config_scene(cfg)
-    u = gws.forward(dev(sc), slm, prec=gws.PREC_MIXED, domain=gws.DOMAIN_SPECTRUM)
+    g = dev(sc)
+    us = {t: gws.forward(g, slm, prec=gws.PREC_MIXED, domain=gws.DOMAIN_SPECTRUM, tile_cfg=t) for t in (1, 11)}
     report = {}
     for bi, band in enumerate(("dc", "mid", "outer", "corner")):
         for l in range(slm.n_lambda):
             r, c = _band_samples(slm, band, 40, 1000 + 10 * bi + l)
             lam = np.full(r.shape, l, np.int32)
-            got = u[l, torch.as_tensor(r, dtype=torch.long), torch.as_tensor(c, dtype=torch.long)].cpu().numpy()
             ref = O.spectrum_at(sc, slm, lam, r, c)
-            e = rel_l2(got, ref)
             peak = np.abs(ref).max()
-            report[(band, l)] = (e, float(np.abs(got - ref).max() / peak), float(peak))
-            assert e < TOLMX, (band, l, e)
-    print(cfg, {f"{b}/{l}": f"rel-L2 {v[0]:.2e}, max|err|/peak {v[1]:.2e}, peak {v[2]:.3g}"
-                for (b, l), v in report.items()})
+            for t, u in us.items():
+                got = u[l, torch.as_tensor(r, dtype=torch.long), torch.as_tensor(c, dtype=torch.long)].cpu().numpy()
+                e = rel_l2(got, ref)
+                report[(t, band, l)] = (e, float(np.abs(got - ref).max() / peak), float(peak))
+                assert e < TOLMX, (t, band, l, e)
+    print(cfg, {f"cfg{t}/{b}/{l}": f"rel-L2 {v[0]:.2e}, max|err|/peak {v[1]:.2e}, peak {v[2]:.3g}"
+                for (t, b, l), v in report.items()})
 
 
 def test_fp64_path_at_slm_size_sampled():
