@@ -293,7 +293,8 @@ GWS_API int gws_last_launch_count(void);
  * pairs per thread whose cos runs on the FP32 pipe.  Host only. */
 GWS_API int gws_tile_config(int id, int *desc);
 
-/* gws_tile_config with the whole description: writes desc[0 .. min(n_desc, 9) - 1], the eight
+/* gws_tile_config with the whole description (no counterpart in the paper, like
+ * gws_tile_config): writes desc[0 .. min(n_desc, 9) - 1], the eight
  * values above followed by desc[8] = 1 where the configuration evaluates every second pixel
  * pair by the column step (its phase factor as the left neighbour's times one per-record
  * rotation and a first-order residual; chunks whose residual would exceed 2e-3 rad fall back
