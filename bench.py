@@ -74,11 +74,11 @@ def fwd_pairs_per_clk(cfg_desc) -> tuple[float, str]:
 
 
 BWD_PAIRS_PER_CLK = 128.0 / 30.0
-# The generic per-pair counts of the hot-path survey (minimal formula, per-frequency terms amortised
+# The generic per-pair counts (minimal formula, per-frequency terms amortised
 # over Gaussians): forward 23 FP32 issues + 3 MUFU -> min(128/23, 6.4) = 5.57 pairs/clk/SM; backward
 # the same 3 MUFU + 23 recompute + 2 x 14 accumulation lane-ops = 51 -> 128/51 = 2.51 pairs/clk/SM.
-FWD_PAIRS_PER_CLK_SURVEY = min(128.0 / 23.0, FWD_PAIRS_PER_CLK)
-BWD_PAIRS_PER_CLK_SURVEY = 128.0 / 51.0
+FWD_PAIRS_PER_CLK_GENERIC = min(128.0 / 23.0, FWD_PAIRS_PER_CLK)
+BWD_PAIRS_PER_CLK_GENERIC = 128.0 / 51.0
 FOCAL_PLANES = (2e-3, 5e-3, 8e-3)  # refocus planes of the differentiable workload's loss (m)
 
 
@@ -471,16 +471,16 @@ def run_ours(args):
         dom_ms["refocus_loss"] = statistics.median(loss_ms)
     full_size = args.workload == WORKLOAD and not fp64 and args.n is None and args.blend == "oit"
 
-    def roof(kernel, kms, per_clk, basis, traffic_mb, survey_per_clk=None, survey_basis=""):
+    def roof(kernel, kms, per_clk, basis, traffic_mb, generic_per_clk=None, generic_basis=""):
         achieved = pairs / (kms * 1e-3)
         peak = n_sm * sm_mhz * 1e6 * per_clk
         r = {"kernel": kernel, "bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
              "frac": achieved / peak, "traffic": None if traffic_mb is None else traffic_mb * 1e6,
              "peak_basis": f"{n_sm} SMs x {sm_mhz:.0f} MHz (median sampled) x {per_clk:.2f} pairs/clk/SM, " + basis}
-        if survey_per_clk is not None:
-            sp = n_sm * sm_mhz * 1e6 * survey_per_clk
-            r["survey_count"] = {"peak": sp / 1e9, "frac": achieved / sp, "per_clk": survey_per_clk,
-                                 "basis": survey_basis}
+        if generic_per_clk is not None:
+            sp = n_sm * sm_mhz * 1e6 * generic_per_clk
+            r["generic_count"] = {"peak": sp / 1e9, "frac": achieved / sp, "per_clk": generic_per_clk,
+                                 "basis": generic_basis}
         return r
 
     if args.blend in ("exact", "partial"):
@@ -504,13 +504,13 @@ def run_ours(args):
             "k_splat_fp64" if fp64 else "k_splat_mixed", splat, fwd_per_clk,
             fwd_basis + (" (FP32/MUFU peak; the FP64 path runs on the FP64 pipe)" if fp64 else ""),
             args.traffic_mb if args.traffic_mb is not None else (SPLAT_TRAFFIC_MB.get(tile_cfg) if full_size else None),
-            None if fp64 else FWD_PAIRS_PER_CLK_SURVEY,
-            "survey count: 23 FP32 issues + 3 MUFU per pair -> min(128/23, 6.4) pairs/clk/SM")}
+            None if fp64 else FWD_PAIRS_PER_CLK_GENERIC,
+            "generic count: 23 FP32 issues + 3 MUFU per pair -> min(128/23, 6.4) pairs/clk/SM")}
     if bwd_ms:
         rooflines["splat_bwd"] = roof("k_splat_bwd", dom_ms["splat_bwd"], BWD_PAIRS_PER_CLK,
                                       "FP32 bound (30 lane-ops per pair at 128 lanes/clk/SM; MUFU bound 6.4)",
-                                      BWD_TRAFFIC_MB if full_size else None, BWD_PAIRS_PER_CLK_SURVEY,
-                                      "survey count: 3 MUFU + 23 recompute + 2 x 14 accumulation = 51 FP32 lane-ops "
+                                      BWD_TRAFFIC_MB if full_size else None, BWD_PAIRS_PER_CLK_GENERIC,
+                                      "generic count: 3 MUFU + 23 recompute + 2 x 14 accumulation = 51 FP32 lane-ops "
                                       "per pair -> 128/51 pairs/clk/SM")
     if front_ms:
         dom_ms["front_end"] = statistics.median(front_ms)
