@@ -104,15 +104,15 @@ __device__ __forceinline__ void splat_record(const float4 *__restrict__ sv, floa
     }
 }
 
-// Pixel p of a thread's PX in the packed layout: pack and lane.  Layout 0 pairs neighbours
-// (p = 2h, 2h + 1).  Layout 1 (the column-step configurations) pairs p = 4k + {0, 2} in pack 2k and
-// p = 4k + {1, 3} in pack 2k + 1, so that each lane of an odd pack sits one column right of the
-// same lane of the even pack before it.
 // Largest |t_z| max|dl| of a record the column step takes: (1 + j e) errs from e^{j e} by
 // e^2 / 2 <= 2e-6 of the term.  On the 8 um and 3.74 um grids of 1920 and 3840 columns,
 // max|dl| <= 0.0095 / m, so every record with |mu_z| <= 33 mm qualifies.
 constexpr float kStepEps = 2e-3f;
 
+// Pixel p of a thread's PX in the packed layout: pack and lane.  Layout 0 pairs neighbours
+// (p = 2h, 2h + 1).  Layout 1 (the column-step configurations) pairs p = 4k + {0, 2} in pack 2k and
+// p = 4k + {1, 3} in pack 2k + 1, so that each lane of an odd pack sits one column right of the
+// same lane of the even pack before it.
 template <int LAYOUT>
 __host__ __device__ constexpr int pix_of(int h, int lane) {
     return LAYOUT == 0 ? 2 * h + lane : (h & 1) + 4 * (h >> 1) + 2 * lane;
@@ -126,7 +126,7 @@ __host__ __device__ constexpr int pix_of(int h, int lane) {
 // (1 + j t_z dl) for the residual.  The first-order residual errs by (t_z dl)^2 / 2: the cull
 // sends a chunk to splat_record instead whenever a record's |t_z| max|dl| over the tile exceeds
 // kStepEps.  The odd packs need no sin/cos of their own: per record and thread, 2 sin/cos in
-// place of 8, for 12 more FP32 lane-ops per odd pack.
+// place of 8, for 8 more FP32 lane-ops per odd pack (36 against 28).
 template <int PH>
 __device__ __forceinline__ void splat_record_step(const float4 *__restrict__ sv, float dy, float dxm,
                                                   const float2 *ddx, const float2 *dz, const float2 *lfz,
