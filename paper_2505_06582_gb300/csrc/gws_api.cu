@@ -410,6 +410,7 @@ struct Front {
 
 static gws_status run_front(const gws_gaussians *scenes, const int64_t *n, int n_scenes, const gws_slm *slm,
                             const gws_opts *o, const Layout &L, bool need_T, Front *F, cudaStream_t s) {
+    NvtxRange nvtx("gws: validate, depth sort, transmittance");
     SceneTable &T = F->T;
     std::memset(&T, 0, sizeof T);
     T.n_scenes = n_scenes;
@@ -468,6 +469,7 @@ static int seg_bits(int n_seg) {
 // records in decreasing-footprint order per segment; returns the record array
 static gws_status run_records(const Front &F, const gws_slm *slm, const gws_opts *o, const Layout &L, int backward,
                               cudaStream_t s, Rec **rec_out) {
+    NvtxRange nvtx("gws: footprints, binning, records");
     const long long n_rec = F.n_total * slm->n_lambda;
     const FootParams FP = foot_params(slm, o);
     GPre *gp = at<GPre>(o, L.gpre);
@@ -512,6 +514,7 @@ static gws_status batch_fft(const Plan &p, int H, int W, int nl, int nb, int B, 
 // inverse FFT.
 static gws_status exact_forward(const gws_gaussians *scene, long long n, const gws_slm *slm, const gws_opts *o,
                                 const Layout &L, const Front &F, void *out, cudaStream_t s) {
+    NvtxRange nvtx("gws: exact blending");
     const int nl = slm->n_lambda, H = slm->H, W = slm->W;
     const long long hw = (long long)H * W;
     const double dfx = 1.0 / (W * slm->pitch_x), dfy = 1.0 / (H * slm->pitch_y);
@@ -579,6 +582,7 @@ static gws_status exact_forward(const gws_gaussians *scene, long long n, const g
 // accumulated with the ramps e^{-j 2 pi f . mu}; a final centred inverse DFT gives the field.
 static gws_status pc_forward(const gws_gaussians *scene, long long n, const gws_slm *slm, const gws_opts *o,
                              const Layout &L, const Front &F, void *out, cudaStream_t s) {
+    NvtxRange nvtx("gws: partial coherence");
     const int nl = slm->n_lambda, H = slm->H, W = slm->W;
     const long long hw = (long long)H * W;
     const double dfx = 1.0 / (W * slm->pitch_x), dfy = 1.0 / (H * slm->pitch_y);
@@ -677,6 +681,7 @@ static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, in
     GS(check_workspace(o, L));
     cudaStream_t s = (cudaStream_t)o->stream;
     CanaryGuard guard(o, L, s);
+    NvtxRange nvtx_call("gws_forward");
     timers_reset(o);
     timer_mark(o, GWS_TIMER_TOTAL, 0, s);
     const int nl = slm->n_lambda, H = slm->H, W = slm->W;
@@ -716,6 +721,7 @@ static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, in
         a.phase_match = o->phase_match ? 1 : 0;
         a.status = at<int>(o, L.status);
         for (int k = 0; k < n_scenes; ++k) a.out[k] = out[k];
+        NvtxRange nvtx("gws: splat (FP64)");
         timer_mark(o, GWS_TIMER_SPLAT_FWD, 0, s);
         CU(launch_splat_fp64(a, s));
         timer_mark(o, GWS_TIMER_SPLAT_FWD, 1, s);
@@ -766,11 +772,13 @@ static gws_status forward_impl(const gws_gaussians *scenes, const int64_t *n, in
         a.debug = o->debug_flags;
         for (int k = 0; k < n_scenes; ++k) a.out[k] = out[k];
         const int grid = (int)std::min<long long>(n_items, (long long)num_sms() * splat_mixed_ctas_per_sm(L.cfg));
+        NvtxRange nvtx("gws: splat");
         timer_mark(o, GWS_TIMER_SPLAT_FWD, 0, s);
         CU(launch_splat_mixed(L.cfg, a, grid, s));
         timer_mark(o, GWS_TIMER_SPLAT_FWD, 1, s);
     }
     if (fft) {
+        NvtxRange nvtx("gws: inverse DFT");
         Plan p, pb;
         GS(get_plan(H, W, nl, dbl, &p));
         timer_mark(o, GWS_TIMER_FFT, 0, s);
@@ -917,6 +925,7 @@ gws_status gws_encode(const void *field, const gws_slm *slm, const gws_opts *opt
     }
     cudaStream_t s = (cudaStream_t)opts->stream;
     unsigned long long *amax = opts->workspace ? at<unsigned long long>(opts, L.amax) : nullptr;
+    NvtxRange nvtx("gws_encode");
     timers_reset(opts);
     timer_mark(opts, GWS_TIMER_ENCODE, 0, s);
     CU(launch_encode(field, opts->prec == GWS_PREC_FP64, slm->n_lambda, slm->H, slm->W, amax, (double)amp_scale,
@@ -1078,6 +1087,7 @@ gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, c
     GS(check_workspace(opts, L));
     CanaryGuard guard(opts, L, (cudaStream_t)opts->stream);
     cudaStream_t s = (cudaStream_t)opts->stream;
+    NvtxRange nvtx_call("gws_backward");
     timers_reset(opts);
     timer_mark(opts, GWS_TIMER_TOTAL, 0, s);
     CU(cudaMemsetAsync(at<char>(opts, L.status), 0, 16, s));
@@ -1092,6 +1102,7 @@ gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, c
     // dL/du_SLM: the adjoint of the centred inverse DFT (dfx dfy x centred forward DFT)
     const float2 *gsrc = static_cast<const float2 *>(grad_field);
     if (fft) {
+        NvtxRange nvtx("gws: adjoint DFT");
         float2 *gs = at<float2>(opts, L.gspec);
         CU(cudaMemcpyAsync(gs, grad_field, sizeof(float2) * (size_t)nl * H * W, cudaMemcpyDeviceToDevice, s));
         CU(launch_modulate(gs, 0, nl, H, W, 1.0, 1, s));
@@ -1134,9 +1145,12 @@ gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, c
     const int B = bwd_block_size();
     a.n_items = (int)(nl * ((n + B - 1) / B));
     const int grid = (int)std::min<long long>(a.n_items, (long long)num_sms() * bwd_ctas_per_sm());
-    timer_mark(opts, GWS_TIMER_SPLAT_BWD, 0, s);
-    CU(launch_splat_bwd(a, grid, s));
-    timer_mark(opts, GWS_TIMER_SPLAT_BWD, 1, s);
+    {
+        NvtxRange nvtx("gws: splat backward");
+        timer_mark(opts, GWS_TIMER_SPLAT_BWD, 0, s);
+        CU(launch_splat_bwd(a, grid, s));
+        timer_mark(opts, GWS_TIMER_SPLAT_BWD, 1, s);
+    }
     GradArgs G;
     std::memset(&G, 0, sizeof G);
     G.mean = out->mean;

@@ -2,12 +2,22 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
 
 #include "gws_common.cuh"
 
 namespace gws {
+
+// NVTX range over the host-side enqueueing of one stage of a call (named in profiler
+// timelines and usable as an ncu/nsys --nvtx filter; a no-op unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // kernel-launch counter (gws_last_launch_count)
 void count_launches(int k);
