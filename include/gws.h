@@ -304,6 +304,15 @@ GWS_API int gws_tile_config_ext(int id, int *desc, int n_desc);
 GWS_API gws_status gws_autotune(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
                         void *field_scratch, int *best_cfg);
 
+/* The autotuner's in-process table (no counterpart in the paper), for callers that keep its
+ * choices between processes.  gws_tune_get writes to *cfg (host) the configuration recorded for
+ * slm's grid class (H, W, n_lambda) by gws_autotune or gws_tune_set, or 0 if there is none.
+ * gws_tune_set records cfg (1 .. gws_tile_config(0, NULL)) for that class, as gws_autotune does
+ * after timing, or forgets the class's entry for cfg = 0; other values give
+ * GWS_ERR_INVALID_ARG.  Both check slm as gws_forward does, touch no device and are thread-safe. */
+GWS_API gws_status gws_tune_get(const gws_slm *slm, int *cfg);
+GWS_API gws_status gws_tune_set(const gws_slm *slm, int cfg);
+
 /* ---- triangle primitive (supplement, polygon-based methods) ----------------------------------
  *
  * Eq. 10 with the canonical Gaussian replaced by the canonical triangle {(0,0), (1,0), (1,1)}:

@@ -1172,6 +1172,25 @@ gws_status gws_backward(const gws_gaussians *g, int64_t n, const gws_slm *slm, c
     return GWS_OK;
 }
 
+gws_status gws_tune_get(const gws_slm *slm, int *cfg) {
+    if (!cfg) return GWS_ERR_INVALID_ARG;
+    GS(check_slm(slm));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(std::make_tuple(slm->H, slm->W, slm->n_lambda));
+    *cfg = it != g_tuned.end() ? it->second : 0;
+    return GWS_OK;
+}
+
+gws_status gws_tune_set(const gws_slm *slm, int cfg) {
+    GS(check_slm(slm));
+    if (cfg < 0 || cfg > n_tile_cfgs()) return GWS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const auto key = std::make_tuple(slm->H, slm->W, slm->n_lambda);
+    if (cfg == 0) g_tuned.erase(key);
+    else g_tuned[key] = cfg;
+    return GWS_OK;
+}
+
 gws_status gws_autotune(const gws_gaussians *g, int64_t n, const gws_slm *slm, const gws_opts *opts,
                         void *field_scratch, int *best_cfg) {
     if (!best_cfg || !field_scratch) return GWS_ERR_INVALID_ARG;

@@ -9,8 +9,10 @@ from __future__ import annotations
 
 import contextlib
 import ctypes as C
+import json
 import math
 import os
+import tempfile
 import threading
 from dataclasses import dataclass
 
@@ -84,7 +86,8 @@ EXPORTS = ["gws_opts_default", "gws_status_string", "gws_version", "gws_workspac
            "gws_forward", "gws_forward_batched", "gws_backward", "gws_encode", "gws_get_device_status",
            "gws_depth_order", "gws_transmittance", "gws_footprints", "gws_last_launch_count", "gws_autotune",
            "gws_kernel_time_ms", "gws_footprint_pairs", "gws_encode_noalloc", "gws_holographics",
-           "gws_triangles_workspace_size", "gws_forward_triangles", "gws_tile_config", "gws_tile_config_ext"]
+           "gws_triangles_workspace_size", "gws_forward_triangles", "gws_tile_config", "gws_tile_config_ext",
+           "gws_tune_get", "gws_tune_set"]
 
 
 def lib_path(variant: str | None = None) -> str:
@@ -404,18 +407,76 @@ def footprint_pairs(g: Gaussians, slm: Slm, workspace=None, **kw) -> int:
     return int(out.value)
 
 
-def autotune(g: Gaussians, slm: Slm, workspace=None, **kw) -> int:
+def tune_cache_key(device_name: str, slm: Slm) -> str:
+    """Key of a grid class in an autotuner cache file: the device, the library's configuration
+    count (a build with another search space tunes again) and H x W x n_lambda."""
+    slm = Slm.of(slm)
+    n = int(load().gws_tile_config(0, None))
+    return f"{device_name}|{n} configs|{slm.H}x{slm.W}x{slm.n_lambda}"
+
+
+def _read_cache(path: str) -> dict:
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def tuned(slm: Slm) -> int:
+    """The configuration the library's autotuner table holds for this grid class (0: none)."""
+    lib = load()
+    c = C.c_int(0)
+    _check(lib.gws_tune_get(C.byref(Slm.of(slm)._c()), C.byref(c)), "gws_tune_get")
+    return int(c.value)
+
+
+def load_tuned(cache: str, device_name: str, slm: Slm) -> int:
+    """Restores a choice recorded in the JSON file ``cache`` for this device and grid class into
+    the library's table (gws_tune_set) and returns it; 0 if the file has none (or an id the
+    library does not have)."""
+    lib = load()
+    slm = Slm.of(slm)
+    c = _read_cache(cache).get(tune_cache_key(device_name, slm))
+    if not isinstance(c, int) or not 1 <= c <= int(lib.gws_tile_config(0, None)):
+        return 0
+    _check(lib.gws_tune_set(C.byref(slm._c()), C.c_int(c)), "gws_tune_set")
+    return c
+
+
+def store_tuned(cache: str, device_name: str, slm: Slm, cfg: int) -> None:
+    """Adds (or replaces) this device's and grid class's choice in the JSON file ``cache``
+    (written to a temporary file beside it, then renamed over it)."""
+    d = _read_cache(cache)
+    d[tune_cache_key(device_name, slm)] = int(cfg)
+    folder = os.path.dirname(os.path.abspath(cache))
+    fd, tmp = tempfile.mkstemp(prefix=".gws_tune_", dir=folder)
+    with os.fdopen(fd, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, cache)
+
+
+def autotune(g: Gaussians, slm: Slm, workspace=None, cache: str | None = None, **kw) -> int:
     """Times every splat tile configuration on this scene; the fastest becomes the default
-    for this (H, W, n_lambda).  Returns its id."""
+    for this (H, W, n_lambda).  Returns its id.  With ``cache`` (a JSON file), a choice recorded
+    there for this device and grid class is taken without timing, and a new one is recorded."""
     lib = load()
     slm = Slm.of(slm)
     g.check(slm.n_lambda)
+    dev_name = torch.cuda.get_device_name(g.mean.device) if cache is not None else None
+    if cache is not None:
+        c = load_tuned(cache, dev_name, slm)
+        if c:
+            return c
     opts = make_opts(**kw)
     scratch = torch.empty((slm.n_lambda, slm.H, slm.W), dtype=torch.complex64, device=g.mean.device)
     _attach_ws(opts, [g.n], slm, g.mean.device, workspace)
     best = C.c_int(0)
     _check(lib.gws_autotune(C.byref(g._c()), C.c_int64(g.n), C.byref(slm._c()), C.byref(opts),
                             C.c_void_p(scratch.data_ptr()), C.byref(best)), "gws_autotune")
+    if cache is not None:
+        store_tuned(cache, dev_name, slm, int(best.value))
     return int(best.value)
 
 

@@ -276,3 +276,37 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == C.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_autotuner_table_and_its_cache_file(tmp_path):
+    """gws_tune_set / gws_tune_get (host only) and the JSON cache that keeps choices between
+    processes: a stored choice is restored into the library's table for the same device and
+    grid class only; ids the library does not have, and unreadable files, restore nothing."""
+    lib = gws.load()
+    slm = gws.Slm(72, 88, 8e-6, 8e-6, (638e-9, 450e-9))
+    other = gws.Slm(72, 88, 8e-6, 8e-6, (520e-9,))
+    n = lib.gws_tile_config(0, None)
+    assert gws.tuned(slm) == 0
+    assert lib.gws_tune_set(C.byref(slm._c()), C.c_int(n + 1)) == 1
+    assert lib.gws_tune_set(C.byref(slm._c()), C.c_int(-1)) == 1
+    assert lib.gws_tune_get(C.byref(slm._c()), None) == 1
+    assert lib.gws_tune_set(C.byref(slm._c()), C.c_int(n)) == 0 and gws.tuned(slm) == n
+    assert gws.tuned(other) == 0
+    assert lib.gws_tune_set(C.byref(slm._c()), C.c_int(0)) == 0 and gws.tuned(slm) == 0
+
+    cache = str(tmp_path / "tune.json")
+    assert gws.load_tuned(cache, "GPU A", slm) == 0  # no file yet
+    gws.store_tuned(cache, "GPU A", slm, 2)
+    gws.store_tuned(cache, "GPU A", other, 3)
+    assert gws.load_tuned(cache, "GPU B", slm) == 0 and gws.tuned(slm) == 0  # another device
+    assert gws.load_tuned(cache, "GPU A", slm) == 2 and gws.tuned(slm) == 2
+    assert gws.load_tuned(cache, "GPU A", other) == 3 and gws.tuned(other) == 3
+    with open(cache) as f:
+        assert len(__import__("json").load(f)) == 2
+    gws.store_tuned(cache, "GPU A", slm, n + 5)  # an id this build does not have
+    assert gws.load_tuned(cache, "GPU A", slm) == 0
+    with open(cache, "w") as f:
+        f.write("{not json")
+    assert gws.load_tuned(cache, "GPU A", slm) == 0
+    for s in (slm, other):
+        assert lib.gws_tune_set(C.byref(s._c()), C.c_int(0)) == 0
