@@ -447,10 +447,12 @@ def load_tuned(cache: str, device_name: str, slm: Slm) -> int:
 
 def store_tuned(cache: str, device_name: str, slm: Slm, cfg: int) -> None:
     """Adds (or replaces) this device's and grid class's choice in the JSON file ``cache``
-    (written to a temporary file beside it, then renamed over it)."""
+    (written to a temporary file beside it, then renamed over it, so a reader never sees half a
+    file; of two processes storing at once, the later one's file wins)."""
     d = _read_cache(cache)
     d[tune_cache_key(device_name, slm)] = int(cfg)
     folder = os.path.dirname(os.path.abspath(cache))
+    os.makedirs(folder, exist_ok=True)
     fd, tmp = tempfile.mkstemp(prefix=".gws_tune_", dir=folder)
     with os.fdopen(fd, "w") as f:
         json.dump(d, f, indent=1, sort_keys=True)

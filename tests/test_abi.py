@@ -294,7 +294,7 @@ def test_autotuner_table_and_its_cache_file(tmp_path):
     assert gws.tuned(other) == 0
     assert lib.gws_tune_set(C.byref(slm._c()), C.c_int(0)) == 0 and gws.tuned(slm) == 0
 
-    cache = str(tmp_path / "tune.json")
+    cache = str(tmp_path / "sub" / "tune.json")  # its folder is created on the first store
     assert gws.load_tuned(cache, "GPU A", slm) == 0  # no file yet
     gws.store_tuned(cache, "GPU A", slm, 2)
     gws.store_tuned(cache, "GPU A", other, 3)
